@@ -1,0 +1,585 @@
+// WASABI oracle — TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow, single-threaded CPU restatement of the WASABI method of
+// Shimobaba et al., "Fast, large-scale hologram calculation in wavelet domain"
+// (arXiv 1708.04233), written from the paper's text.  Only the tests, the
+// package's smoke check and the benchmark's CPU-baseline leg may load it; the
+// product path (the CUDA library) never does, and the two share no code.
+//
+// Every function cites the passage it follows.  Where the paper is silent or
+// ambiguous the reading taken is stated beside the code (readings R1-R9):
+//   R1 PSF support radius (Sec. 1, step 1: "W_j is the PSF radius"):
+//      one radius R(z) = z * tan(asin(lambda / (2 p))) / p  [pixels], the
+//      alias-free diffraction limit of pitch p; support is the open disk
+//      n = du^2 + dv^2 < R^2; W_j is read as the diameter 2R.
+//   R2 depth quantisation (Sec. 1, step 1; Sec. 2 "Delta z = 30mm/29"):
+//      D bins of width dz = (zmax - zmin)/D, centre z_d = zmin + (d + 1/2) dz,
+//      d_j = min(D - 1, floor((z_j - zmin)/dz)).
+//   R3 coefficients kept (Sec. 1, step 1: N_r = pi (W_j/2)^2 gamma):
+//      gamma < 1: N_r = min(nnz, ceil(gamma * pi * R^2 - 1e-9));
+//      gamma >= 1: every nonzero coefficient.
+//   R4 wavelet: orthonormal 2-D Haar (the paper used coiflets, Sec. 1), Mallat
+//      layout of Fig. 2(a); LH is high-pass along x (columns) and sits at rows
+//      [0,S) x columns [S,2S), HL at rows [S,2S) x columns [0,S), HH at [S,2S)^2.
+//   R5 "strong" coefficients: key = re^2 + im^2 in FP64, descending; equal
+//      keys go to the lower Mallat linear index (row * W + col).
+//   R6 shift weight alpha (Eq. (2)): alpha = 2^-l at level l (l = L for the
+//      scaling band); a window sub-band position (p,q) lands at
+//      P = p + floor((x_j - W/2) / 2^l) (rule 0, "floor") or
+//      P = p + floor((x_j - W/2 + 2^(l-1)) / 2^l) (rule 1, "nearest");
+//      m <-> column <-> x, n <-> row <-> y; positions outside [0, Nh/2^l)
+//      are dropped.
+//   R7 binary hologram (Sec. 2): bit = 1 iff Re(u) > 0 (unit plane reference).
+//   R8 phase arithmetic of the FP32 PSF used for selection (so that the CPU
+//      and the GPU select the same coefficients): r = sqrt(fma(n, p^2, z^2)),
+//      t = r / lambda, f = t - floor(t) in FP64; g = (float) f; cos and sin of
+//      2 pi g from quadrant reduction and Taylor series in Horner form with
+//      fused multiply-adds in FP32 (J.-M. Muller, "Elementary Functions",
+//      range reduction + polynomial evaluation).
+//   R9 Eq. (1) has no 1/r factor and a +i sign, as printed; a_j is used as an
+//      amplitude.
+//
+// Build: g++ -O2 -ffp-contract=off -fPIC -shared (contraction must stay off:
+// the FP32 selection path depends on every rounding being the written one).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// ---------------------------------------------------------------- geometry --
+
+// R1: support radius in pixels for depth z (Sec. 1, step 1).
+double support_radius_px(double lambda, double pitch, double z) {
+  const double s = lambda / (2.0 * pitch);
+  const double t = s / std::sqrt(1.0 - s * s);  // tan(asin(s))
+  return (z * t) / pitch;
+}
+
+// R3: coefficient budget for gamma < 1 (Sec. 1, step 1).
+int64_t keep_target(double gamma, double R) {
+  const double area = kPi * (R * R);
+  return (int64_t)std::ceil(gamma * area - 1e-9);
+}
+
+// Floor division by a power of two, written out (no reliance on >> of a
+// negative number).
+int64_t floor_div(int64_t a, int64_t b) {
+  int64_t q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+  return q;
+}
+
+// R6: the level-l shift of Eq. (2) for a displacement X = x_j - W/2.
+int64_t level_shift(int64_t X, int l, int rule) {
+  const int64_t step = (int64_t)1 << l;
+  if (rule == 0) return floor_div(X, step);
+  return floor_div(X + step / 2, step);
+}
+
+// ------------------------------------------------------------------- phase --
+
+// R8: cos and sin of 2*pi*g for g in [0, 1], FP32, every step rounded as
+// written.  Quadrant reduction: g = q/4 + y with q = nearest integer of 4g and
+// |y| <= 1/8 (the subtraction is exact), x = 2*pi*y in [-pi/4, pi/4]; then the
+// Taylor series of sin to x^9 and of cos to x^10 in Horner form.
+void sincos2pi_f32(float g, float* c_out, float* s_out) {
+  const float two_pi = 6.28318530717958647692f;
+  const float S3 = -1.0f / 6.0f, S5 = 1.0f / 120.0f, S7 = -1.0f / 5040.0f,
+              S9 = 1.0f / 362880.0f;
+  const float C2 = -1.0f / 2.0f, C4 = 1.0f / 24.0f, C6 = -1.0f / 720.0f,
+              C8 = 1.0f / 40320.0f, C10 = -1.0f / 3628800.0f;
+  const float q = std::nearbyint(4.0f * g);
+  const float y = g - 0.25f * q;
+  const float x = y * two_pi;
+  const float x2 = x * x;
+  float ps = std::fma(x2, S9, S7);
+  ps = std::fma(x2, ps, S5);
+  ps = std::fma(x2, ps, S3);
+  const float sn = std::fma(x * x2, ps, x);
+  float pc = std::fma(x2, C10, C8);
+  pc = std::fma(x2, pc, C6);
+  pc = std::fma(x2, pc, C4);
+  pc = std::fma(x2, pc, C2);
+  const float cs = std::fma(x2, pc, 1.0f);
+  switch (((int)q) & 3) {
+    case 0: *c_out = cs;  *s_out = sn;  break;
+    case 1: *c_out = -sn; *s_out = cs;  break;
+    case 2: *c_out = -cs; *s_out = -sn; break;
+    default: *c_out = sn; *s_out = -cs; break;
+  }
+}
+
+// Fractional part of r / lambda for r = sqrt(n p^2 + z^2) (Eq. (1): the
+// phase 2*pi*r/lambda reduced modulo 2*pi).
+double phase_frac(int64_t n, double p2, double z2, double lambda) {
+  const double r = std::sqrt(std::fma((double)n, p2, z2));
+  const double t = r / lambda;
+  return t - std::floor(t);
+}
+
+// ---------------------------------------------------------------- the PSF --
+
+// Sec. 1, step 1: u_z = exp(i k r) circ(...), sampled on a W x W window whose
+// centre pixel (W/2, W/2) holds the point; du = u - W/2, dv = v - W/2.
+// FP32 form (R8).  Output: interleaved complex, row-major (row = v).
+void psf_f32(double lambda, double pitch, double z, int W, float* out) {
+  const double R = support_radius_px(lambda, pitch, z);
+  const double R2 = R * R;
+  const double p2 = pitch * pitch, z2 = z * z;
+  for (int v = 0; v < W; ++v) {
+    for (int u = 0; u < W; ++u) {
+      const int64_t du = u - W / 2, dv = v - W / 2;
+      const int64_t n = du * du + dv * dv;
+      float c = 0.0f, s = 0.0f;
+      if ((double)n < R2) {
+        const float g = (float)phase_frac(n, p2, z2, lambda);
+        sincos2pi_f32(g, &c, &s);
+      }
+      out[2 * ((int64_t)v * W + u) + 0] = c;
+      out[2 * ((int64_t)v * W + u) + 1] = s;
+    }
+  }
+}
+
+// FP64 form: the definition exp(i 2 pi r / lambda) evaluated with the C
+// library's cos and sin.
+void psf_f64(double lambda, double pitch, double z, int W, double* out) {
+  const double R = support_radius_px(lambda, pitch, z);
+  const double R2 = R * R;
+  const double p2 = pitch * pitch, z2 = z * z;
+  for (int v = 0; v < W; ++v) {
+    for (int u = 0; u < W; ++u) {
+      const int64_t du = u - W / 2, dv = v - W / 2;
+      const int64_t n = du * du + dv * dv;
+      double c = 0.0, s = 0.0;
+      if ((double)n < R2) {
+        const double f = phase_frac(n, p2, z2, lambda);
+        c = std::cos(2.0 * kPi * f);
+        s = std::sin(2.0 * kPi * f);
+      }
+      out[2 * ((int64_t)v * W + u) + 0] = c;
+      out[2 * ((int64_t)v * W + u) + 1] = s;
+    }
+  }
+}
+
+// -------------------------------------------------------------- Haar (R4) --
+
+// One forward level on the top-left S x S block of an n x n interleaved
+// complex array (row stride n): each 2x2 block (x00 x01 / x10 x11) gives
+//   s  = ((x00 + x01) + (x10 + x11)) / 2
+//   LH = ((x00 - x01) + (x10 - x11)) / 2   (high along x)
+//   HL = ((x00 + x01) - (x10 + x11)) / 2   (high along y)
+//   HH = ((x00 - x01) - (x10 - x11)) / 2
+template <typename T>
+void haar_fwd_level(T* a, int64_t n, int64_t S, std::vector<T>& tmp) {
+  const int64_t h = S / 2;
+  tmp.assign((size_t)(2 * S * S), T(0));
+  for (int64_t i = 0; i < h; ++i) {
+    for (int64_t j = 0; j < h; ++j) {
+      for (int c = 0; c < 2; ++c) {
+        const T x00 = a[2 * ((2 * i) * n + 2 * j) + c];
+        const T x01 = a[2 * ((2 * i) * n + 2 * j + 1) + c];
+        const T x10 = a[2 * ((2 * i + 1) * n + 2 * j) + c];
+        const T x11 = a[2 * ((2 * i + 1) * n + 2 * j + 1) + c];
+        const T half = T(0.5);
+        tmp[2 * (i * S + j) + c] = ((x00 + x01) + (x10 + x11)) * half;
+        tmp[2 * (i * S + h + j) + c] = ((x00 - x01) + (x10 - x11)) * half;
+        tmp[2 * ((h + i) * S + j) + c] = ((x00 + x01) - (x10 + x11)) * half;
+        tmp[2 * ((h + i) * S + h + j) + c] = ((x00 - x01) - (x10 - x11)) * half;
+      }
+    }
+  }
+  for (int64_t r = 0; r < S; ++r)
+    std::memcpy(&a[2 * r * n], &tmp[2 * r * S], sizeof(T) * 2 * S);
+}
+
+// Inverse of one level: the transpose of the orthonormal map above,
+//   x00 = ((s + LH) + (HL + HH)) / 2      x01 = ((s - LH) + (HL - HH)) / 2
+//   x10 = ((s + LH) - (HL + HH)) / 2      x11 = ((s - LH) - (HL - HH)) / 2
+template <typename T>
+void haar_inv_level(T* a, int64_t n, int64_t S, std::vector<T>& tmp) {
+  const int64_t h = S / 2;
+  tmp.assign((size_t)(2 * S * S), T(0));
+  for (int64_t i = 0; i < h; ++i) {
+    for (int64_t j = 0; j < h; ++j) {
+      for (int c = 0; c < 2; ++c) {
+        const T s = a[2 * (i * n + j) + c];
+        const T lh = a[2 * (i * n + h + j) + c];
+        const T hl = a[2 * ((h + i) * n + j) + c];
+        const T hh = a[2 * ((h + i) * n + h + j) + c];
+        const T half = T(0.5);
+        tmp[2 * ((2 * i) * S + 2 * j) + c] = ((s + lh) + (hl + hh)) * half;
+        tmp[2 * ((2 * i) * S + 2 * j + 1) + c] = ((s - lh) + (hl - hh)) * half;
+        tmp[2 * ((2 * i + 1) * S + 2 * j) + c] = ((s + lh) - (hl + hh)) * half;
+        tmp[2 * ((2 * i + 1) * S + 2 * j + 1) + c] = ((s - lh) - (hl - hh)) * half;
+      }
+    }
+  }
+  for (int64_t r = 0; r < S; ++r)
+    std::memcpy(&a[2 * r * n], &tmp[2 * r * S], sizeof(T) * 2 * S);
+}
+
+// Sec. 1, step 1 ("FWT") and step 3 ("inverse FWT"), L levels, in place.
+template <typename T>
+void haar_fwd(T* a, int64_t n, int L) {
+  std::vector<T> tmp;
+  for (int l = 1; l <= L; ++l) haar_fwd_level(a, n, n >> (l - 1), tmp);
+}
+template <typename T>
+void haar_inv(T* a, int64_t n, int L) {
+  std::vector<T> tmp;
+  for (int l = L; l >= 1; --l) haar_inv_level(a, n, n >> (l - 1), tmp);
+}
+
+// Position of Mallat entry (row, col) of an n x n, L-level transform:
+// level l (1..L), band 0 = scaling (l = L only), 1 = LH, 2 = HL, 3 = HH,
+// sub-band coordinates p (x, column) and q (y, row).  Fig. 2(a).
+void mallat_decode(int64_t row, int64_t col, int64_t n, int L, int* lev,
+                   int* band, int64_t* p, int64_t* q) {
+  for (int l = 1; l <= L; ++l) {
+    const int64_t S = n >> l;
+    if (row >= S || col >= S) {
+      *lev = l;
+      if (row < S) { *band = 1; *p = col - S; *q = row; }
+      else if (col < S) { *band = 2; *p = col; *q = row - S; }
+      else { *band = 3; *p = col - S; *q = row - S; }
+      return;
+    }
+  }
+  *lev = L; *band = 0; *p = col; *q = row;
+}
+
+// Inverse of mallat_decode for a hologram-sized buffer of side n.
+void mallat_encode(int lev, int band, int64_t P, int64_t Q, int64_t n,
+                   int64_t* row, int64_t* col) {
+  const int64_t S = n >> lev;
+  switch (band) {
+    case 0: *row = Q; *col = P; break;
+    case 1: *row = Q; *col = S + P; break;
+    case 2: *row = S + Q; *col = P; break;
+    default: *row = S + Q; *col = S + P; break;
+  }
+}
+
+// ---------------------------------------------------------- selection (R5) --
+
+// Sec. 1, step 1: keep N_r strong coefficients.  Returns N_r; idx_out gets
+// the kept Mallat linear indices in ascending order.
+template <typename T>
+int64_t select_strong(const T* coef, int W, double gamma, double R,
+                      int32_t* idx_out) {
+  const int64_t n = (int64_t)W * W;
+  std::vector<std::pair<double, int32_t>> nz;
+  for (int64_t i = 0; i < n; ++i) {
+    const double re = (double)coef[2 * i], im = (double)coef[2 * i + 1];
+    const double key = re * re + im * im;
+    if (key > 0.0) nz.emplace_back(key, (int32_t)i);
+  }
+  int64_t nr = (int64_t)nz.size();
+  if (gamma < 1.0) nr = std::min<int64_t>(nr, keep_target(gamma, R));
+  if (nr < 0) nr = 0;
+  std::sort(nz.begin(), nz.end(), [](const std::pair<double, int32_t>& a,
+                                     const std::pair<double, int32_t>& b) {
+    if (a.first != b.first) return a.first > b.first;
+    return a.second < b.second;
+  });
+  std::vector<int32_t> kept((size_t)nr);
+  for (int64_t k = 0; k < nr; ++k) kept[(size_t)k] = nz[(size_t)k].second;
+  std::sort(kept.begin(), kept.end());
+  std::copy(kept.begin(), kept.end(), idx_out);
+  return nr;
+}
+
+// ------------------------------------------------------------------- LUT --
+
+// Sec. 1, step 1 for every depth: PSF, L-level FWT, keep N_r strong.
+// Per depth d, entries [off_d, off_d + nr[d]) of idx/val, off_d = sum of the
+// earlier nr.  Returns 0, or -1 when cap is too small or a window is too
+// small for its PSF (2R + 1 > W).
+template <typename T>
+int build_lut(double lambda, double pitch, const double* zd, int D, int W,
+              int L, double gamma, int64_t* nr, int64_t cap, int32_t* idx,
+              T* val, int threads, bool fp32_psf) {
+  const int64_t n = (int64_t)W * W;
+  std::vector<std::vector<int32_t>> sel((size_t)D);
+  std::vector<std::vector<T>> vals((size_t)D);
+  int bad = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads > 0 ? threads : 1) reduction(+ : bad)
+#endif
+  for (int d = 0; d < D; ++d) {
+    const double R = support_radius_px(lambda, pitch, zd[d]);
+    if (2.0 * R + 1.0 > (double)W) { bad += 1; continue; }
+    std::vector<T> coef((size_t)(2 * n));
+    if (fp32_psf) {
+      std::vector<float> tmp((size_t)(2 * n));
+      psf_f32(lambda, pitch, zd[d], W, tmp.data());
+      for (int64_t i = 0; i < 2 * n; ++i) coef[(size_t)i] = (T)tmp[(size_t)i];
+    } else {
+      std::vector<double> tmp((size_t)(2 * n));
+      psf_f64(lambda, pitch, zd[d], W, tmp.data());
+      for (int64_t i = 0; i < 2 * n; ++i) coef[(size_t)i] = (T)tmp[(size_t)i];
+    }
+    haar_fwd(coef.data(), W, L);
+    std::vector<int32_t> kept((size_t)n);
+    const int64_t k = select_strong(coef.data(), W, gamma, R, kept.data());
+    kept.resize((size_t)k);
+    std::vector<T> v((size_t)(2 * k));
+    for (int64_t i = 0; i < k; ++i) {
+      v[(size_t)(2 * i)] = coef[(size_t)(2 * kept[(size_t)i])];
+      v[(size_t)(2 * i + 1)] = coef[(size_t)(2 * kept[(size_t)i] + 1)];
+    }
+    sel[(size_t)d] = std::move(kept);
+    vals[(size_t)d] = std::move(v);
+  }
+  if (bad) return -1;
+  int64_t off = 0;
+  for (int d = 0; d < D; ++d) {
+    const int64_t k = (int64_t)sel[(size_t)d].size();
+    if (off + k > cap) return -1;
+    nr[d] = k;
+    std::copy(sel[(size_t)d].begin(), sel[(size_t)d].end(), idx + off);
+    std::copy(vals[(size_t)d].begin(), vals[(size_t)d].end(), val + 2 * off);
+    off += k;
+  }
+  return 0;
+}
+
+// ----------------------------------------------------- superposition (Eq. 2) --
+
+// Eq. (2) with the sub-hologram coordinate transform of Sec. 1, large-scale
+// step 2 (x'_j = x_j - ox): psi (an Nh x Nh Mallat buffer, interleaved
+// complex, accumulated into) += a_j c_k at the shifted position of every kept
+// coefficient k of point j's depth (R6).  Accumulation order: points in input
+// order, coefficients in LUT order.
+template <typename T>
+int superpose(int W, int L, int D, const int64_t* nr, const int32_t* idx,
+              const T* val, const int32_t* x, const int32_t* y, const float* a,
+              const uint32_t* d, int64_t N, int64_t Nh, int64_t ox, int64_t oy,
+              int rule, T* psi) {
+  std::vector<int64_t> off((size_t)D + 1, 0);
+  for (int k = 0; k < D; ++k) off[(size_t)k + 1] = off[(size_t)k] + nr[k];
+  // The (level, band, p, q) of every LUT entry (a pure function of its index).
+  const int64_t total = off[(size_t)D];
+  std::vector<int> lev((size_t)total), band((size_t)total);
+  std::vector<int64_t> pp((size_t)total), qq((size_t)total);
+  for (int64_t e = 0; e < total; ++e)
+    mallat_decode(idx[e] / W, idx[e] % W, W, L, &lev[(size_t)e],
+                  &band[(size_t)e], &pp[(size_t)e], &qq[(size_t)e]);
+  const int64_t margin = (int64_t)1 << L;
+  for (int64_t j = 0; j < N; ++j) {
+    if (d[j] >= (uint32_t)D) return -1;
+    const int64_t X = (int64_t)x[j] - ox - W / 2;
+    const int64_t Y = (int64_t)y[j] - oy - W / 2;
+    // A point whose whole window (plus one tile) lies off this buffer has
+    // every coefficient dropped by the range test below; skip it early.
+    if (X + W + margin < 0 || X - margin >= Nh || Y + W + margin < 0 ||
+        Y - margin >= Nh)
+      continue;
+    const T aj = (T)a[j];
+    for (int64_t e = off[d[j]]; e < off[d[j] + 1]; ++e) {
+      const int l = lev[(size_t)e];
+      const int64_t P = pp[(size_t)e] + level_shift(X, l, rule);
+      const int64_t Q = qq[(size_t)e] + level_shift(Y, l, rule);
+      const int64_t Sh = Nh >> l;
+      if (P < 0 || P >= Sh || Q < 0 || Q >= Sh) continue;
+      int64_t row, col;
+      mallat_encode(l, band[(size_t)e], P, Q, Nh, &row, &col);
+      T* dst = psi + 2 * (row * Nh + col);
+      dst[0] += aj * val[2 * e];
+      dst[1] += aj * val[2 * e + 1];
+    }
+  }
+  return 0;
+}
+
+// --------------------------------------------------------- Eq. (1) directly --
+
+// u(x_h, y_h) = sum_j a_j exp(i 2 pi r_hj / lambda) [aperture], FP64, for the
+// region [ox, ox + w) x [oy, oy + h) (row-major, interleaved).  z is per point.
+void cgh_direct(double lambda, double pitch, const int32_t* x, const int32_t* y,
+                const float* a, const double* z, int64_t N, int64_t ox,
+                int64_t oy, int64_t w, int64_t h, int aperture, double* u,
+                int threads) {
+  const double p2 = pitch * pitch;
+  std::vector<double> R2((size_t)N);
+  for (int64_t j = 0; j < N; ++j) {
+    const double R = support_radius_px(lambda, pitch, z[j]);
+    R2[(size_t)j] = R * R;
+  }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads > 0 ? threads : 1)
+#endif
+  for (int64_t yy = 0; yy < h; ++yy) {
+    for (int64_t xx = 0; xx < w; ++xx) {
+      double re = 0.0, im = 0.0;
+      for (int64_t j = 0; j < N; ++j) {
+        const int64_t dx = ox + xx - x[j], dy = oy + yy - y[j];
+        const int64_t n = dx * dx + dy * dy;
+        if (aperture && !((double)n < R2[(size_t)j])) continue;
+        const double f = phase_frac(n, p2, z[j] * z[j], lambda);
+        re += (double)a[j] * std::cos(2.0 * kPi * f);
+        im += (double)a[j] * std::sin(2.0 * kPi * f);
+      }
+      u[2 * (yy * w + xx) + 0] = re;
+      u[2 * (yy * w + xx) + 1] = im;
+    }
+  }
+}
+
+}  // namespace
+
+// =================================================================== C ABI ==
+
+extern "C" {
+
+double orc_support_radius(double lambda, double pitch, double z) {
+  return support_radius_px(lambda, pitch, z);
+}
+
+int64_t orc_keep_target(double gamma, double R) { return keep_target(gamma, R); }
+
+// R2: bin centres of D depth bins over [zmin, zmax].
+void orc_depth_grid(double zmin, double zmax, int D, double* zd) {
+  const double dz = (zmax - zmin) / (double)D;
+  for (int d = 0; d < D; ++d) zd[d] = zmin + ((double)d + 0.5) * dz;
+}
+
+// R2: depth index of each point; returns the number of points outside
+// [zmin, zmax] (their index is set to D).
+int64_t orc_quantize(const double* z, int64_t N, double zmin, double zmax,
+                     int D, uint32_t* d) {
+  const double dz = (zmax - zmin) / (double)D;
+  int64_t bad = 0;
+  for (int64_t j = 0; j < N; ++j) {
+    if (!(z[j] >= zmin && z[j] <= zmax)) { d[j] = (uint32_t)D; ++bad; continue; }
+    int64_t k = (int64_t)std::floor((z[j] - zmin) / dz);
+    if (k > D - 1) k = D - 1;
+    d[j] = (uint32_t)k;
+  }
+  return bad;
+}
+
+void orc_sincos2pi_f32(const float* g, int64_t n, float* c, float* s) {
+  for (int64_t i = 0; i < n; ++i) sincos2pi_f32(g[i], &c[i], &s[i]);
+}
+
+void orc_psf_f32(double lambda, double pitch, double z, int W, float* out) {
+  psf_f32(lambda, pitch, z, W, out);
+}
+void orc_psf_f64(double lambda, double pitch, double z, int W, double* out) {
+  psf_f64(lambda, pitch, z, W, out);
+}
+
+void orc_haar_fwd_f32(float* a, int64_t n, int L) { haar_fwd(a, n, L); }
+void orc_haar_inv_f32(float* a, int64_t n, int L) { haar_inv(a, n, L); }
+void orc_haar_fwd_f64(double* a, int64_t n, int L) { haar_fwd(a, n, L); }
+void orc_haar_inv_f64(double* a, int64_t n, int L) { haar_inv(a, n, L); }
+
+void orc_mallat_decode(int64_t row, int64_t col, int64_t n, int L, int* lev,
+                       int* band, int64_t* p, int64_t* q) {
+  mallat_decode(row, col, n, L, lev, band, p, q);
+}
+
+int64_t orc_select_f32(const float* coef, int W, double gamma, double R,
+                       int32_t* idx_out) {
+  return select_strong(coef, W, gamma, R, idx_out);
+}
+int64_t orc_select_f64(const double* coef, int W, double gamma, double R,
+                       int32_t* idx_out) {
+  return select_strong(coef, W, gamma, R, idx_out);
+}
+
+int orc_build_lut_f32(double lambda, double pitch, const double* zd, int D,
+                      int W, int L, double gamma, int64_t* nr, int64_t cap,
+                      int32_t* idx, float* val, int threads) {
+  return build_lut<float>(lambda, pitch, zd, D, W, L, gamma, nr, cap, idx, val,
+                          threads, true);
+}
+int orc_build_lut_f64(double lambda, double pitch, const double* zd, int D,
+                      int W, int L, double gamma, int64_t* nr, int64_t cap,
+                      int32_t* idx, double* val, int threads) {
+  return build_lut<double>(lambda, pitch, zd, D, W, L, gamma, nr, cap, idx,
+                           val, threads, false);
+}
+
+int orc_superpose_f32(int W, int L, int D, const int64_t* nr, const int32_t* idx,
+                      const float* val, const int32_t* x, const int32_t* y,
+                      const float* a, const uint32_t* d, int64_t N, int64_t Nh,
+                      int64_t ox, int64_t oy, int rule, float* psi) {
+  return superpose<float>(W, L, D, nr, idx, val, x, y, a, d, N, Nh, ox, oy,
+                          rule, psi);
+}
+int orc_superpose_f64(int W, int L, int D, const int64_t* nr, const int32_t* idx,
+                      const double* val, const int32_t* x, const int32_t* y,
+                      const float* a, const uint32_t* d, int64_t N, int64_t Nh,
+                      int64_t ox, int64_t oy, int rule, double* psi) {
+  return superpose<double>(W, L, D, nr, idx, val, x, y, a, d, N, Nh, ox, oy,
+                           rule, psi);
+}
+
+// Sec. 1, large-scale steps 2-4 for one sub-hologram (s, t) of side Ns:
+// shift the points, superpose into a fresh Ns x Ns Mallat buffer, inverse
+// FWT.  u_sub: Ns x Ns interleaved complex, row-major.
+int orc_subhologram_f32(int W, int L, int D, const int64_t* nr,
+                        const int32_t* idx, const float* val, const int32_t* x,
+                        const int32_t* y, const float* a, const uint32_t* d,
+                        int64_t N, int64_t Ns, int64_t s, int64_t t, int rule,
+                        float* u_sub) {
+  std::memset(u_sub, 0, sizeof(float) * 2 * Ns * Ns);
+  const int rc = superpose<float>(W, L, D, nr, idx, val, x, y, a, d, N, Ns,
+                                  s * Ns, t * Ns, rule, u_sub);
+  if (rc) return rc;
+  haar_inv(u_sub, Ns, L);
+  return 0;
+}
+int orc_subhologram_f64(int W, int L, int D, const int64_t* nr,
+                        const int32_t* idx, const double* val, const int32_t* x,
+                        const int32_t* y, const float* a, const uint32_t* d,
+                        int64_t N, int64_t Ns, int64_t s, int64_t t, int rule,
+                        double* u_sub) {
+  std::memset(u_sub, 0, sizeof(double) * 2 * Ns * Ns);
+  const int rc = superpose<double>(W, L, D, nr, idx, val, x, y, a, d, N, Ns,
+                                   s * Ns, t * Ns, rule, u_sub);
+  if (rc) return rc;
+  haar_inv(u_sub, Ns, L);
+  return 0;
+}
+
+// R7: bits row-major, 8 pixels per byte, least significant bit = lowest x.
+void orc_binarize_f32(const float* u, int64_t w, int64_t h, uint8_t* bits) {
+  std::memset(bits, 0, (size_t)((w * h + 7) / 8));
+  for (int64_t yy = 0; yy < h; ++yy)
+    for (int64_t xx = 0; xx < w; ++xx) {
+      const int64_t i = yy * w + xx;
+      if (u[2 * i] > 0.0f) bits[i >> 3] |= (uint8_t)(1u << (i & 7));
+    }
+}
+
+void orc_cgh_direct_f64(double lambda, double pitch, const int32_t* x,
+                        const int32_t* y, const float* a, const double* z,
+                        int64_t N, int64_t ox, int64_t oy, int64_t w, int64_t h,
+                        int aperture, double* u, int threads) {
+  cgh_direct(lambda, pitch, x, y, a, z, N, ox, oy, w, h, aperture, u, threads);
+}
+
+int orc_have_openmp(void) {
+#ifdef _OPENMP
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+}  // extern "C"
