@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""WASABI hologram benchmark (paper-scale 65,536^2 binarised hologram).
+
+One step = the whole hot path on one batch of synthetic input: LUT build
+(PSF + Haar + shrinkage, 128 depths), point quantisation, binning +
+superposition into the 34.4 GB tile-major wavelet buffer, and the fused
+inverse Haar + binarisation.  Inputs are resident in HBM when the timed region
+starts; the wavelet buffer (34.4 GB) is far larger than L2, so no flush is
+needed.  `e2e` repeats the same step through the public API with pinned host
+buffers: the host->device copy of the points and the device->host copy of the
+bits are inside its timed region.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import CONFIGS  # noqa: E402
+
+METRIC = "WASABI hologram Mpoint*coeff/s at 65536^2 (hologram s, HBM fraction)"
+UNIT = "Mpoint*coeff/s"
+KERNELS_PER_STEP = 11  # psf_haar, select, tile_count, tile_scan, scatter, quantize,
+#                        count, scan, scatter_points, superpose, inverse
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload_desc(c):
+    return {"workload": f"{c.name}: {c.Nh}x{c.Nh} binarised hologram, {c.N} height-field points, "
+                        f"{c.D} depths, W={c.W}, L={c.L}, keep={c.gamma}",
+            "Nh": c.Nh, "N": c.N, "lambda_m": c.lam, "pitch_m": c.pitch, "z_range_m": [c.zmin, c.zmax],
+            "depths": c.D, "window": c.W, "levels": c.L, "keep_ratio": c.gamma, "output": c.output,
+            "lut_dtype": c.lut_dtype, "l2": "inputs larger than L2 (34.4 GB wavelet buffer per step)"}
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = [r.split(",") for r in self.out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].strip().replace(".", "").isdigit())}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(c, pts, threads: int, n_sub: int = 2, sub: int = 1024, depths_sample: int = 4):
+    """Time the oracle as it stands on a bounded sample of the workload and
+    scale to the whole hologram: `depths_sample` LUT depths (of c.D) and
+    `n_sub` sub-holograms of sub x sub (of (Nh/sub)^2), paper procedure."""
+    import concurrent.futures as cf
+
+    import oracle
+    zd = oracle.depth_grid(c.zmin, c.zmax, c.D)
+    d, _ = oracle.quantize(pts["z"], c.zmin, c.zmax, c.D)
+    idx = np.linspace(0, c.D - 1, depths_sample).astype(int)
+    t0 = time.perf_counter()
+    oracle.build_lut(c.lam, c.pitch, zd[idx], c.W, c.L, c.gamma, threads=threads)
+    t_lut = (time.perf_counter() - t0) * c.D / depths_sample
+    full = oracle.build_lut(c.lam, c.pitch, zd, c.W, c.L, c.gamma, threads=threads)  # untimed
+    p = dict(pts, d=d)
+    per_side = c.Nh // sub
+    rng = np.random.default_rng(0)
+    cells = [(int(s), int(t)) for s, t in rng.integers(0, per_side, (max(n_sub, threads), 2))][:max(n_sub, threads)]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda st: oracle.subhologram(full, p, sub, st[0], st[1]), cells))
+    t_sub = (time.perf_counter() - t0) / len(cells) * threads  # per sub-hologram, one thread
+    t_holo = t_sub * per_side * per_side / threads + t_lut
+    work = float(np.sum(full.nr[d]))
+    return {"value": work / t_holo / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"LUT for {depths_sample} of {c.D} depths (scaled x{c.D / depths_sample:g}) + "
+                      f"{len(cells)} random {sub}x{sub} sub-holograms (paper Sec. 1 procedure, scaled to "
+                      f"{per_side * per_side}), threads={threads}",
+            "est_hologram_s": t_holo}
+
+
+def run_reference(args, c):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pts = c.points()
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_sample(c, pts, threads, n_sub=1, depths_sample=1)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample(c, pts, threads, n_sub=1, depths_sample=1))
+    wall = time.perf_counter() - t0
+    v = float(np.median([s["value"] for s in vals]))
+    cb = dict(vals[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": f"synthetic (seeded height-field point cloud, seed {c.seed})",
+            "config": _workload_desc(c), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, c):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1708_04233_gb300 as w
+    from paper_1708_04233_gb300 import build as wbuild
+    wbuild.build()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    pts = c.points()
+    N = c.N
+    depths = w.depth_grid(c.zmin, c.zmax, c.D)
+    x = torch.from_numpy(pts["x"]).to(dev)
+    y = torch.from_numpy(pts["y"]).to(dev)
+    z = torch.from_numpy(pts["z"]).to(dev)
+    a = torch.from_numpy(pts["a"]).to(dev)
+    pbuf = torch.empty((N, 4), dtype=torch.int32, device=dev)
+    wbuf = torch.empty(c.Nh * c.Nh, dtype=torch.complex64, device=dev)
+    bits = torch.empty(c.Nh * c.Nh // 8, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    ev = {k: [] for k in ("lut", "superpose", "inverse")}
+
+    def step(record=False, xs=x, ys=y, zs=z, as_=a):
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True) if record else None
+            if record:
+                e0.record(stream)
+            lut = w.build_lut(c.lam, c.pitch, depths, c.W, c.L, c.gamma, dtype=c.lut_dtype, stream=stream)
+            w.quantize_points(xs, ys, zs, as_, c.zmin, c.zmax, c.D, out=pbuf, stream=stream)
+            if record:
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record(stream)
+            if step.scratch is None:
+                step.scratch = torch.empty(w.scratch_bytes(lut, N, c.Nh, c.Nh), dtype=torch.uint8, device=dev)
+            w.superpose(lut, pbuf, c.Nh, c.Nh, rule=0, wbuf=wbuf, scratch=step.scratch, stream=stream)
+            if record:
+                e2 = torch.cuda.Event(enable_timing=True)
+                e2.record(stream)
+            w.inverse_haar(wbuf, c.Nh, c.Nh, c.L, bits=bits, want="bits", stream=stream)
+            if record:
+                e3 = torch.cuda.Event(enable_timing=True)
+                e3.record(stream)
+                ev["lut"].append((e0, e1))
+                ev["superpose"].append((e1, e2))
+                ev["inverse"].append((e2, e3))
+            step.last_lut = lut
+            lut.close()
+            return lut
+    step.scratch = None
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    # Warm-up (also sizes the scratch and validates the device status).
+    for _ in range(max(args.warmup, 1)):
+        step()
+    w.sync_status(stream)
+    # Work units: sum over points of N_r(d_j) (kept coefficients per point).
+    lut = w.build_lut(c.lam, c.pitch, depths, c.W, c.L, c.gamma, dtype=c.lut_dtype, stream=stream)
+    nr = lut.counts()
+    lut.close()
+    d_host = pbuf[:, 3].cpu().numpy().view(np.uint32)
+    units = float(np.sum(nr[d_host]))
+
+    peak, peak_kind = _peaks()
+    with ClockSampler(local) as clk:
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(record=True)
+        t1.record(stream)
+        barrier()
+    w.sync_status(stream)
+    ms = t0.elapsed_time(t1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    stage_ms = {k: float(np.mean([s.elapsed_time(e) for s, e in v])) for k, v in ev.items()}
+
+    # End to end through the public API with pinned host buffers.
+    hx = torch.from_numpy(pts["x"]).pin_memory()
+    hy = torch.from_numpy(pts["y"]).pin_memory()
+    hz = torch.from_numpy(pts["z"]).pin_memory()
+    ha = torch.from_numpy(pts["a"]).pin_memory()
+    hbits = torch.empty(bits.numel(), dtype=torch.uint8).pin_memory()
+    dx, dy, dz, da = (torch.empty_like(t) for t in (x, y, z, a))
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            for d_, h_ in ((dx, hx), (dy, hy), (dz, hz), (da, ha)):
+                d_.copy_(h_, non_blocking=True)
+            step(xs=dx, ys=dy, zs=dz, as_=da)
+            hbits.copy_(bits, non_blocking=True)
+    e2e_step()
+    barrier()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_ms = (time.perf_counter() - te) * 1e3 / args.steps
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    h2d = sum(t.numel() * t.element_size() for t in (hx, hy, hz, ha))
+    d2h = hbits.numel()
+
+    inv_bytes = c.Nh * c.Nh * 8 + c.Nh * c.Nh // 8
+    sup_bytes = c.Nh * c.Nh * 8 + N * 16
+    inv_gbs = inv_bytes / (stage_ms["inverse"] * 1e-3) / 1e9
+    sup_gbs = sup_bytes / (stage_ms["superpose"] * 1e-3) / 1e9
+    dom = "inverse" if stage_ms["inverse"] >= stage_ms["superpose"] else "superpose"
+    ach = inv_gbs if dom == "inverse" else sup_gbs
+    roof = {"kernel": "inverse_kernel<4> (fused inverse Haar + binarise)" if dom == "inverse"
+            else "superpose_kernel<4,f32> (+ binning, one ABI call)",
+            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_source": peak_kind, "traffic": None,
+            "algorithmic_bytes": inv_bytes if dom == "inverse" else sup_bytes}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": units * world / (ms * 1e-3) / 1e6, "unit": UNIT,
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": f"synthetic (seeded height-field point cloud, SplitMix64 seed {c.seed})",
+               "config": dict(_workload_desc(c), parallelism=f"replicas x{world}"),
+               "hologram_s": ms * 1e-3, "point_coeff_per_step": units,
+               "stages_ms": stage_ms,
+               "superpose_mpc_s": units / (stage_ms["superpose"] * 1e-3) / 1e6,
+               "hbm": {"inverse_gbs": inv_gbs, "inverse_frac": inv_gbs / peak,
+                       "superpose_write_gbs": sup_gbs, "superpose_frac": sup_gbs / peak},
+               "roofline": roof,
+               "e2e": {"value": units * world / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+                       "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+               "gpu_launches": KERNELS_PER_STEP * args.steps,
+               "clocks": clk.summary()}
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = oracle_sample(c, pts, os.cpu_count() or 1)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wasabi", choices=["wasabi", "reference"])
+    ap.add_argument("--config", default="C3", choices=["C2", "C3", "C4"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    c = CONFIGS[args.config]
+    if args.impl == "reference":
+        run_reference(args, c)
+    else:
+        run_gpu(args, c)
+
+
+if __name__ == "__main__":
+    main()

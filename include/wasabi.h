@@ -1,0 +1,201 @@
+/*
+ * wasabi.h — C ABI of libwasabi, a GB300 (sm_103a) implementation of WASABI
+ * (wavelet shrinkage-based superposition) hologram synthesis, after
+ * T. Shimobaba et al., "Fast, large-scale hologram calculation in wavelet
+ * domain", arXiv 1708.04233.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns a wasabi_status; no exception and no abort ever
+ *    crosses this boundary.  On failure wasabi_last_error() returns a
+ *    thread-local message.
+ *  - "dev" pointers are CUDA device pointers on the CURRENT device; "host"
+ *    pointers are ordinary host memory.  Streams are cudaStream_t passed as
+ *    void* (NULL = the legacy default stream).
+ *  - Argument checks are synchronous.  Device work is asynchronous on the
+ *    given stream unless stated otherwise; errors that only the device can see
+ *    (a point's depth index out of range, a timed-out wait) are recorded in a
+ *    per-device status word that wasabi_sync_status() reads and clears.
+ *  - The caller owns points, wavelet buffers, outputs and scratch memory; the
+ *    library owns only wasabi_lut objects.
+ *  - Lengths (wavelength, pitch, depths) share one unit, e.g. metres.
+ *
+ * Geometry shared by all calls (the readings of the paper taken here):
+ *  - Pixel (x, y): x is the column, y the row; row-major images.
+ *  - PSF support radius at depth z (Sec. 1, step 1 "PSF radius"):
+ *      R(z) = z * s / sqrt(1 - s^2) / pitch  [pixels],  s = lambda / (2 pitch),
+ *    i.e. z tan(asin(lambda / 2p)) / p, the alias-free limit; the support is
+ *    the open disk du^2 + dv^2 < R^2 around the point.
+ *  - Haar: orthonormal, L levels.  On each 2x2 block (x00 x01 / x10 x11)
+ *      s  = ((x00 + x01) + (x10 + x11)) / 2     LH = ((x00 - x01) + (x10 - x11)) / 2
+ *      HL = ((x00 + x01) - (x10 + x11)) / 2     HH = ((x00 - x01) - (x10 - x11)) / 2
+ *    (LH is high-pass along x).  Mallat layout (Fig. 2(a)): at level l with
+ *    sub-band side S, LH sits at rows [0,S) x cols [S,2S), HL at rows [S,2S) x
+ *    cols [0,S), HH at [S,2S)^2; the scaling band of level L at [0,S)^2.
+ *  - Tile-major wavelet buffer ("wbuf"): a hologram of holo_w x holo_h pixels
+ *    is cut into 2^L x 2^L tiles (holo_w, holo_h multiples of 2^L); tile
+ *    (TX, TY) holds the 4^L Haar coefficients whose support lies inside it,
+ *    contiguously, at complex offset (TY * holo_w/2^L + TX) * 4^L.  Within a
+ *    tile, the coefficient of level l, band b (0 = scaling, only at l = L;
+ *    1 = LH, 2 = HL, 3 = HH) and in-tile position (ix, iy), with m = L - l and
+ *    0 <= ix, iy < 2^m, is at slot  (b << 2m) + (iy << m) + ix.
+ *    Complex values are float2 (re, im), i.e. complex64.
+ *  - Shift rule of Eq. (2) (alpha = 2^-l): a window coefficient at sub-band
+ *    position (p, q) of level l lands at P = p + shift_l(x - W/2),
+ *    Q = q + shift_l(y - W/2) with shift_l(X) = floor(X / 2^l) (FLOOR) or
+ *    floor((X + 2^(l-1)) / 2^l) (NEAREST); the scaling band uses l = L.
+ *    Positions outside [0, holo/2^l) are dropped.
+ */
+#ifndef WASABI_H
+#define WASABI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int wasabi_status;
+#define WASABI_OK 0
+#define WASABI_E_INVALID (-1) /* bad argument (sizes, window, levels, keep ratio ...) */
+#define WASABI_E_NOMEM (-2)   /* a library allocation failed or scratch too small  */
+#define WASABI_E_CUDA (-3)    /* a CUDA runtime call or a launch failed            */
+#define WASABI_E_RANGE (-4)   /* device-detected: depth index >= D, z outside range */
+#define WASABI_E_TIMEOUT (-5) /* device-detected: a bounded wait gave up           */
+
+/* Object point, 16 bytes (one float4 load), caller-owned.  x, y: integer pixel
+ * indices (may lie outside the hologram, |x|, |y| < 2^30); a: amplitude a_j of
+ * Eq. (1); d: index of the point's quantised depth in the LUT. */
+typedef struct {
+  int32_t x, y;
+  float a;
+  uint32_t d;
+} wasabi_point;
+
+typedef struct wasabi_lut wasabi_lut; /* opaque, library-owned, device-resident */
+
+typedef enum { WASABI_F32 = 0, WASABI_F16S = 1, WASABI_BF16S = 2 } wasabi_lut_dtype;
+typedef enum { WASABI_SHIFT_FLOOR = 0, WASABI_SHIFT_NEAREST = 1 } wasabi_shift_rule;
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* wasabi_last_error(void);
+
+/* Depth quantisation grid (Sec. 1, step 1 "discretized by Delta z"; Sec. 2):
+ * D bins of width dz = (zmax - zmin) / D over [zmin, zmax]; writes the D bin
+ * centres zmin + (d + 1/2) dz to depths_host.  E_INVALID if D < 1 or
+ * zmax <= zmin. */
+wasabi_status wasabi_depth_grid(double zmin, double zmax, int n_depths, double* depths_host);
+
+/* A0, point preparation (Sec. 1, step 1 depth discretisation): for i < n,
+ * out_dev[i] = {x[i], y[i], a[i], d} with d = min(D - 1, floor((z[i] - zmin) / dz)),
+ * dz = (zmax - zmin) / D, in FP64.  All arrays are device arrays of n
+ * elements.  A z outside [zmin, zmax] (or NaN) gets d = D and records
+ * WASABI_E_RANGE in the status word. */
+wasabi_status wasabi_quantize_points(const int32_t* x_dev, const int32_t* y_dev,
+                                     const double* z_dev, const float* a_dev, int64_t n,
+                                     double zmin, double zmax, int n_depths,
+                                     wasabi_point* out_dev, void* stream);
+
+/* A1-A3, the look-up table (Sec. 1, step 1): for each depth z_d
+ * (depths_host[0..n_depths)), the PSF u_z = exp(i 2 pi r / lambda) on the
+ * W x W window centred at pixel (W/2, W/2) with r = sqrt(n pitch^2 + z^2),
+ * n = du^2 + dv^2, restricted to the disk n < R(z)^2; its L-level Haar
+ * transform; and the N_r strongest coefficients by re^2 + im^2 (FP64), equal
+ * strengths going to the lower Mallat index row * W + col.
+ * N_r = min(nnz, ceil(keep_ratio * pi * R^2 - 1e-9)) for keep_ratio < 1, and
+ * every nonzero coefficient for keep_ratio >= 1 (Sec. 1, step 1:
+ * N_r = pi (W_j/2)^2 gamma with W_j the PSF diameter 2R).
+ * Phase arithmetic (so CPU and GPU select identical sets): f = t - floor(t),
+ * t = r / lambda, in FP64; cos/sin of 2 pi (float) f by quadrant reduction and
+ * Taylor polynomials in FP32 with fused multiply-adds.
+ * Requires 1 <= levels <= 5 (2 <= levels for the inverse), window a multiple
+ * of 2^(levels+1) with window / 2^levels <= 512, 2 R(z_d) + 1 <= window for
+ * every depth, s = lambda / (2 pitch) < 1, keep_ratio > 0, 1 <= n_depths <= 4096.
+ * dtype selects how superposition reads the values: FP32, or FP16 / BF16 with
+ * one FP32 scale per 32 consecutive entries (scale = max |re|, |im| of the
+ * block; stored value = value / scale, rounded to nearest).
+ * Allocates device memory (stream-ordered) and enqueues the build on stream;
+ * *out is usable by later work on the same stream at once.
+ * E_INVALID on bad arguments, E_NOMEM, E_CUDA. */
+wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths_host,
+                               int n_depths, int window, int levels, double keep_ratio,
+                               int dtype, void* stream, wasabi_lut** out);
+
+/* Releases a LUT (stream-ordered on the stream it was built on). */
+wasabi_status wasabi_lut_destroy(wasabi_lut* lut);
+
+/* Kept-coefficient counts N_r per depth into nr_host[0..n_depths).
+ * Synchronises with the LUT's build stream. */
+wasabi_status wasabi_lut_counts(const wasabi_lut* lut, int64_t* nr_host);
+
+/* Depth `depth`'s kept coefficients as Mallat linear indices (row * W + col of
+ * the W x W window transform), sorted ascending, into idx_host; *n_inout is
+ * the capacity on entry and the count on return (E_NOMEM, with the count, if
+ * too small).  Synchronising. */
+wasabi_status wasabi_lut_selection(const wasabi_lut* lut, int depth, int32_t* idx_host,
+                                   int64_t* n_inout);
+
+/* Depth `depth`'s LUT entries in storage order (window tiles row-major, then
+ * slot order): Mallat index and the value superposition uses (decoded to
+ * FP32 for F16S / BF16S) as interleaved (re, im).  Synchronising. */
+wasabi_status wasabi_lut_entries(const wasabi_lut* lut, int depth, int32_t* idx_host,
+                                 float* val_host, int64_t* n_inout);
+
+/* Scratch bytes wasabi_superpose needs for n points on a holo_w x holo_h
+ * hologram with this LUT. */
+wasabi_status wasabi_scratch_bytes(const wasabi_lut* lut, int64_t n, int holo_w, int holo_h,
+                                   size_t* bytes_out);
+
+/* A4 + A5, superposition in the wavelet domain (Eq. (2)):
+ *   psi = sum_j a_j sum_k c_{d_j,k} placed by the shift rule,
+ * written to wbuf_dev (tile-major, holo_w * holo_h complex64, fully
+ * overwritten: no prior zeroing needed).  points_dev: n wasabi_point;
+ * scratch_dev: at least wasabi_scratch_bytes() bytes, 256-byte aligned.
+ * holo_w, holo_h: multiples of 2^L (the LUT's levels), >= 2^L.
+ * A point with d >= D records WASABI_E_RANGE and contributes nothing. */
+wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n,
+                               int holo_w, int holo_h, int rule, void* wbuf_dev,
+                               void* scratch_dev, size_t scratch_bytes, void* stream);
+
+/* A6 + A7, inverse transformation (Sec. 1, step 3; Sec. 2 binary hologram):
+ * the L-level inverse Haar of the tile-major wbuf_dev gives the field u.
+ * u_dev (may be NULL): holo_w x holo_h complex64, row-major.
+ * bits_dev (may be NULL): the binary hologram bit = (Re u > 0) for a unit
+ * plane reference wave, row-major, 8 pixels per byte, least significant bit =
+ * lowest x; holo_w must be a multiple of 8.  At least one output non-NULL.
+ * 2 <= levels <= 5. */
+wasabi_status wasabi_inverse_haar(const void* wbuf_dev, int holo_w, int holo_h, int levels,
+                                  void* u_dev, uint8_t* bits_dev, void* stream);
+
+/* Eq. (1), the direct sum, on the GPU:
+ *   u(x_h, y_h) = sum_j a_j exp(i 2 pi r_hj / lambda) [aperture],
+ * r_hj = sqrt(((x_h - x_j)^2 + (y_h - y_j)^2) pitch^2 + z_{d_j}^2), with the
+ * point's quantised depth z_{d_j} = depths_host[d_j]; aperture = 1 restricts
+ * each term to the PSF disk n < R(z)^2 (the second form of Eq. (1)), 0 sums
+ * every pixel.  u_dev: holo_w x holo_h complex64, row-major, overwritten.
+ * FP64 is used for the phase reduction r / lambda mod 1, FP32 elsewhere.
+ * scratch_dev: at least cgh_direct_scratch_bytes() bytes. */
+wasabi_status cgh_direct_scratch_bytes(int64_t n, int holo_w, int holo_h, size_t* bytes_out);
+wasabi_status cgh_direct(double lambda, double pitch, const double* depths_host, int n_depths,
+                         const wasabi_point* points_dev, int64_t n, int holo_w, int holo_h,
+                         int aperture, void* u_dev, void* scratch_dev, size_t scratch_bytes,
+                         void* stream);
+
+/* Synchronises `stream`, then returns and clears the current device's status
+ * word: WASABI_OK, WASABI_E_RANGE or WASABI_E_TIMEOUT (E_CUDA if the stream
+ * itself failed). */
+wasabi_status wasabi_sync_status(void* stream);
+
+/* Test exports.  Forward L-level Haar of a row-major complex64 image into the
+ * tile-major layout (the inverse of wasabi_inverse_haar's complex output),
+ * and the permutation of a tile-major buffer into the whole-image Mallat
+ * layout (row-major complex64, holo_w x holo_h). */
+wasabi_status wasabi_haar_forward(const void* u_dev, int holo_w, int holo_h, int levels,
+                                  void* wbuf_dev, void* stream);
+wasabi_status wasabi_wbuf_to_mallat(const void* wbuf_dev, int holo_w, int holo_h, int levels,
+                                    void* mallat_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WASABI_H */

@@ -1,0 +1,79 @@
+"""ctypes declarations of libwasabi's C ABI (include/wasabi.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Loading fails loudly when the library has not been built; there is
+no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+OK, E_INVALID, E_NOMEM, E_CUDA, E_RANGE, E_TIMEOUT = 0, -1, -2, -3, -4, -5
+F32, F16S, BF16S = 0, 1, 2
+SHIFT_FLOOR, SHIFT_NEAREST = 0, 1
+
+_NAMES = {E_INVALID: "WASABI_E_INVALID", E_NOMEM: "WASABI_E_NOMEM", E_CUDA: "WASABI_E_CUDA",
+          E_RANGE: "WASABI_E_RANGE", E_TIMEOUT: "WASABI_E_TIMEOUT"}
+
+# (name, restype, argtypes) for every exported entry point.
+_VP, _I32P, _I64P, _F64P, _F32P, _U8P = (C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                         C.POINTER(C.c_double), C.POINTER(C.c_float),
+                                         C.POINTER(C.c_uint8))
+_i, _i64, _d, _sz = C.c_int, C.c_int64, C.c_double, C.c_size_t
+SIGNATURES = [
+    ("wasabi_last_error", C.c_char_p, []),
+    ("wasabi_depth_grid", _i, [_d, _d, _i, _F64P]),
+    ("wasabi_quantize_points", _i, [_VP, _VP, _VP, _VP, _i64, _d, _d, _i, _VP, _VP]),
+    ("wasabi_build_lut", _i, [_d, _d, _F64P, _i, _i, _i, _d, _i, _VP, C.POINTER(_VP)]),
+    ("wasabi_lut_destroy", _i, [_VP]),
+    ("wasabi_lut_counts", _i, [_VP, _I64P]),
+    ("wasabi_lut_selection", _i, [_VP, _i, _I32P, _I64P]),
+    ("wasabi_lut_entries", _i, [_VP, _i, _I32P, _F32P, _I64P]),
+    ("wasabi_scratch_bytes", _i, [_VP, _i64, _i, _i, C.POINTER(_sz)]),
+    ("wasabi_superpose", _i, [_VP, _VP, _i64, _i, _i, _i, _VP, _VP, _sz, _VP]),
+    ("wasabi_inverse_haar", _i, [_VP, _i, _i, _i, _VP, _VP, _VP]),
+    ("cgh_direct_scratch_bytes", _i, [_i64, _i, _i, C.POINTER(_sz)]),
+    ("cgh_direct", _i, [_d, _d, _F64P, _i, _VP, _i64, _i, _i, _i, _VP, _VP, _sz, _VP]),
+    ("wasabi_sync_status", _i, [_VP]),
+    ("wasabi_haar_forward", _i, [_VP, _i, _i, _i, _VP, _VP]),
+    ("wasabi_wbuf_to_mallat", _i, [_VP, _i, _i, _i, _VP, _VP]),
+]
+
+_lib = None
+
+
+class WasabiError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libwasabi.so; raise if it is missing (no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"libwasabi.so is not built ({_build.LIB}); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        _build.build()
+    L = C.CDLL(_build.LIB)
+    for name, res, args in SIGNATURES:
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def check(code: int) -> None:
+    if code != OK:
+        raise WasabiError(code, load().wasabi_last_error().decode(errors="replace"))

@@ -1,0 +1,207 @@
+"""Tensor-level wrappers of the libwasabi entry points (marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import check
+
+_DTYPES = {"f32": _abi.F32, "f16s": _abi.F16S, "bf16s": _abi.BF16S}
+
+
+def _lib():
+    return _abi.load()
+
+
+def _stream(stream=None) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> C.c_void_p | None:
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def depth_grid(zmin: float, zmax: float, n_depths: int) -> np.ndarray:
+    out = np.empty(n_depths, np.float64)
+    check(_lib().wasabi_depth_grid(zmin, zmax, n_depths,
+                                   out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+class Lut:
+    """A device-resident WASABI look-up table (library-owned)."""
+
+    def __init__(self, handle: C.c_void_p, lam, pitch, depths, window, levels, keep_ratio,
+                 dtype, stream):
+        self._h = handle
+        self.lam, self.pitch = lam, pitch
+        self.depths = np.asarray(depths, np.float64)
+        self.window, self.levels, self.keep_ratio, self.dtype = window, levels, keep_ratio, dtype
+        self._stream = stream
+
+    @property
+    def handle(self) -> C.c_void_p:
+        if self._h is None:
+            raise ValueError("LUT already destroyed")
+        return self._h
+
+    @property
+    def n_depths(self) -> int:
+        return int(self.depths.size)
+
+    def counts(self) -> np.ndarray:
+        out = np.empty(self.n_depths, np.int64)
+        check(_lib().wasabi_lut_counts(self.handle, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return out
+
+    def selection(self, depth: int) -> np.ndarray:
+        n = C.c_int64(self.window * self.window)
+        out = np.empty(n.value, np.int32)
+        check(_lib().wasabi_lut_selection(self.handle, depth,
+                                          out.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(n)))
+        return out[:n.value].copy()
+
+    def entries(self, depth: int) -> tuple[np.ndarray, np.ndarray]:
+        n = C.c_int64(self.window * self.window)
+        idx = np.empty(n.value, np.int32)
+        val = np.empty(n.value, np.complex64)
+        check(_lib().wasabi_lut_entries(self.handle, depth,
+                                        idx.ctypes.data_as(C.POINTER(C.c_int32)),
+                                        val.ctypes.data_as(C.POINTER(C.c_float)), C.byref(n)))
+        return idx[:n.value].copy(), val[:n.value].copy()
+
+    def close(self) -> None:
+        if self._h is not None:
+            _lib().wasabi_lut_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_lut(lam: float, pitch: float, depths, window: int, levels: int, keep_ratio: float,
+              dtype: str = "f32", stream=None) -> Lut:
+    d = np.ascontiguousarray(depths, np.float64)
+    h = C.c_void_p()
+    check(_lib().wasabi_build_lut(lam, pitch, d.ctypes.data_as(C.POINTER(C.c_double)), d.size,
+                                  window, levels, keep_ratio, _DTYPES[dtype], _stream(stream),
+                                  C.byref(h)))
+    return Lut(h, lam, pitch, d, window, levels, keep_ratio, dtype, stream)
+
+
+def pack_points(x, y, a, d, device="cuda") -> torch.Tensor:
+    """Lay out (x, y, a, d) as the ABI's 16-byte point records, shape (N, 4) int32."""
+    x = np.ascontiguousarray(x, np.int32)
+    rec = np.empty((x.size, 4), np.int32)
+    rec[:, 0] = x
+    rec[:, 1] = np.ascontiguousarray(y, np.int32)
+    rec[:, 2] = np.ascontiguousarray(a, np.float32).view(np.int32)
+    rec[:, 3] = np.ascontiguousarray(d, np.uint32).view(np.int32)
+    return torch.from_numpy(rec).to(device)
+
+
+def quantize_points(x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, a: torch.Tensor,
+                    zmin: float, zmax: float, n_depths: int, out: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    n = x.numel()
+    if out is None:
+        out = torch.empty((n, 4), dtype=torch.int32, device=x.device)
+    check(_lib().wasabi_quantize_points(_ptr(x), _ptr(y), _ptr(z), _ptr(a), n, zmin, zmax,
+                                        n_depths, _ptr(out), _stream(stream)))
+    return out
+
+
+def scratch_bytes(lut: Lut, n: int, w: int, h: int) -> int:
+    out = C.c_size_t()
+    check(_lib().wasabi_scratch_bytes(lut.handle, n, w, h, C.byref(out)))
+    return int(out.value)
+
+
+def superpose(lut: Lut, points: torch.Tensor, w: int, h: int, rule: int = 0,
+              wbuf: torch.Tensor | None = None, scratch: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+    """Eq. (2): the tile-major wavelet buffer (h*w complex64)."""
+    n = points.shape[0]
+    dev = points.device
+    if wbuf is None:
+        wbuf = torch.empty(h * w, dtype=torch.complex64, device=dev)
+    need = scratch_bytes(lut, n, w, h)
+    if scratch is None:
+        scratch = torch.empty(need, dtype=torch.uint8, device=dev)
+    check(_lib().wasabi_superpose(lut.handle, _ptr(points) if n else C.c_void_p(None), n, w, h,
+                                  rule, _ptr(wbuf), _ptr(scratch), scratch.numel(),
+                                  _stream(stream)))
+    return wbuf
+
+
+def inverse_haar(wbuf: torch.Tensor, w: int, h: int, levels: int, u: torch.Tensor | None = None,
+                 bits: torch.Tensor | None = None, want: str = "complex", stream=None):
+    dev = wbuf.device
+    if want in ("complex", "both") and u is None:
+        u = torch.empty((h, w), dtype=torch.complex64, device=dev)
+    if want in ("bits", "both") and bits is None:
+        bits = torch.empty((h * w + 7) // 8, dtype=torch.uint8, device=dev)
+    check(_lib().wasabi_inverse_haar(_ptr(wbuf), w, h, levels, _ptr(u), _ptr(bits), _stream(stream)))
+    if want == "complex":
+        return u
+    if want == "bits":
+        return bits
+    return u, bits
+
+
+def hologram(lut: Lut, points: torch.Tensor, w: int, h: int, want: str = "complex", rule: int = 0,
+             stream=None):
+    wbuf = superpose(lut, points, w, h, rule, stream=stream)
+    return inverse_haar(wbuf, w, h, lut.levels, want=want, stream=stream)
+
+
+def cgh_direct_scratch_bytes(n: int, w: int, h: int) -> int:
+    out = C.c_size_t()
+    check(_lib().cgh_direct_scratch_bytes(n, w, h, C.byref(out)))
+    return int(out.value)
+
+
+def cgh_direct(lam: float, pitch: float, depths, points: torch.Tensor, w: int, h: int,
+               aperture: bool = True, u: torch.Tensor | None = None,
+               scratch: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Eq. (1) on the GPU (h x w complex64)."""
+    d = np.ascontiguousarray(depths, np.float64)
+    n = points.shape[0]
+    dev = points.device
+    if u is None:
+        u = torch.empty((h, w), dtype=torch.complex64, device=dev)
+    if scratch is None:
+        scratch = torch.empty(cgh_direct_scratch_bytes(n, w, h), dtype=torch.uint8, device=dev)
+    check(_lib().cgh_direct(lam, pitch, d.ctypes.data_as(C.POINTER(C.c_double)), d.size,
+                            _ptr(points) if n else C.c_void_p(None), n, w, h, int(aperture),
+                            _ptr(u), _ptr(scratch), scratch.numel(), _stream(stream)))
+    return u
+
+
+def sync_status(stream=None) -> None:
+    """Wait for the stream and raise if a kernel recorded an error."""
+    check(_lib().wasabi_sync_status(_stream(stream)))
+
+
+def haar_forward(u: torch.Tensor, levels: int, stream=None) -> torch.Tensor:
+    h, w = u.shape
+    wbuf = torch.empty(h * w, dtype=torch.complex64, device=u.device)
+    check(_lib().wasabi_haar_forward(_ptr(u), w, h, levels, _ptr(wbuf), _stream(stream)))
+    return wbuf
+
+
+def wbuf_to_mallat(wbuf: torch.Tensor, w: int, h: int, levels: int, stream=None) -> torch.Tensor:
+    out = torch.empty((h, w), dtype=torch.complex64, device=wbuf.device)
+    check(_lib().wasabi_wbuf_to_mallat(_ptr(wbuf), w, h, levels, _ptr(out), _stream(stream)))
+    return out

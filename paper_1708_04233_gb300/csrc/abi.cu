@@ -1,0 +1,684 @@
+// libwasabi C ABI: argument checks, LUT ownership, scratch layout and the
+// launches of the kernels in the other translation units.  See
+// include/wasabi.h for the contract of each entry point.
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_fp16.h>
+
+#include "internal.cuh"
+
+namespace wsb {
+int superpose_max_cell_rows();
+int direct_max_cell_rows();
+}  // namespace wsb
+
+// ------------------------------------------------------------ device status
+// One word per device (a file-scope device variable: no allocation needed).
+__device__ int g_wasabi_status = 0;
+
+namespace wsb {
+namespace {
+
+thread_local std::string t_err;
+std::mutex g_mu;
+constexpr int kMaxDev = 64;
+int* g_status_ptr[kMaxDev] = {nullptr};
+int g_num_sms[kMaxDev] = {0};
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+int current_device() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return dev;
+}
+
+// Status word address and SM count of the current device (looked up once).
+bool device_info(int** status, int* sms) {
+  const int dev = current_device();
+  if (dev < 0 || dev >= kMaxDev) { set_error("device ordinal %d out of range", dev); return false; }
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_status_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_wasabi_status);
+    if (e != cudaSuccess) { set_error("cudaGetSymbolAddress(status): %s", cudaGetErrorString(e)); return false; }
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) { set_error("cudaDeviceGetAttribute: %s", cudaGetErrorString(e)); return false; }
+    g_status_ptr[dev] = static_cast<int*>(p);
+    g_num_sms[dev] = n;
+  }
+  if (status) *status = g_status_ptr[dev];
+  if (sms) *sms = g_num_sms[dev];
+  return true;
+}
+
+wasabi_status cuda_fail(const char* what, cudaError_t e) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return WASABI_E_CUDA;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Support radius in pixels: z tan(asin(lambda / 2p)) / p.
+double support_radius(double lambda, double pitch, double z) {
+  const double s = lambda / (2.0 * pitch);
+  const double t = s / std::sqrt(1.0 - s * s);
+  return (z * t) / pitch;
+}
+
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v && *v ? std::atoi(v) : dflt;
+}
+
+}  // namespace
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+}
+
+int* device_status_ptr() {
+  int* p = nullptr;
+  device_info(&p, nullptr);
+  return p;
+}
+
+}  // namespace wsb
+
+using namespace wsb;
+
+// ---------------------------------------------------------------- LUT object
+struct wasabi_lut {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double lambda = 0, pitch = 0, gamma = 0;
+  int D = 0, W = 0, L = 0, nwt = 0, dtype = 0;
+  int reach = 0;  // pixels: footprint half-extent bound (max floor(R) + 2^(L+1))
+  std::vector<double> z, R;
+  std::vector<DepthMeta> meta;
+  long long total_cap = 0;
+  void* block = nullptr;  // one device allocation for all arrays below
+  uint32_t* pos = nullptr;
+  float2* val = nullptr;
+  uint32_t* val16 = nullptr;
+  float* scale = nullptr;
+  int32_t* tile_off = nullptr;
+  DepthMeta* meta_dev = nullptr;
+  long long* nr_dev = nullptr;
+
+  LutView view() const {
+    LutView v;
+    v.D = D; v.W = W; v.L = L; v.nwt = nwt; v.dtype = dtype;
+    v.pos = pos; v.val = val; v.val16 = val16; v.scale = scale;
+    v.tile_off = tile_off; v.meta = meta_dev;
+    return v;
+  }
+};
+
+namespace {
+
+// Carves consecutive 256-byte-aligned regions out of one block.
+struct Carver {
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename T>
+  T* take(size_t count) {
+    off = align_up(off, 256);
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// Super-tile side and block size for a hologram (the autotuner's default).
+void superpose_config(const wasabi_lut* lut, int w, int h, int* cell, int* threads) {
+  int T = env_int("WASABI_SUPERPOSE_T", 128);
+  int nt = env_int("WASABI_SUPERPOSE_THREADS", 1024);
+  T = std::min(T, 16 << lut->L);  // a window-tile row range must fit one warp
+  T = std::max(T, 1 << lut->L);
+  T = (T >> lut->L) << lut->L;
+  (void)w; (void)h;
+  *cell = T;
+  *threads = nt;
+}
+
+struct BinLayout {
+  int cell, ncx, ncy;
+  size_t bytes;
+  int *cnt, *off, *cursor, *counter;
+  wasabi_point* sorted;
+};
+
+BinLayout bin_layout(int64_t n, int w, int h, int cell, void* base) {
+  BinLayout b;
+  b.cell = cell;
+  b.ncx = (w + cell - 1) / cell;
+  b.ncy = (h + cell - 1) / cell;
+  const size_t ncells = (size_t)b.ncx * b.ncy;
+  Carver c;
+  c.base = static_cast<char*>(base);
+  b.cnt = c.take<int>(ncells + 1);
+  b.off = c.take<int>(ncells + 1);
+  b.cursor = c.take<int>(ncells);
+  b.counter = c.take<int>(64);
+  b.sorted = c.take<wasabi_point>((size_t)std::max<int64_t>(n, 1));
+  b.bytes = align_up(c.off, 256);
+  return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* wasabi_last_error(void) { return t_err.c_str(); }
+
+wasabi_status wasabi_depth_grid(double zmin, double zmax, int n_depths, double* depths_host) {
+  if (n_depths < 1 || !(zmax > zmin) || !depths_host) {
+    set_error("depth_grid: need n_depths >= 1, zmax > zmin and an output array");
+    return WASABI_E_INVALID;
+  }
+  const double dz = (zmax - zmin) / (double)n_depths;
+  for (int d = 0; d < n_depths; ++d) depths_host[d] = zmin + ((double)d + 0.5) * dz;
+  return WASABI_OK;
+}
+
+wasabi_status wasabi_quantize_points(const int32_t* x_dev, const int32_t* y_dev, const double* z_dev,
+                                     const float* a_dev, int64_t n, double zmin, double zmax,
+                                     int n_depths, wasabi_point* out_dev, void* stream) {
+  if (n < 0 || n_depths < 1 || !(zmax > zmin) || (n > 0 && (!x_dev || !y_dev || !z_dev || !a_dev || !out_dev))) {
+    set_error("quantize_points: bad arguments");
+    return WASABI_E_INVALID;
+  }
+  int* status;
+  if (!device_info(&status, nullptr)) return WASABI_E_CUDA;
+  const double dz = (zmax - zmin) / (double)n_depths;
+  const cudaError_t e = launch_quantize(x_dev, y_dev, z_dev, a_dev, n, zmin, zmax, dz, n_depths,
+                                        out_dev, status, (cudaStream_t)stream);
+  return e == cudaSuccess ? WASABI_OK : cuda_fail("quantize launch", e);
+}
+
+wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths_host, int n_depths,
+                               int window, int levels, double keep_ratio, int dtype, void* stream,
+                               wasabi_lut** out) {
+  if (!out) { set_error("build_lut: out is NULL"); return WASABI_E_INVALID; }
+  *out = nullptr;
+  if (!(lambda > 0) || !(pitch > 0) || !(lambda / (2.0 * pitch) < 1.0)) {
+    set_error("build_lut: need lambda > 0, pitch > 0 and lambda / (2 pitch) < 1");
+    return WASABI_E_INVALID;
+  }
+  if (n_depths < 1 || n_depths > kMaxDepths || !depths_host) {
+    set_error("build_lut: n_depths must be in [1, %d]", kMaxDepths);
+    return WASABI_E_INVALID;
+  }
+  if (levels < 1 || levels > kMaxLevels) {
+    set_error("build_lut: levels must be in [1, %d]", kMaxLevels);
+    return WASABI_E_INVALID;
+  }
+  if (window <= 0 || window % (2 << levels) != 0 || (window >> levels) > kMaxWindowTiles) {
+    set_error("build_lut: window must be a positive multiple of 2^(levels+1) with window/2^levels <= %d",
+              kMaxWindowTiles);
+    return WASABI_E_INVALID;
+  }
+  if (!(keep_ratio > 0)) { set_error("build_lut: keep_ratio must be > 0"); return WASABI_E_INVALID; }
+  if (dtype != WASABI_F32 && dtype != WASABI_F16S && dtype != WASABI_BF16S) {
+    set_error("build_lut: unknown dtype %d", dtype);
+    return WASABI_E_INVALID;
+  }
+  wasabi_lut* lut = new wasabi_lut;
+  lut->stream = (cudaStream_t)stream;
+  lut->lambda = lambda; lut->pitch = pitch; lut->gamma = keep_ratio;
+  lut->D = n_depths; lut->W = window; lut->L = levels; lut->nwt = window >> levels; lut->dtype = dtype;
+  const int TSL = 1 << (2 * levels);
+  std::vector<double> R2(n_depths);
+  std::vector<long long> target(n_depths);
+  lut->z.assign(depths_host, depths_host + n_depths);
+  lut->R.resize(n_depths);
+  lut->meta.resize(n_depths);
+  int max_nb = 1, max_fr = 0;
+  long long max_cap = 0, base = 0;
+  for (int d = 0; d < n_depths; ++d) {
+    const double z = depths_host[d];
+    if (!(z > 0)) { delete lut; set_error("build_lut: depth %d must be > 0", d); return WASABI_E_INVALID; }
+    const double R = support_radius(lambda, pitch, z);
+    if (2.0 * R + 1.0 > (double)window) {
+      delete lut;
+      set_error("build_lut: PSF of depth %d has radius %.2f px, needs a window >= %d", d, R,
+                (int)std::ceil(2.0 * R + 1.0));
+      return WASABI_E_INVALID;
+    }
+    lut->R[d] = R;
+    R2[d] = R * R;
+    const int fr = (int)std::floor(R);
+    max_fr = std::max(max_fr, fr);
+    DepthMeta m;
+    m.tlo = std::max(0, (window / 2 - fr) >> levels);
+    m.thi = std::min(lut->nwt - 1, (window / 2 + fr) >> levels);
+    const int nb = m.thi - m.tlo + 1;
+    max_nb = std::max(max_nb, nb);
+    const long long box = (long long)nb * nb * TSL;
+    long long cap = box;
+    if (keep_ratio < 1.0) {
+      target[d] = (long long)std::ceil(keep_ratio * (kPi * (R * R)) - 1e-9);
+      cap = std::min(cap, std::max(0ll, target[d]));
+    } else {
+      target[d] = LLONG_MAX;
+    }
+    cap = (long long)align_up((size_t)std::max(cap, 1ll), 32);
+    m.base = (int)base;
+    m.cap = (int)cap;
+    base += cap;
+    max_cap = std::max(max_cap, cap);
+    lut->meta[d] = m;
+  }
+  if (base > INT_MAX) { delete lut; set_error("build_lut: table too large"); return WASABI_E_INVALID; }
+  lut->total_cap = base;
+  lut->reach = max_fr + (2 << levels);
+  const int ntpd = lut->nwt * lut->nwt + 1;
+  const cudaStream_t s = (cudaStream_t)stream;
+  int* status;
+  int sms;
+  if (!device_info(&status, &sms)) { delete lut; return WASABI_E_CUDA; }
+  lut->device = current_device();
+
+  // Persistent arrays.
+  Carver c;
+  c.take<uint32_t>((size_t)base);                                    // pos
+  c.take<float2>((size_t)base);                                      // val
+  if (dtype != WASABI_F32) { c.take<uint32_t>((size_t)base); c.take<float>((size_t)base / 32 + 1); }
+  c.take<int32_t>((size_t)n_depths * ntpd);                          // tile_off
+  c.take<DepthMeta>((size_t)n_depths);
+  c.take<long long>((size_t)n_depths);                               // nr
+  const size_t persist_bytes = align_up(c.off, 256);
+  cudaError_t e = cudaMallocAsync(&lut->block, persist_bytes, s);
+  if (e != cudaSuccess) { delete lut; set_error("build_lut: cudaMallocAsync: %s", cudaGetErrorString(e)); return WASABI_E_NOMEM; }
+  c = Carver();
+  c.base = static_cast<char*>(lut->block);
+  lut->pos = c.take<uint32_t>((size_t)base);
+  lut->val = c.take<float2>((size_t)base);
+  if (dtype != WASABI_F32) {
+    lut->val16 = c.take<uint32_t>((size_t)base);
+    lut->scale = c.take<float>((size_t)base / 32 + 1);
+  }
+  lut->tile_off = c.take<int32_t>((size_t)n_depths * ntpd);
+  lut->meta_dev = c.take<DepthMeta>((size_t)n_depths);
+  lut->nr_dev = c.take<long long>((size_t)n_depths);
+
+  // Build scratch.
+  Carver sc;
+  sc.take<float2>((size_t)n_depths * window * window);
+  sc.take<unsigned long long>((size_t)n_depths);
+  sc.take<unsigned long long>((size_t)2 * n_depths);
+  sc.take<int>((size_t)n_depths * lut->nwt * lut->nwt);
+  sc.take<double>((size_t)n_depths);
+  sc.take<double>((size_t)n_depths);
+  sc.take<long long>((size_t)n_depths);
+  void* scratch = nullptr;
+  e = cudaMallocAsync(&scratch, align_up(sc.off, 256), s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(lut->block, s);
+    delete lut;
+    set_error("build_lut: scratch cudaMallocAsync: %s", cudaGetErrorString(e));
+    return WASABI_E_NOMEM;
+  }
+  sc = Carver();
+  sc.base = static_cast<char*>(scratch);
+  LutBuildArgs a;
+  a.D = n_depths; a.W = window; a.L = levels; a.nwt = lut->nwt; a.dtype = dtype;
+  a.max_nb = max_nb; a.max_cap = max_cap;
+  a.lambda = lambda; a.pitch = pitch;
+  a.coef = sc.take<float2>((size_t)n_depths * window * window);
+  a.nnz = sc.take<unsigned long long>((size_t)n_depths);
+  a.thr = sc.take<unsigned long long>((size_t)2 * n_depths);
+  a.tile_cnt = sc.take<int>((size_t)n_depths * lut->nwt * lut->nwt);
+  double* z_dev = sc.take<double>((size_t)n_depths);
+  double* R2_dev = sc.take<double>((size_t)n_depths);
+  long long* target_dev = sc.take<long long>((size_t)n_depths);
+  a.z_dev = z_dev; a.R2_dev = R2_dev; a.target_dev = target_dev;
+  a.nr_dev = lut->nr_dev; a.pos = lut->pos; a.val = lut->val; a.val16 = lut->val16; a.scale = lut->scale;
+  a.tile_off = lut->tile_off; a.meta = lut->meta_dev; a.status = status;
+
+  bool okc = true;
+  okc = okc && cudaMemcpyAsync(z_dev, depths_host, sizeof(double) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  okc = okc && cudaMemcpyAsync(R2_dev, R2.data(), sizeof(double) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  okc = okc && cudaMemcpyAsync(target_dev, target.data(), sizeof(long long) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  okc = okc && cudaMemcpyAsync(lut->meta_dev, lut->meta.data(), sizeof(DepthMeta) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  okc = okc && cudaMemsetAsync(a.nnz, 0, sizeof(unsigned long long) * n_depths, s) == cudaSuccess;
+  // The per-depth tables come from pageable host memory; make their upload
+  // complete before the host vectors are released.
+  okc = okc && cudaStreamSynchronize(s) == cudaSuccess;
+  if (!okc) {
+    cudaFreeAsync(scratch, s);
+    cudaFreeAsync(lut->block, s);
+    delete lut;
+    return cuda_fail("build_lut: upload", cudaGetLastError());
+  }
+  e = launch_lut_build(a, s);
+  cudaFreeAsync(scratch, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(lut->block, s);
+    delete lut;
+    return cuda_fail("build_lut: launch", e);
+  }
+  *out = lut;
+  return WASABI_OK;
+}
+
+wasabi_status wasabi_lut_destroy(wasabi_lut* lut) {
+  if (!lut) return WASABI_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(lut->device);
+  cudaFreeAsync(lut->block, lut->stream);
+  cudaSetDevice(prev);
+  delete lut;
+  return WASABI_OK;
+}
+
+wasabi_status wasabi_lut_counts(const wasabi_lut* lut, int64_t* nr_host) {
+  if (!lut || !nr_host) { set_error("lut_counts: NULL argument"); return WASABI_E_INVALID; }
+  cudaError_t e = cudaStreamSynchronize(lut->stream);
+  if (e != cudaSuccess) return cuda_fail("lut_counts: sync", e);
+  std::vector<long long> nr(lut->D);
+  e = cudaMemcpy(nr.data(), lut->nr_dev, sizeof(long long) * lut->D, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail("lut_counts: copy", e);
+  for (int d = 0; d < lut->D; ++d) nr_host[d] = nr[d];
+  return WASABI_OK;
+}
+
+namespace {
+wasabi_status read_depth(const wasabi_lut* lut, int depth, std::vector<uint32_t>* pos,
+                         std::vector<float2>* val) {
+  if (!lut || depth < 0 || depth >= lut->D) { set_error("lut: bad depth"); return WASABI_E_INVALID; }
+  cudaError_t e = cudaStreamSynchronize(lut->stream);
+  if (e != cudaSuccess) return cuda_fail("lut: sync", e);
+  long long nr = 0;
+  e = cudaMemcpy(&nr, lut->nr_dev + depth, sizeof nr, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail("lut: copy", e);
+  const size_t b = (size_t)lut->meta[depth].base;
+  pos->resize((size_t)nr);
+  val->resize((size_t)nr);
+  if (nr == 0) return WASABI_OK;
+  e = cudaMemcpy(pos->data(), lut->pos + b, sizeof(uint32_t) * nr, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail("lut: copy", e);
+  if (lut->dtype == WASABI_F32) {
+    e = cudaMemcpy(val->data(), lut->val + b, sizeof(float2) * nr, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail("lut: copy", e);
+  } else {
+    std::vector<uint32_t> q((size_t)nr);
+    std::vector<float> sc((size_t)(nr + 31) / 32);
+    e = cudaMemcpy(q.data(), lut->val16 + b, sizeof(uint32_t) * nr, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(sc.data(), lut->scale + b / 32, sizeof(float) * sc.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail("lut: copy", e);
+    for (size_t i = 0; i < (size_t)nr; ++i) {
+      float re, im;
+      const uint16_t lo = (uint16_t)(q[i] & 0xffff), hi = (uint16_t)(q[i] >> 16);
+      if (lut->dtype == WASABI_BF16S) {
+        uint32_t a = (uint32_t)lo << 16, c = (uint32_t)hi << 16;
+        std::memcpy(&re, &a, 4);
+        std::memcpy(&im, &c, 4);
+      } else {
+        re = __half2float(__ushort_as_half(lo));
+        im = __half2float(__ushort_as_half(hi));
+      }
+      (*val)[i] = make_float2(re * sc[i / 32], im * sc[i / 32]);
+    }
+  }
+  return WASABI_OK;
+}
+
+int32_t pos_to_mallat(const wasabi_lut* lut, uint32_t p) {
+  const int tx = p & 511, ty = (p >> 9) & 511, lev = (p >> 18) & 7;
+  const int band = (p >> 21) & 3, ix = (p >> 23) & 15, iy = (int)(p >> 27);
+  return mallat_index(lut->W, lut->L, tx, ty, tile_slot(lut->L, lev, band, ix, iy));
+}
+}  // namespace
+
+wasabi_status wasabi_lut_selection(const wasabi_lut* lut, int depth, int32_t* idx_host, int64_t* n_inout) {
+  if (!n_inout) { set_error("lut_selection: NULL count"); return WASABI_E_INVALID; }
+  std::vector<uint32_t> pos;
+  std::vector<float2> val;
+  const wasabi_status st = read_depth(lut, depth, &pos, &val);
+  if (st != WASABI_OK) return st;
+  const int64_t cap = *n_inout;
+  *n_inout = (int64_t)pos.size();
+  if ((int64_t)pos.size() > cap || (!idx_host && !pos.empty())) { set_error("lut_selection: capacity too small"); return WASABI_E_NOMEM; }
+  std::vector<int32_t> idx(pos.size());
+  for (size_t i = 0; i < pos.size(); ++i) idx[i] = pos_to_mallat(lut, pos[i]);
+  std::sort(idx.begin(), idx.end());
+  std::copy(idx.begin(), idx.end(), idx_host);
+  return WASABI_OK;
+}
+
+wasabi_status wasabi_lut_entries(const wasabi_lut* lut, int depth, int32_t* idx_host, float* val_host,
+                                 int64_t* n_inout) {
+  if (!n_inout) { set_error("lut_entries: NULL count"); return WASABI_E_INVALID; }
+  std::vector<uint32_t> pos;
+  std::vector<float2> val;
+  const wasabi_status st = read_depth(lut, depth, &pos, &val);
+  if (st != WASABI_OK) return st;
+  const int64_t cap = *n_inout;
+  *n_inout = (int64_t)pos.size();
+  if ((int64_t)pos.size() > cap || ((!idx_host || !val_host) && !pos.empty())) { set_error("lut_entries: capacity too small"); return WASABI_E_NOMEM; }
+  for (size_t i = 0; i < pos.size(); ++i) {
+    idx_host[i] = pos_to_mallat(lut, pos[i]);
+    val_host[2 * i] = val[i].x;
+    val_host[2 * i + 1] = val[i].y;
+  }
+  return WASABI_OK;
+}
+
+wasabi_status wasabi_scratch_bytes(const wasabi_lut* lut, int64_t n, int holo_w, int holo_h, size_t* bytes_out) {
+  if (!lut || !bytes_out || n < 0 || holo_w <= 0 || holo_h <= 0) {
+    set_error("scratch_bytes: bad arguments");
+    return WASABI_E_INVALID;
+  }
+  // The smallest cell the configuration can pick bounds every layout.
+  const int cell = std::max(1 << lut->L, std::min(64, 16 << lut->L));
+  *bytes_out = bin_layout(n, holo_w, holo_h, cell, nullptr).bytes;
+  return WASABI_OK;
+}
+
+wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n, int holo_w,
+                               int holo_h, int rule, void* wbuf_dev, void* scratch_dev, size_t scratch_bytes,
+                               void* stream) {
+  if (!lut || n < 0 || (n > 0 && !points_dev) || !wbuf_dev || !scratch_dev) {
+    set_error("superpose: NULL argument");
+    return WASABI_E_INVALID;
+  }
+  const int ts = 1 << lut->L;
+  if (holo_w < ts || holo_h < ts || holo_w % ts || holo_h % ts || holo_w > (1 << 29) || holo_h > (1 << 29)) {
+    set_error("superpose: holo_w and holo_h must be multiples of 2^L = %d", ts);
+    return WASABI_E_INVALID;
+  }
+  if (rule != WASABI_SHIFT_FLOOR && rule != WASABI_SHIFT_NEAREST) { set_error("superpose: unknown rule"); return WASABI_E_INVALID; }
+  if (((uintptr_t)scratch_dev | (uintptr_t)wbuf_dev) & 255) { set_error("superpose: buffers must be 256-byte aligned"); return WASABI_E_INVALID; }
+  if (current_device() != lut->device) { set_error("superpose: LUT lives on another device"); return WASABI_E_INVALID; }
+  int* status;
+  int sms;
+  if (!device_info(&status, &sms)) return WASABI_E_CUDA;
+  int cell, threads;
+  superpose_config(lut, holo_w, holo_h, &cell, &threads);
+  BinLayout b = bin_layout(n, holo_w, holo_h, cell, scratch_dev);
+  size_t need = 0;
+  wasabi_scratch_bytes(lut, n, holo_w, holo_h, &need);
+  if (scratch_bytes < need || scratch_bytes < b.bytes) {
+    set_error("superpose: scratch too small (%zu < %zu bytes)", scratch_bytes, std::max(need, b.bytes));
+    return WASABI_E_NOMEM;
+  }
+  const int rows = (cell + 2 * lut->reach) / cell + 2;
+  if (rows > superpose_max_cell_rows()) { set_error("superpose: window too large for the super-tile"); return WASABI_E_INVALID; }
+  const cudaStream_t s = (cudaStream_t)stream;
+  BinArgs ba;
+  ba.pts = points_dev; ba.n = n; ba.D = lut->D; ba.w = holo_w; ba.h = holo_h; ba.cell = cell;
+  ba.ncx = b.ncx; ba.ncy = b.ncy; ba.reach = lut->reach;
+  ba.cnt = b.cnt; ba.off = b.off; ba.cursor = b.cursor; ba.sorted = b.sorted; ba.status = status;
+  cudaError_t e = launch_binning(ba, s);
+  if (e != cudaSuccess) return cuda_fail("superpose: binning", e);
+  e = cudaMemsetAsync(b.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail("superpose: memset", e);
+  SuperposeArgs sa;
+  sa.lut = lut->view();
+  sa.sorted = b.sorted; sa.cell_off = b.off; sa.ncx = b.ncx; sa.ncy = b.ncy; sa.cell = cell;
+  sa.w = holo_w; sa.h = holo_h; sa.ntx = holo_w >> lut->L; sa.nty = holo_h >> lut->L;
+  sa.rule = rule; sa.reach = lut->reach; sa.counter = b.counter;
+  sa.wbuf = static_cast<float2*>(wbuf_dev); sa.status = status; sa.threads = threads;
+  const long long nst = (long long)((sa.ntx + (cell >> lut->L) - 1) / (cell >> lut->L)) *
+                        ((sa.nty + (cell >> lut->L) - 1) / (cell >> lut->L));
+  const size_t smem = superpose_smem_bytes(cell, lut->D, threads);
+  const int per_sm = std::max(1, std::min(2048 / threads, (int)((227 * 1024) / (smem + 1024))));
+  sa.grid = (int)std::min<long long>(nst, (long long)sms * per_sm);
+  e = launch_superpose(sa, s);
+  return e == cudaSuccess ? WASABI_OK : cuda_fail("superpose: launch", e);
+}
+
+wasabi_status wasabi_inverse_haar(const void* wbuf_dev, int holo_w, int holo_h, int levels, void* u_dev,
+                                  uint8_t* bits_dev, void* stream) {
+  if (!wbuf_dev || (!u_dev && !bits_dev)) { set_error("inverse_haar: need the buffer and an output"); return WASABI_E_INVALID; }
+  if (levels < 2 || levels > kMaxLevels) { set_error("inverse_haar: levels must be in [2, %d]", kMaxLevels); return WASABI_E_INVALID; }
+  const int ts = 1 << levels;
+  if (holo_w < ts || holo_h < ts || holo_w % ts || holo_h % ts) {
+    set_error("inverse_haar: holo_w and holo_h must be multiples of 2^levels");
+    return WASABI_E_INVALID;
+  }
+  if (bits_dev && holo_w % 8) { set_error("inverse_haar: bits output needs holo_w % 8 == 0"); return WASABI_E_INVALID; }
+  if (((uintptr_t)wbuf_dev & 15) || ((uintptr_t)u_dev & 15) || ((uintptr_t)bits_dev & 3)) {
+    set_error("inverse_haar: misaligned buffer");
+    return WASABI_E_INVALID;
+  }
+  int* status;
+  int sms;
+  if (!device_info(&status, &sms)) return WASABI_E_CUDA;
+  const cudaError_t e = launch_inverse(static_cast<const float2*>(wbuf_dev), holo_w, holo_h, levels,
+                                       static_cast<float2*>(u_dev), bits_dev, status, sms, (cudaStream_t)stream);
+  return e == cudaSuccess ? WASABI_OK : cuda_fail("inverse_haar: launch", e);
+}
+
+namespace {
+int direct_cell(int w, int h, bool aperture) {
+  int cell = 64;
+  if (!aperture) {
+    const int maxdim = std::max(w, h);
+    while ((maxdim + cell - 1) / cell + 2 > direct_max_cell_rows()) cell *= 2;
+  }
+  return cell;
+}
+}  // namespace
+
+wasabi_status cgh_direct_scratch_bytes(int64_t n, int holo_w, int holo_h, size_t* bytes_out) {
+  if (!bytes_out || n < 0 || holo_w <= 0 || holo_h <= 0) { set_error("cgh_direct_scratch_bytes: bad arguments"); return WASABI_E_INVALID; }
+  const size_t b = bin_layout(n, holo_w, holo_h, 64, nullptr).bytes;
+  *bytes_out = b + align_up(sizeof(double) * kMaxDepths, 256) + align_up(sizeof(long long) * kMaxDepths, 256);
+  return WASABI_OK;
+}
+
+wasabi_status cgh_direct(double lambda, double pitch, const double* depths_host, int n_depths,
+                         const wasabi_point* points_dev, int64_t n, int holo_w, int holo_h, int aperture,
+                         void* u_dev, void* scratch_dev, size_t scratch_bytes, void* stream) {
+  if (!(lambda > 0) || !(pitch > 0) || !(lambda / (2.0 * pitch) < 1.0) || n_depths < 1 ||
+      n_depths > kMaxDepths || !depths_host || n < 0 || (n > 0 && !points_dev) || !u_dev || !scratch_dev ||
+      holo_w <= 0 || holo_h <= 0 || holo_w > (1 << 29) || holo_h > (1 << 29)) {
+    set_error("cgh_direct: bad arguments");
+    return WASABI_E_INVALID;
+  }
+  if (((uintptr_t)scratch_dev & 255) || ((uintptr_t)u_dev & 7)) { set_error("cgh_direct: misaligned buffer"); return WASABI_E_INVALID; }
+  size_t need = 0;
+  cgh_direct_scratch_bytes(n, holo_w, holo_h, &need);
+  if (scratch_bytes < need) { set_error("cgh_direct: scratch too small (%zu < %zu)", scratch_bytes, need); return WASABI_E_NOMEM; }
+  int* status;
+  int sms;
+  if (!device_info(&status, &sms)) return WASABI_E_CUDA;
+  const int cell = direct_cell(holo_w, holo_h, aperture != 0);
+  BinLayout b = bin_layout(n, holo_w, holo_h, cell, scratch_dev);
+  Carver c;
+  c.base = static_cast<char*>(scratch_dev);
+  c.off = b.bytes;
+  double* beta_dev = c.take<double>(kMaxDepths);
+  long long* nlim_dev = c.take<long long>(kMaxDepths);
+  std::vector<double> beta(n_depths);
+  std::vector<long long> nlim(n_depths);
+  double Rmax = 0;
+  for (int d = 0; d < n_depths; ++d) {
+    const double z = depths_host[d];
+    if (!(z > 0)) { set_error("cgh_direct: depth %d must be > 0", d); return WASABI_E_INVALID; }
+    const double zl = z / lambda;
+    beta[d] = zl * zl;
+    const double R = support_radius(lambda, pitch, z);
+    Rmax = std::max(Rmax, R);
+    nlim[d] = aperture ? (long long)std::ceil(R * R) : LLONG_MAX;
+  }
+  const double pl = pitch / lambda;
+  const cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(beta_dev, beta.data(), sizeof(double) * n_depths, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(nlim_dev, nlim.data(), sizeof(long long) * n_depths, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail("cgh_direct: upload", e);
+  const int reach = aperture ? (int)std::floor(Rmax) + 1 : (INT_MAX / 4);
+  BinArgs ba;
+  ba.pts = points_dev; ba.n = n; ba.D = n_depths; ba.w = holo_w; ba.h = holo_h; ba.cell = cell;
+  ba.ncx = b.ncx; ba.ncy = b.ncy; ba.reach = reach;
+  ba.cnt = b.cnt; ba.off = b.off; ba.cursor = b.cursor; ba.sorted = b.sorted; ba.status = status;
+  e = launch_binning(ba, s);
+  if (e != cudaSuccess) return cuda_fail("cgh_direct: binning", e);
+  e = cudaMemsetAsync(b.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail("cgh_direct: memset", e);
+  DirectArgs da;
+  da.lambda = lambda; da.pitch = pitch; da.sorted = b.sorted; da.cell_off = b.off;
+  da.ncx = b.ncx; da.ncy = b.ncy; da.cell = cell; da.w = holo_w; da.h = holo_h; da.D = n_depths;
+  da.beta_dev = beta_dev; da.nlim_dev = nlim_dev; da.alpha = pl * pl; da.reach = reach;
+  da.counter = b.counter; da.u = static_cast<float2*>(u_dev); da.status = status;
+  const long long ntiles = (long long)((holo_w + 31) / 32) * ((holo_h + 31) / 32);
+  da.grid = (int)std::min<long long>(ntiles, (long long)sms * 8);
+  e = launch_direct(da, s);
+  return e == cudaSuccess ? WASABI_OK : cuda_fail("cgh_direct: launch", e);
+}
+
+wasabi_status wasabi_sync_status(void* stream) {
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail("sync_status: stream", e);
+  int v = 0;
+  e = cudaMemcpyFromSymbol(&v, g_wasabi_status, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail("sync_status: read", e);
+  const int zero = 0;
+  e = cudaMemcpyToSymbol(g_wasabi_status, &zero, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail("sync_status: clear", e);
+  if (v != 0) set_error("device reported status %d", v);
+  return v;
+}
+
+wasabi_status wasabi_haar_forward(const void* u_dev, int holo_w, int holo_h, int levels, void* wbuf_dev,
+                                  void* stream) {
+  if (!u_dev || !wbuf_dev || levels < 1 || levels > kMaxLevels) { set_error("haar_forward: bad arguments"); return WASABI_E_INVALID; }
+  const int ts = 1 << levels;
+  if (holo_w < ts || holo_h < ts || holo_w % ts || holo_h % ts) { set_error("haar_forward: sizes must be multiples of 2^levels"); return WASABI_E_INVALID; }
+  const cudaError_t e = launch_haar_forward(static_cast<const float2*>(u_dev), holo_w, holo_h, levels,
+                                            static_cast<float2*>(wbuf_dev), (cudaStream_t)stream);
+  return e == cudaSuccess ? WASABI_OK : cuda_fail("haar_forward: launch", e);
+}
+
+wasabi_status wasabi_wbuf_to_mallat(const void* wbuf_dev, int holo_w, int holo_h, int levels, void* mallat_dev,
+                                    void* stream) {
+  if (!wbuf_dev || !mallat_dev || levels < 1 || levels > kMaxLevels) { set_error("wbuf_to_mallat: bad arguments"); return WASABI_E_INVALID; }
+  const int ts = 1 << levels;
+  if (holo_w < ts || holo_h < ts || holo_w % ts || holo_h % ts) { set_error("wbuf_to_mallat: sizes must be multiples of 2^levels"); return WASABI_E_INVALID; }
+  const cudaError_t e = launch_wbuf_to_mallat(static_cast<const float2*>(wbuf_dev), holo_w, holo_h, levels,
+                                              static_cast<float2*>(mallat_dev), (cudaStream_t)stream);
+  return e == cudaSuccess ? WASABI_OK : cuda_fail("wbuf_to_mallat: launch", e);
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+// Eq. (1) on the GPU: u(x_h, y_h) = sum_j a_j exp(i 2 pi r_hj / lambda) over
+// the points whose PSF disk covers the pixel (or over all points when the
+// aperture is off).
+//
+// A persistent CTA owns 32 x 32 pixel tiles; for each tile it scans the binned
+// points of the cell rows within reach, keeps those whose disk meets the tile
+// (nearest-point distance test), and every thread accumulates its 4 pixels
+// over the kept points in FP32.
+//
+// Phase: r / lambda = sqrt(q) with q = n (p / lambda)^2 + (z / lambda)^2 and
+// n = dx^2 + dy^2.  q is formed in FP64; an FP32 estimate s0 of sqrt(q) is
+// refined by one Newton step whose residual q - s0^2 is taken in FP64 (the
+// reduction r / lambda mod 1 is thus carried out at FP64 accuracy, ~1e-11
+// cycles), and the fractional cycle feeds an FP32 sincospi.
+#include "internal.cuh"
+
+namespace wsb {
+namespace {
+
+constexpr int kTile = 32;
+constexpr int kNT = 256;
+constexpr int kCap = kNT;
+constexpr int kMaxRows = 128;
+
+__device__ __forceinline__ int floor_div(int a, int b) {
+  const int q = a / b;
+  return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+__global__ void __launch_bounds__(kNT) direct_kernel(DirectArgs a) {
+  __shared__ int4 list[kCap];
+  __shared__ double lbeta[kCap];
+  __shared__ long long lnlim[kCap];
+  __shared__ int s_tile, s_n, s_nrows, s_total;
+  __shared__ int s_rowstart[kMaxRows], s_rowpre[kMaxRows + 1];
+  const int tid = threadIdx.x;
+  const int ntx = (a.w + kTile - 1) / kTile, nty = (a.h + kTile - 1) / kTile;
+  const int ntiles = ntx * nty;
+  const int col = tid & 31, row0 = tid >> 5;  // pixels (col, row0 + 8 q), q < 4
+
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const int X0 = (t % ntx) * kTile, Y0 = (t / ntx) * kTile;
+    const int X1 = min(X0 + kTile, a.w), Y1 = min(Y0 + kTile, a.h);
+
+    const int cx0 = max(0, floor_div(X0 - a.reach, a.cell));
+    const int cx1 = min(a.ncx - 1, floor_div(X1 - 1 + a.reach, a.cell));
+    const int cy0 = max(0, floor_div(Y0 - a.reach, a.cell));
+    const int cy1 = min(a.ncy - 1, floor_div(Y1 - 1 + a.reach, a.cell));
+    if (tid == 0) {
+      const int nrows = (cx0 <= cx1 && cy0 <= cy1) ? cy1 - cy0 + 1 : 0;
+      int run = 0;
+      for (int r = 0; r < nrows; ++r) {
+        const int c0 = (cy0 + r) * a.ncx;
+        const int s0 = a.cell_off[c0 + cx0];
+        s_rowstart[r] = s0;
+        s_rowpre[r] = run;
+        run += a.cell_off[c0 + cx1 + 1] - s0;
+      }
+      s_rowpre[nrows] = run;
+      s_nrows = nrows;
+      s_total = run;
+    }
+    __syncthreads();
+    const int total = s_total, nrows = s_nrows;
+
+    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c0 = 0; c0 < total; c0 += kNT) {
+      if (tid == 0) s_n = 0;
+      __syncthreads();
+      const int i = c0 + tid;
+      if (i < total) {
+        int r = 0;
+        while (r + 1 < nrows && s_rowpre[r + 1] <= i) ++r;
+        const int4 p = __ldg(reinterpret_cast<const int4*>(a.sorted) + s_rowstart[r] + (i - s_rowpre[r]));
+        const long long nlim = __ldg(&a.nlim_dev[p.w]);
+        const long long ddx = p.x < X0 ? X0 - p.x : (p.x > X1 - 1 ? p.x - (X1 - 1) : 0);
+        const long long ddy = p.y < Y0 ? Y0 - p.y : (p.y > Y1 - 1 ? p.y - (Y1 - 1) : 0);
+        if (ddx * ddx + ddy * ddy < nlim) {
+          const int slot = atomicAdd(&s_n, 1);
+          list[slot] = p;
+          lbeta[slot] = __ldg(&a.beta_dev[p.w]);
+          lnlim[slot] = nlim;
+        }
+      }
+      __syncthreads();
+      const int n = s_n;
+      const int px = X0 + col;
+      for (int s = 0; s < n; ++s) {
+        const int4 p = list[s];
+        const double beta = lbeta[s];
+        const long long nlim = lnlim[s];
+        const float amp = __int_as_float(p.z);
+        const long long dx = px - p.x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const long long dy = Y0 + row0 + 8 * q - p.y;
+          const long long nn = dx * dx + dy * dy;
+          if (nn < nlim) {
+            const double qd = __fma_rn((double)nn, a.alpha, beta);
+            const float qf = __double2float_rn(qd);
+            const float r0 = rsqrtf(qf);
+            const float s0 = qf * r0;
+            const double e = __fma_rn(-(double)s0, (double)s0, qd);
+            const float corr = __double2float_rn(e) * (0.5f * r0);
+            const float f = (s0 - floorf(s0)) + corr;
+            float sn, cs;
+            sincospif(2.0f * f, &sn, &cs);
+            re[q] = fmaf(amp, cs, re[q]);
+            im[q] = fmaf(amp, sn, im[q]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    const int px = X0 + col;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int py = Y0 + row0 + 8 * q;
+      if (px < X1 && py < Y1) a.u[(size_t)py * a.w + px] = make_float2(re[q], im[q]);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int direct_max_cell_rows() { return kMaxRows; }
+
+cudaError_t launch_direct(const DirectArgs& a, cudaStream_t s) {
+  direct_kernel<<<a.grid, kNT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace wsb

@@ -1,0 +1,483 @@
+// LUT builder (Sec. 1, step 1 "pre-computation"): per depth, the PSF on a
+// W x W window, its L-level orthonormal Haar transform and the N_r strongest
+// coefficients, compacted into a per-depth, window-tile-binned table.
+//
+// Work is confined to the window tiles that meet the PSF disk (the per-depth
+// bounding box meta[d].tlo..thi): every coefficient of a tile outside it is 0
+// because a tile's Haar coefficients depend only on that tile's pixels.
+//
+// Kernels (all on one stream):
+//   psf_haar_kernel   one block per (bbox tile group, depth): PSF pixels, then
+//                     the tile's Haar levels in shared memory (FP32, fixed
+//                     operation order, no contraction) -> coef scratch, nnz
+//   select_kernel     one block per depth: exact top-N_r of key = re^2 + im^2
+//                     (FP64 bit patterns, MSB radix select), equal keys
+//                     resolved by Mallat index (radix select on the index)
+//   tile_count_kernel one warp per window tile: kept count
+//   tile_scan_kernel  one block per depth: tile offsets (CSR)
+//   scatter_kernel    one warp per window tile: ordered compaction
+//   encode_kernel     one warp per 32 entries: FP16/BF16 + FP32 scale
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.cuh"
+
+namespace wsb {
+namespace {
+
+// cos and sin of 2*pi*g, g in [0, 1], FP32.  Quadrant reduction: q = nearest
+// integer of 4g, y = g - q/4 (exact), x = 2*pi*y in [-pi/4, pi/4]; Taylor
+// series of sin to x^9 and cos to x^10 in Horner form with fused multiply-adds
+// (range reduction + polynomial, J.-M. Muller, "Elementary Functions").  Every
+// operation is an explicitly rounded intrinsic so the result is a fixed
+// function of g.
+__device__ __forceinline__ void sincos2pi(float g, float* c_out, float* s_out) {
+  constexpr float two_pi = 6.28318530717958647692f;
+  constexpr float S3 = -1.0f / 6.0f, S5 = 1.0f / 120.0f, S7 = -1.0f / 5040.0f,
+                  S9 = 1.0f / 362880.0f;
+  constexpr float C2 = -1.0f / 2.0f, C4 = 1.0f / 24.0f, C6 = -1.0f / 720.0f,
+                  C8 = 1.0f / 40320.0f, C10 = -1.0f / 3628800.0f;
+  const float q = rintf(__fmul_rn(4.0f, g));
+  const float y = __fsub_rn(g, __fmul_rn(0.25f, q));
+  const float x = __fmul_rn(y, two_pi);
+  const float x2 = __fmul_rn(x, x);
+  float ps = __fmaf_rn(x2, S9, S7);
+  ps = __fmaf_rn(x2, ps, S5);
+  ps = __fmaf_rn(x2, ps, S3);
+  const float sn = __fmaf_rn(__fmul_rn(x, x2), ps, x);
+  float pc = __fmaf_rn(x2, C10, C8);
+  pc = __fmaf_rn(x2, pc, C6);
+  pc = __fmaf_rn(x2, pc, C4);
+  pc = __fmaf_rn(x2, pc, C2);
+  const float cs = __fmaf_rn(x2, pc, 1.0f);
+  switch (((int)q) & 3) {
+    case 0: *c_out = cs;  *s_out = sn;  break;
+    case 1: *c_out = -sn; *s_out = cs;  break;
+    case 2: *c_out = -cs; *s_out = -sn; break;
+    default: *c_out = sn; *s_out = -cs; break;
+  }
+}
+
+__device__ __forceinline__ float haar_s(float a, float b, float c, float d) {
+  return __fmul_rn(__fadd_rn(__fadd_rn(a, b), __fadd_rn(c, d)), 0.5f);
+}
+__device__ __forceinline__ float haar_lh(float a, float b, float c, float d) {
+  return __fmul_rn(__fadd_rn(__fsub_rn(a, b), __fsub_rn(c, d)), 0.5f);
+}
+__device__ __forceinline__ float haar_hl(float a, float b, float c, float d) {
+  return __fmul_rn(__fsub_rn(__fadd_rn(a, b), __fadd_rn(c, d)), 0.5f);
+}
+__device__ __forceinline__ float haar_hh(float a, float b, float c, float d) {
+  return __fmul_rn(__fsub_rn(__fsub_rn(a, b), __fsub_rn(c, d)), 0.5f);
+}
+
+__device__ __forceinline__ unsigned long long key_bits(float2 c) {
+  const double k = __dadd_rn(__dmul_rn((double)c.x, (double)c.x), __dmul_rn((double)c.y, (double)c.y));
+  return (unsigned long long)__double_as_longlong(k);
+}
+
+// Window tile i (row-major) of depth d's bounding box.
+struct BoxIter {
+  int tlo, nb, L, nwt;
+  __device__ __forceinline__ void tile(int i, int* tx, int* ty) const {
+    *tx = tlo + i % nb;
+    *ty = tlo + i / nb;
+  }
+  __device__ __forceinline__ long long coef_index(int tx, int ty, int slot) const {
+    return (((long long)ty * nwt + tx) << (2 * L)) + slot;
+  }
+};
+
+template <int L>
+__global__ void __launch_bounds__((1 << (2 * L)) >= 256 ? (1 << (2 * L)) : 256)
+psf_haar_kernel(LutBuildArgs a) {
+  constexpr int TS = 1 << L;
+  constexpr int TSL = TS * TS;
+  constexpr int NT = TSL >= 256 ? TSL : 256;
+  constexpr int TPB = NT / TSL;
+  __shared__ float2 sa[TPB][TSL];
+  __shared__ float2 sb[TPB][TSL];
+  __shared__ float2 co[TPB][TSL];
+  __shared__ unsigned int nz;
+  const int d = blockIdx.y;
+  const DepthMeta md = a.meta[d];
+  const int nb = md.thi - md.tlo + 1;
+  const int tl = threadIdx.x / TSL, pix = threadIdx.x % TSL;
+  const int bt = blockIdx.x * TPB + tl;  // tile index inside the box
+  const bool valid = bt < nb * nb;
+  const int tx = md.tlo + (valid ? bt % nb : 0), ty = md.tlo + (valid ? bt / nb : 0);
+  if (threadIdx.x == 0) nz = 0;
+
+  // PSF pixel (Eq. (1) PSF with the circular aperture of step 1).
+  const int pu = pix % TS, pv = pix / TS;
+  float2 val = make_float2(0.f, 0.f);
+  if (valid) {
+    const long long du = (long long)(tx * TS + pu) - a.W / 2;
+    const long long dv = (long long)(ty * TS + pv) - a.W / 2;
+    const long long n = du * du + dv * dv;
+    if ((double)n < a.R2_dev[d]) {
+      const double z = a.z_dev[d];
+      const double r = __dsqrt_rn(__fma_rn((double)n, __dmul_rn(a.pitch, a.pitch), __dmul_rn(z, z)));
+      const double t = __ddiv_rn(r, a.lambda);
+      const double f = __dsub_rn(t, floor(t));
+      sincos2pi(__double2float_rn(f), &val.x, &val.y);
+    }
+  }
+  sa[tl][pix] = val;
+  __syncthreads();
+
+  float2* cur = sa[tl];
+  float2* nxt = sb[tl];
+#pragma unroll
+  for (int l = 1; l <= L; ++l) {
+    const int S = TS >> (l - 1), h = S >> 1, m = L - l;
+    if (pix < h * h) {
+      const int i = pix / h, j = pix % h;
+      const float2 x00 = cur[(2 * i) * TS + 2 * j], x01 = cur[(2 * i) * TS + 2 * j + 1];
+      const float2 x10 = cur[(2 * i + 1) * TS + 2 * j], x11 = cur[(2 * i + 1) * TS + 2 * j + 1];
+      nxt[i * TS + j] = make_float2(haar_s(x00.x, x01.x, x10.x, x11.x), haar_s(x00.y, x01.y, x10.y, x11.y));
+      co[tl][(1 << (2 * m)) + (i << m) + j] =
+          make_float2(haar_lh(x00.x, x01.x, x10.x, x11.x), haar_lh(x00.y, x01.y, x10.y, x11.y));
+      co[tl][(2 << (2 * m)) + (i << m) + j] =
+          make_float2(haar_hl(x00.x, x01.x, x10.x, x11.x), haar_hl(x00.y, x01.y, x10.y, x11.y));
+      co[tl][(3 << (2 * m)) + (i << m) + j] =
+          make_float2(haar_hh(x00.x, x01.x, x10.x, x11.x), haar_hh(x00.y, x01.y, x10.y, x11.y));
+    }
+    __syncthreads();
+    float2* tmp = cur; cur = nxt; nxt = tmp;
+  }
+  if (pix == 0) co[tl][0] = cur[0];
+  __syncthreads();
+  const float2 c = co[tl][pix];
+  if (valid) a.coef[(long long)d * a.W * a.W + (((long long)ty * a.nwt + tx) << (2 * L)) + pix] = c;
+  const unsigned b = __ballot_sync(0xffffffffu, valid && (c.x != 0.f || c.y != 0.f));
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(&nz, (unsigned)__popc(b));
+  __syncthreads();
+  if (threadIdx.x == 0 && nz) atomicAdd(&a.nnz[d], (unsigned long long)nz);
+}
+
+// Block-wide exclusive scan of one unsigned per thread (blockDim.x = 1024).
+__device__ unsigned block_excl_scan(unsigned v, unsigned* total) {
+  __shared__ unsigned warp_sum[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned w = warp_sum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    warp_sum[lane] = w;  // inclusive
+  }
+  __syncthreads();
+  const unsigned before = (wid ? warp_sum[wid - 1] : 0u) + x - v;
+  if (total) *total = warp_sum[31];
+  __syncthreads();
+  return before;
+}
+
+constexpr int kModeGE = 0;   // keep key_bits >= T
+constexpr int kModeTie = 1;  // keep key_bits > T, or == T with Mallat index <= I*
+
+// One block per depth.  thr[2d] = T, thr[2d+1] = (mode << 32) | I*.
+__global__ void __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
+  __shared__ unsigned hist[4096];
+  __shared__ int s_found;
+  __shared__ unsigned s_cum;
+  const int d = blockIdx.x;
+  const DepthMeta md = a.meta[d];
+  const int nb = md.thi - md.tlo + 1;
+  const BoxIter it{md.tlo, nb, a.L, a.nwt};
+  const int ntb = nb * nb, tsl = 1 << (2 * a.L);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const float2* c = a.coef + (long long)d * a.W * a.W;
+  const long long nnz = (long long)a.nnz[d];
+  const long long k = min(nnz, a.target_dev[d]);
+  if (threadIdx.x == 0) a.nr_dev[d] = k;
+  if (k == nnz || k <= 0) {
+    if (threadIdx.x == 0) {
+      a.thr[2 * d] = k == nnz ? 1ull : ~0ull;  // 1: any nonzero key; ~0: none
+      a.thr[2 * d + 1] = (unsigned long long)kModeGE << 32;
+    }
+    return;
+  }
+  unsigned long long prefix = 0, hi_mask = 0;
+  unsigned rem = (unsigned)k;
+  int shift = 64;
+  bool done = false;
+  while (shift > 0 && !done) {
+    const int width = shift >= 11 ? 11 : shift;
+    shift -= width;
+    const unsigned nbins = 1u << width;
+    for (unsigned i = threadIdx.x; i < nbins; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int ti = warp; ti < ntb; ti += nwarps) {
+      int tx, ty;
+      it.tile(ti, &tx, &ty);
+      const float2* ct = c + it.coef_index(tx, ty, 0);
+      for (int slot = lane; slot < tsl; slot += 32) {
+        const unsigned long long kb = key_bits(ct[slot]);
+        if (kb != 0 && (kb & hi_mask) == prefix)
+          atomicAdd(&hist[(kb >> shift) & (nbins - 1)], 1u);
+      }
+    }
+    __syncthreads();
+    // Each thread owns 4 bins (2048 bins max -> threads 0..511 used); suffix
+    // sums from the top bin down find the bin holding the rem-th largest key.
+    const int t_rev = 1023 - threadIdx.x;  // thread 1023 owns the top bins
+    unsigned local = 0;
+    for (int j = 0; j < 4; ++j) {
+      const unsigned b = 4u * t_rev + j;
+      if (b < nbins) local += hist[b];
+    }
+    if (threadIdx.x == 0) s_found = -1;
+    const unsigned above = block_excl_scan(local, nullptr);  // sum over higher t_rev
+    unsigned cum = above;
+    for (int j = 3; j >= 0; --j) {
+      const unsigned b = 4u * t_rev + j;
+      if (b >= nbins) continue;
+      const unsigned hb = hist[b];
+      if (cum < rem && rem <= cum + hb) { s_found = (int)b; s_cum = cum; }
+      cum += hb;
+    }
+    __syncthreads();
+    if (s_found < 0) {  // counts inconsistent with nnz: keep nothing, report
+      if (threadIdx.x == 0) {
+        a.thr[2 * d] = ~0ull;
+        a.thr[2 * d + 1] = (unsigned long long)kModeGE << 32;
+        a.nr_dev[d] = 0;
+        atomicCAS(a.status, 0, WASABI_E_RANGE);
+      }
+      return;
+    }
+    const unsigned bstar = (unsigned)s_found;
+    rem -= s_cum;
+    prefix |= (unsigned long long)bstar << shift;
+    hi_mask |= (unsigned long long)(nbins - 1) << shift;
+    if (hist[bstar] == rem) done = true;
+    __syncthreads();
+  }
+  if (done) {
+    if (threadIdx.x == 0) {
+      a.thr[2 * d] = prefix;
+      a.thr[2 * d + 1] = (unsigned long long)kModeGE << 32;
+    }
+    return;
+  }
+  // Ties at the exact key T = prefix: the rem lowest Mallat indices among them.
+  unsigned iprefix = 0, ihi = 0;
+  for (int ishift = 12; ishift >= 0; ishift -= 12) {
+    for (unsigned i = threadIdx.x; i < 4096; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int ti = warp; ti < ntb; ti += nwarps) {
+      int tx, ty;
+      it.tile(ti, &tx, &ty);
+      const float2* ct = c + it.coef_index(tx, ty, 0);
+      for (int slot = lane; slot < tsl; slot += 32) {
+        const unsigned long long kb = key_bits(ct[slot]);
+        if (kb != prefix) continue;
+        const unsigned mi = (unsigned)mallat_index(a.W, a.L, tx, ty, slot);
+        if ((mi & ihi) == iprefix) atomicAdd(&hist[(mi >> ishift) & 4095u], 1u);
+      }
+    }
+    __syncthreads();
+    unsigned local = 0;
+    for (int j = 0; j < 4; ++j) local += hist[4 * threadIdx.x + j];
+    if (threadIdx.x == 0) s_found = -1;
+    const unsigned below = block_excl_scan(local, nullptr);
+    unsigned cum = below;
+    for (int j = 0; j < 4; ++j) {
+      const unsigned b = 4u * threadIdx.x + j;
+      const unsigned hb = hist[b];
+      if (cum < rem && rem <= cum + hb) { s_found = (int)b; s_cum = cum; }
+      cum += hb;
+    }
+    __syncthreads();
+    if (s_found < 0) {
+      if (threadIdx.x == 0) {
+        a.thr[2 * d] = ~0ull;
+        a.thr[2 * d + 1] = (unsigned long long)kModeGE << 32;
+        a.nr_dev[d] = 0;
+        atomicCAS(a.status, 0, WASABI_E_RANGE);
+      }
+      return;
+    }
+    rem -= s_cum;
+    iprefix |= (unsigned)s_found << ishift;
+    ihi |= 4095u << ishift;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.thr[2 * d] = prefix;
+    a.thr[2 * d + 1] = ((unsigned long long)kModeTie << 32) | iprefix;
+  }
+}
+
+__device__ __forceinline__ bool kept(unsigned long long kb, unsigned long long T, unsigned long long aux,
+                                     int W, int L, int tx, int ty, int slot) {
+  if (kb == 0) return false;
+  if ((int)(aux >> 32) == kModeGE) return kb >= T;
+  if (kb != T) return kb > T;
+  return (unsigned)mallat_index(W, L, tx, ty, slot) <= (unsigned)(aux & 0xffffffffu);
+}
+
+// One warp per window tile of the whole grid (tiles outside the box: 0).
+__global__ void __launch_bounds__(256) tile_count_kernel(LutBuildArgs a) {
+  const int d = blockIdx.y;
+  const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int ntile = a.nwt * a.nwt;
+  if (tile >= ntile) return;
+  const DepthMeta md = a.meta[d];
+  const int tx = tile % a.nwt, ty = tile / a.nwt;
+  int cnt = 0;
+  if (tx >= md.tlo && tx <= md.thi && ty >= md.tlo && ty <= md.thi) {
+    const unsigned long long T = a.thr[2 * d], aux = a.thr[2 * d + 1];
+    const float2* c = a.coef + (long long)d * a.W * a.W + ((long long)tile << (2 * a.L));
+    const int tsl = 1 << (2 * a.L);
+    for (int j0 = 0; j0 < tsl; j0 += 32) {
+      const int slot = j0 + lane;
+      bool s = false;
+      if (slot < tsl) s = kept(key_bits(c[slot]), T, aux, a.W, a.L, tx, ty, slot);
+      cnt += __popc(__ballot_sync(0xffffffffu, s));
+    }
+  }
+  if (lane == 0) a.tile_cnt[(long long)d * ntile + tile] = cnt;
+}
+
+__global__ void __launch_bounds__(1024) tile_scan_kernel(LutBuildArgs a) {
+  const int d = blockIdx.x;
+  const int ntile = a.nwt * a.nwt;
+  const int per = (ntile + 1023) / 1024;
+  const int t0 = threadIdx.x * per;
+  const int* cnt = a.tile_cnt + (long long)d * ntile;
+  int32_t* off = a.tile_off + (long long)d * (ntile + 1);
+  unsigned local = 0;
+  for (int t = t0; t < min(t0 + per, ntile); ++t) local += (unsigned)cnt[t];
+  unsigned total;
+  unsigned run = block_excl_scan(local, &total);
+  const int base = a.meta[d].base, cap = a.meta[d].cap;
+  // Offsets never leave the depth's region, even if the counts were wrong.
+  for (int t = t0; t < min(t0 + per, ntile); ++t) {
+    off[t] = base + min((int)run, cap);
+    run += (unsigned)cnt[t];
+  }
+  if (threadIdx.x == 0) {
+    off[ntile] = base + min((int)total, cap);
+    if ((long long)total != a.nr_dev[d]) atomicCAS(a.status, 0, WASABI_E_RANGE);
+  }
+}
+
+__global__ void __launch_bounds__(256) scatter_kernel(LutBuildArgs a) {
+  const int d = blockIdx.y;
+  const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int ntile = a.nwt * a.nwt;
+  if (tile >= ntile) return;
+  const DepthMeta md = a.meta[d];
+  const int tx = tile % a.nwt, ty = tile / a.nwt;
+  if (tx < md.tlo || tx > md.thi || ty < md.tlo || ty > md.thi) return;
+  const unsigned long long T = a.thr[2 * d], aux = a.thr[2 * d + 1];
+  const float2* c = a.coef + (long long)d * a.W * a.W + ((long long)tile << (2 * a.L));
+  int off = a.tile_off[(long long)d * (ntile + 1) + tile];
+  const int tsl = 1 << (2 * a.L);
+  for (int j0 = 0; j0 < tsl; j0 += 32) {
+    const int slot = j0 + lane;
+    bool s = false;
+    float2 v = make_float2(0.f, 0.f);
+    if (slot < tsl) {
+      v = c[slot];
+      s = kept(key_bits(v), T, aux, a.W, a.L, tx, ty, slot);
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, s);
+    const int e = off + __popc(b & ((1u << lane) - 1u));
+    if (s && e < md.base + md.cap) {
+      int lev, band, ix, iy;
+      slot_decode(a.L, slot, &lev, &band, &ix, &iy);
+      a.pos[e] = pack_pos(tx, ty, lev, band, ix, iy);
+      a.val[e] = v;
+    }
+    off += __popc(b);
+  }
+}
+
+// One warp per block of 32 consecutive entries of one depth.
+__global__ void __launch_bounds__(256) encode_kernel(LutBuildArgs a) {
+  const int d = blockIdx.y;
+  const long long blk = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const long long nr = a.nr_dev[d];
+  if (blk * 32 >= nr) return;
+  const long long e = a.meta[d].base + blk * 32 + lane;
+  const bool valid = blk * 32 + lane < nr;
+  const float2 v = valid ? a.val[e] : make_float2(0.f, 0.f);
+  float m = fmaxf(fabsf(v.x), fabsf(v.y));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const float s = m > 0.f ? m : 1.f;
+  const float qr = __fdiv_rn(v.x, s), qi = __fdiv_rn(v.y, s);
+  uint32_t packed;
+  if (a.dtype == WASABI_F16S) {
+    packed = (uint32_t)__half_as_ushort(__float2half_rn(qr)) |
+             ((uint32_t)__half_as_ushort(__float2half_rn(qi)) << 16);
+  } else {
+    packed = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(qr)) |
+             ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(qi)) << 16);
+  }
+  a.val16[e] = valid ? packed : 0u;
+  if (lane == 0) a.scale[e >> 5] = s;
+}
+
+template <int L>
+cudaError_t launch_psf_haar(const LutBuildArgs& a, int max_nb, cudaStream_t s) {
+  constexpr int TSL = 1 << (2 * L);
+  constexpr int NT = TSL >= 256 ? TSL : 256;
+  constexpr int TPB = NT / TSL;
+  const dim3 grid((unsigned)((max_nb * max_nb + TPB - 1) / TPB), (unsigned)a.D);
+  psf_haar_kernel<L><<<grid, NT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_lut_build(const LutBuildArgs& a, cudaStream_t s) {
+  // The largest per-depth box sizes the psf grid (smaller boxes idle out).
+  const int max_nb = a.max_nb;
+  cudaError_t e;
+  switch (a.L) {
+    case 1: e = launch_psf_haar<1>(a, max_nb, s); break;
+    case 2: e = launch_psf_haar<2>(a, max_nb, s); break;
+    case 3: e = launch_psf_haar<3>(a, max_nb, s); break;
+    case 4: e = launch_psf_haar<4>(a, max_nb, s); break;
+    case 5: e = launch_psf_haar<5>(a, max_nb, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  select_kernel<<<a.D, 1024, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int ntile = a.nwt * a.nwt;
+  const dim3 tgrid((unsigned)((ntile + 7) / 8), (unsigned)a.D);
+  tile_count_kernel<<<tgrid, 256, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  tile_scan_kernel<<<a.D, 1024, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  scatter_kernel<<<tgrid, 256, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.dtype != WASABI_F32) {
+    const long long blocks = (a.max_cap + 31) / 32;
+    const dim3 egrid((unsigned)((blocks + 7) / 8), (unsigned)a.D);
+    encode_kernel<<<egrid, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace wsb
