@@ -77,6 +77,7 @@ def lib():
         f.restype = C.c_int
         f.argtypes = [C.c_double, C.c_double, _f64p, C.c_int, C.c_int, C.c_int,
                       C.c_double, _i64p, C.c_int64, _i32p, t, C.c_int]
+    L.orc_build_lut_f64.argtypes = L.orc_build_lut_f64.argtypes + [C.c_int]
     for nm, t in (("orc_superpose_f32", _f32p), ("orc_superpose_f64", _f64p)):
         f = getattr(L, nm)
         f.restype = C.c_int
@@ -221,9 +222,14 @@ class Lut:
         return self.idx[o[d]:o[d + 1]], self.val[o[d]:o[d + 1]]
 
 
-def build_lut(lam, pitch, depths, W, L, gamma, dtype="f32", threads=1) -> Lut:
+def build_lut(lam, pitch, depths, W, L, gamma, dtype="f32", threads=1,
+              select_fp32=False) -> Lut:
     """Sec. 1, step 1 at every depth.  dtype 'f32' uses the FP32 PSF form
-    (reading R8) that decides the selection; 'f64' is the FP64 definition."""
+    (reading R8) that decides the selection; 'f64' is the FP64 definition.
+    With select_fp32 (f64 only) the kept index set is the one the FP32 form
+    selects and the values are FP64: the reference for precision errors,
+    since which coefficients are kept is an integer decision taken in the
+    GPU kernel's precision."""
     depths = np.ascontiguousarray(depths, np.float64)
     D = depths.size
     if gamma >= 1.0:
@@ -241,7 +247,7 @@ def build_lut(lam, pitch, depths, W, L, gamma, dtype="f32", threads=1) -> Lut:
         val = np.empty(max(cap, 1), np.complex128)
         rc = lib().orc_build_lut_f64(lam, pitch, _p(depths, _f64p), D, W, L, gamma,
                                      _p(nr, _i64p), cap, _p(idx, _i32p),
-                                     _p(val, _f64p), threads)
+                                     _p(val, _f64p), threads, int(select_fp32))
     if rc != 0:
         raise ValueError("oracle build_lut rejected its arguments (window too "
                          "small for a PSF, or capacity)")

@@ -310,7 +310,7 @@ int64_t select_strong(const T* coef, int W, double gamma, double R,
 template <typename T>
 int build_lut(double lambda, double pitch, const double* zd, int D, int W,
               int L, double gamma, int64_t* nr, int64_t cap, int32_t* idx,
-              T* val, int threads, bool fp32_psf) {
+              T* val, int threads, bool fp32_psf, bool select_fp32 = false) {
   const int64_t n = (int64_t)W * W;
   std::vector<std::vector<int32_t>> sel((size_t)D);
   std::vector<std::vector<T>> vals((size_t)D);
@@ -333,7 +333,18 @@ int build_lut(double lambda, double pitch, const double* zd, int D, int W,
     }
     haar_fwd(coef.data(), W, L);
     std::vector<int32_t> kept((size_t)n);
-    const int64_t k = select_strong(coef.data(), W, gamma, R, kept.data());
+    int64_t k;
+    if (!fp32_psf && select_fp32) {
+      // Keep the coefficients that the FP32 path keeps (the selection is an
+      // integer decision taken in the GPU kernel's precision), with FP64
+      // values.
+      std::vector<float> c32((size_t)(2 * n));
+      psf_f32(lambda, pitch, zd[d], W, c32.data());
+      haar_fwd(c32.data(), W, L);
+      k = select_strong(c32.data(), W, gamma, R, kept.data());
+    } else {
+      k = select_strong(coef.data(), W, gamma, R, kept.data());
+    }
     kept.resize((size_t)k);
     std::vector<T> v((size_t)(2 * k));
     for (int64_t i = 0; i < k; ++i) {
@@ -507,11 +518,12 @@ int orc_build_lut_f32(double lambda, double pitch, const double* zd, int D,
   return build_lut<float>(lambda, pitch, zd, D, W, L, gamma, nr, cap, idx, val,
                           threads, true);
 }
+// select_fp32 != 0: FP64 values at the indices the FP32 path selects.
 int orc_build_lut_f64(double lambda, double pitch, const double* zd, int D,
                       int W, int L, double gamma, int64_t* nr, int64_t cap,
-                      int32_t* idx, double* val, int threads) {
+                      int32_t* idx, double* val, int threads, int select_fp32) {
   return build_lut<double>(lambda, pitch, zd, D, W, L, gamma, nr, cap, idx,
-                           val, threads, false);
+                           val, threads, false, select_fp32 != 0);
 }
 
 int orc_superpose_f32(int W, int L, int D, const int64_t* nr, const int32_t* idx,

@@ -43,7 +43,7 @@ def test_c2_lut_bit_exact(w, orc):
     _compare(w, orc, 633e-9, 1e-6, zd, 1024, 4, 0.02)
 
 
-@pytest.mark.parametrize("L,W", [(1, 64), (2, 64), (3, 128), (5, 128)])
+@pytest.mark.parametrize("L,W", [(1, 128), (2, 128), (3, 128), (5, 128)])
 def test_levels(w, orc, L, W):
     zd = orc.depth_grid(20e-6, 150e-6, 5)
     _compare(w, orc, 633e-9, 1e-6, zd, W, L, 0.1)

@@ -167,7 +167,7 @@ def test_reduced_precision_forms(w, orc):
     """C4 forms on a small case: error against the FP64 oracle is reported
     per dtype; FP16 must stay close to FP32."""
     lam, pitch, zd, pts, _ = _oracle_case(orc, 12, 300, 512, 4, 256, 0.05)
-    o64 = orc.build_lut(lam, pitch, zd, 256, 4, 0.05, dtype="f64")
+    o64 = orc.build_lut(lam, pitch, zd, 256, 4, 0.05, dtype="f64", select_fp32=True)
     ref = orc.hologram(o64, pts, 512)
     p = w.pack_points(pts["x"], pts["y"], pts["a"], pts["d"])
     errs = {}
@@ -175,6 +175,6 @@ def test_reduced_precision_forms(w, orc):
         lut = w.build_lut(lam, pitch, zd, 256, 4, 0.05, dtype=dt)
         errs[dt] = rel_l2(w.hologram(lut, p, 512, 512).cpu().numpy(), ref)
     print("rel-L2 vs FP64 oracle:", errs)
-    assert errs["f32"] <= 1e-4
+    assert errs["f32"] <= 1e-5
     assert errs["f16s"] <= 1e-3
     assert errs["bf16s"] <= 1e-2

@@ -69,3 +69,15 @@ def test_lut_sizes_c1(orc):
         idx, val = lut.depth(d)
         assert np.all(np.diff(idx) > 0)
         assert np.all(val != 0)
+
+
+def test_fp64_values_with_fp32_selection(orc):
+    """The precision reference keeps the FP32 index set and carries FP64
+    values, which differ from the FP32 values only by FP32 rounding."""
+    zd = orc.depth_grid(20e-6, 150e-6, 6)
+    l32 = orc.build_lut(633e-9, 1e-6, zd, 256, 4, 0.05, dtype="f32")
+    l64 = orc.build_lut(633e-9, 1e-6, zd, 256, 4, 0.05, dtype="f64", select_fp32=True)
+    assert np.array_equal(l32.nr, l64.nr)
+    assert np.array_equal(l32.idx, l64.idx)
+    assert l64.val.dtype == np.complex128
+    assert np.max(np.abs(l64.val - l32.val.astype(np.complex128))) < 2e-6
