@@ -56,6 +56,13 @@ bool device_info(int** status, int* sms) {
     if (e != cudaSuccess) { set_error("cudaDeviceGetAttribute: %s", cudaGetErrorString(e)); return false; }
     g_status_ptr[dev] = static_cast<int*>(p);
     g_num_sms[dev] = n;
+    // Stream-ordered scratch (LUT builds) is freed back to the default pool;
+    // keep it there instead of unmapping it at every synchronisation.
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
   }
   if (status) *status = g_status_ptr[dev];
   if (sms) *sms = g_num_sms[dev];
@@ -120,12 +127,13 @@ struct wasabi_lut {
   int32_t* tile_off = nullptr;
   DepthMeta* meta_dev = nullptr;
   long long* nr_dev = nullptr;
+  float* cmax = nullptr;
 
   LutView view() const {
     LutView v;
     v.D = D; v.W = W; v.L = L; v.nwt = nwt; v.dtype = dtype;
     v.pos = pos; v.val = val; v.val16 = val16; v.scale = scale;
-    v.tile_off = tile_off; v.meta = meta_dev;
+    v.tile_off = tile_off; v.meta = meta_dev; v.cmax = cmax;
     return v;
   }
 };
@@ -149,9 +157,11 @@ struct Carver {
 void superpose_config(const wasabi_lut* lut, int w, int h, int* cell, int* threads) {
   int T = env_int("WASABI_SUPERPOSE_T", 128);
   int nt = env_int("WASABI_SUPERPOSE_THREADS", 1024);
-  T = std::min(T, 16 << lut->L);  // a window-tile row range must fit one warp
+  T = std::min(T, 128);  // the T x T accumulator lives in shared memory
   T = std::max(T, 1 << lut->L);
   T = (T >> lut->L) << lut->L;
+  while (T > (1 << lut->L) && superpose_smem_bytes(T, lut->L, lut->D) > 220 * 1024) T >>= 1;
+  nt = std::max(64, std::min(1024, nt / 32 * 32));
   (void)w; (void)h;
   *cell = T;
   *threads = nt;
@@ -303,6 +313,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   c.take<int32_t>((size_t)n_depths * ntpd);                          // tile_off
   c.take<DepthMeta>((size_t)n_depths);
   c.take<long long>((size_t)n_depths);                               // nr
+  c.take<float>(1);                                                  // cmax
   const size_t persist_bytes = align_up(c.off, 256);
   cudaError_t e = cudaMallocAsync(&lut->block, persist_bytes, s);
   if (e != cudaSuccess) { delete lut; set_error("build_lut: cudaMallocAsync: %s", cudaGetErrorString(e)); return WASABI_E_NOMEM; }
@@ -317,10 +328,12 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   lut->tile_off = c.take<int32_t>((size_t)n_depths * ntpd);
   lut->meta_dev = c.take<DepthMeta>((size_t)n_depths);
   lut->nr_dev = c.take<long long>((size_t)n_depths);
+  lut->cmax = c.take<float>(1);
 
   // Build scratch.
   Carver sc;
   sc.take<float2>((size_t)n_depths * window * window);
+  sc.take<unsigned long long>((size_t)n_depths * window * window);
   sc.take<unsigned long long>((size_t)n_depths);
   sc.take<unsigned long long>((size_t)2 * n_depths);
   sc.take<int>((size_t)n_depths * lut->nwt * lut->nwt);
@@ -342,6 +355,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   a.max_nb = max_nb; a.max_cap = max_cap;
   a.lambda = lambda; a.pitch = pitch;
   a.coef = sc.take<float2>((size_t)n_depths * window * window);
+  a.keys = sc.take<unsigned long long>((size_t)n_depths * window * window);
   a.nnz = sc.take<unsigned long long>((size_t)n_depths);
   a.thr = sc.take<unsigned long long>((size_t)2 * n_depths);
   a.tile_cnt = sc.take<int>((size_t)n_depths * lut->nwt * lut->nwt);
@@ -350,7 +364,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   long long* target_dev = sc.take<long long>((size_t)n_depths);
   a.z_dev = z_dev; a.R2_dev = R2_dev; a.target_dev = target_dev;
   a.nr_dev = lut->nr_dev; a.pos = lut->pos; a.val = lut->val; a.val16 = lut->val16; a.scale = lut->scale;
-  a.tile_off = lut->tile_off; a.meta = lut->meta_dev; a.status = status;
+  a.tile_off = lut->tile_off; a.meta = lut->meta_dev; a.cmax = lut->cmax; a.status = status;
 
   bool okc = true;
   okc = okc && cudaMemcpyAsync(z_dev, depths_host, sizeof(double) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
@@ -358,6 +372,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   okc = okc && cudaMemcpyAsync(target_dev, target.data(), sizeof(long long) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
   okc = okc && cudaMemcpyAsync(lut->meta_dev, lut->meta.data(), sizeof(DepthMeta) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
   okc = okc && cudaMemsetAsync(a.nnz, 0, sizeof(unsigned long long) * n_depths, s) == cudaSuccess;
+  okc = okc && cudaMemsetAsync(lut->cmax, 0, sizeof(float), s) == cudaSuccess;
   // The per-depth tables come from pageable host memory; make their upload
   // complete before the host vectors are released.
   okc = okc && cudaStreamSynchronize(s) == cudaSuccess;
@@ -528,20 +543,24 @@ wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points
   ba.pts = points_dev; ba.n = n; ba.D = lut->D; ba.w = holo_w; ba.h = holo_h; ba.cell = cell;
   ba.ncx = b.ncx; ba.ncy = b.ncy; ba.reach = lut->reach;
   ba.cnt = b.cnt; ba.off = b.off; ba.cursor = b.cursor; ba.sorted = b.sorted; ba.status = status;
-  cudaError_t e = launch_binning(ba, s);
-  if (e != cudaSuccess) return cuda_fail("superpose: binning", e);
-  e = cudaMemsetAsync(b.counter, 0, sizeof(int), s);
+  ba.amax = reinterpret_cast<float*>(b.counter + 1);
+  cudaError_t e = cudaMemsetAsync(b.counter, 0, 2 * sizeof(int), s);  // tile counter, amax
   if (e != cudaSuccess) return cuda_fail("superpose: memset", e);
+  e = launch_binning(ba, s);
+  if (e != cudaSuccess) return cuda_fail("superpose: binning", e);
   SuperposeArgs sa;
   sa.lut = lut->view();
   sa.sorted = b.sorted; sa.cell_off = b.off; sa.ncx = b.ncx; sa.ncy = b.ncy; sa.cell = cell;
   sa.w = holo_w; sa.h = holo_h; sa.ntx = holo_w >> lut->L; sa.nty = holo_h >> lut->L;
   sa.rule = rule; sa.reach = lut->reach; sa.counter = b.counter;
+  sa.amax = ba.amax;
+  sa.acc_float = env_int("WASABI_ACC_FLOAT", 0) != 0;
   sa.wbuf = static_cast<float2*>(wbuf_dev); sa.status = status; sa.threads = threads;
   const long long nst = (long long)((sa.ntx + (cell >> lut->L) - 1) / (cell >> lut->L)) *
                         ((sa.nty + (cell >> lut->L) - 1) / (cell >> lut->L));
-  const size_t smem = superpose_smem_bytes(cell, lut->D, threads);
-  const int per_sm = std::max(1, std::min(2048 / threads, (int)((227 * 1024) / (smem + 1024))));
+  const size_t smem = superpose_smem_bytes(cell, lut->L, lut->D);
+  if (smem > 220 * 1024) { set_error("superpose: super-tile %d needs %zu B of shared memory", cell, smem); return WASABI_E_INVALID; }
+  const int per_sm = std::max(1, std::min(2048 / threads, (int)((227 * 1024) / (smem + 2048))));
   sa.grid = (int)std::min<long long>(nst, (long long)sms * per_sm);
   e = launch_superpose(sa, s);
   return e == cudaSuccess ? WASABI_OK : cuda_fail("superpose: launch", e);
@@ -633,6 +652,7 @@ wasabi_status cgh_direct(double lambda, double pitch, const double* depths_host,
   ba.pts = points_dev; ba.n = n; ba.D = n_depths; ba.w = holo_w; ba.h = holo_h; ba.cell = cell;
   ba.ncx = b.ncx; ba.ncy = b.ncy; ba.reach = reach;
   ba.cnt = b.cnt; ba.off = b.off; ba.cursor = b.cursor; ba.sorted = b.sorted; ba.status = status;
+  ba.amax = nullptr;
   e = launch_binning(ba, s);
   if (e != cudaSuccess) return cuda_fail("cgh_direct: binning", e);
   e = cudaMemsetAsync(b.counter, 0, sizeof(int), s);

@@ -54,44 +54,61 @@ __global__ void count_kernel(BinArgs b, CellOf cf) {
   const wasabi_point p = b.pts[i];
   if (p.d >= (uint32_t)b.D) atomicCAS(b.status, 0, WASABI_E_RANGE);
   const int c = cf(p);
-  if (c >= 0) atomicAdd(&b.cnt[c], 1);
+  if (c >= 0) {
+    atomicAdd(&b.cnt[c], 1);
+    // Non-negative floats order like their bit patterns.
+    if (b.amax) atomicMax(reinterpret_cast<int*>(b.amax), __float_as_int(fabsf(p.a)));
+  }
 }
 
 // Single-block exclusive scan of ncells counts into off[0..ncells] and
-// cursor[0..ncells).
+// cursor[0..ncells): chunks of 4096 counts, each thread a coalesced int4,
+// one block scan per chunk, a running carry between chunks.
 __global__ void __launch_bounds__(1024) scan_kernel(BinArgs b, int ncells) {
   __shared__ unsigned warp_sum[32];
-  const int per = (ncells + 1023) / 1024;
-  const int t0 = threadIdx.x * per;
-  const int t1 = min(t0 + per, ncells);
-  unsigned local = 0;
-  for (int t = t0; t < t1; ++t) local += (unsigned)b.cnt[t];
+  __shared__ unsigned s_carry;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned x = local;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) warp_sum[wid] = x;
+  if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
-  if (wid == 0) {
-    unsigned w = warp_sum[lane];
+  for (int base = 0; base < ncells; base += 4096) {
+    const int i0 = base + 4 * threadIdx.x;
+    int c[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) c[j] = i0 + j < ncells ? b.cnt[i0 + j] : 0;
+    const unsigned local = (unsigned)(c[0] + c[1] + c[2] + c[3]);
+    unsigned x = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
+      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    warp_sum[lane] = w;
+    if (lane == 31) warp_sum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      unsigned w = warp_sum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      warp_sum[lane] = w;
+    }
+    __syncthreads();
+    const unsigned carry = s_carry;
+    unsigned run = carry + (wid ? warp_sum[wid - 1] : 0u) + x - local;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (i0 + j < ncells) {
+        b.off[i0 + j] = (int)run;
+        b.cursor[i0 + j] = (int)run;
+      }
+      run += (unsigned)c[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = carry + warp_sum[31];
+    __syncthreads();
   }
-  __syncthreads();
-  unsigned run = (wid ? warp_sum[wid - 1] : 0u) + x - local;
-  for (int t = t0; t < t1; ++t) {
-    b.off[t] = (int)run;
-    b.cursor[t] = (int)run;
-    run += (unsigned)b.cnt[t];
-  }
-  if (threadIdx.x == 1023) b.off[ncells] = (int)warp_sum[31];
+  if (threadIdx.x == 0) b.off[ncells] = (int)s_carry;
 }
 
 __global__ void scatter_points_kernel(BinArgs b, CellOf cf) {

@@ -69,6 +69,7 @@ struct LutView {
   const float* scale;     // one per 32 entries (index e >> 5)
   const int32_t* tile_off;
   const DepthMeta* meta;
+  const float* cmax;      // largest |re| or |im| of any kept coefficient
 };
 
 // ------------------------------------------------------------------ launchers
@@ -86,6 +87,7 @@ struct LutBuildArgs {
   const double* R2_dev;     // D squared radii (pixels^2)
   const long long* target_dev;  // D budgets (LLONG_MAX = keep all nonzero)
   float2* coef;             // scratch D * W * W
+  unsigned long long* keys; // scratch D * W * W: FP64 bit patterns of re^2 + im^2
   unsigned long long* nnz;  // scratch D
   unsigned long long* thr;  // scratch D x 2 selection descriptors
   int* tile_cnt;            // scratch D * nwt * nwt
@@ -96,6 +98,7 @@ struct LutBuildArgs {
   float* scale;
   int32_t* tile_off;
   const DepthMeta* meta;
+  float* cmax;              // out: largest |re| or |im| kept (zeroed by caller)
   int* status;
 };
 cudaError_t launch_lut_build(const LutBuildArgs& a, cudaStream_t s);
@@ -113,7 +116,8 @@ struct BinArgs {
   int cell;        // cell side (pixels)
   int ncx, ncy;
   int reach;       // pixels: a point farther than this outside the hologram is dropped
-  int* cnt;        // ncells + 1 (zeroed by caller)
+  int* cnt;        // ncells + 1 (zeroed here)
+  float* amax;     // largest |a| of the binned points (zeroed by caller)
   int* off;        // ncells + 1
   int* cursor;     // ncells
   wasabi_point* sorted;
@@ -130,13 +134,15 @@ struct SuperposeArgs {
   int rule;
   int reach;            // pixels
   int* counter;         // zeroed by caller
+  const float* amax;    // largest |a| of the binned points
+  int acc_float;        // 0: exact fixed-point accumulation, 1: FP32 atomics
   float2* wbuf;
   int* status;
   int threads;          // block size
   int grid;             // persistent CTAs
 };
 cudaError_t launch_superpose(const SuperposeArgs& a, cudaStream_t s);
-size_t superpose_smem_bytes(int cell, int D, int threads);
+size_t superpose_smem_bytes(int cell, int L, int D);
 
 cudaError_t launch_inverse(const float2* wbuf, int w, int h, int L, float2* u, uint8_t* bits,
                            int* status, int num_sms, cudaStream_t s);

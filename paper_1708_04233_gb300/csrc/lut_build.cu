@@ -149,8 +149,13 @@ psf_haar_kernel(LutBuildArgs a) {
   if (pix == 0) co[tl][0] = cur[0];
   __syncthreads();
   const float2 c = co[tl][pix];
-  if (valid) a.coef[(long long)d * a.W * a.W + (((long long)ty * a.nwt + tx) << (2 * L)) + pix] = c;
-  const unsigned b = __ballot_sync(0xffffffffu, valid && (c.x != 0.f || c.y != 0.f));
+  const bool nzc = c.x != 0.f || c.y != 0.f;
+  if (valid) {
+    const long long ci = (long long)d * a.W * a.W + (((long long)ty * a.nwt + tx) << (2 * L)) + pix;
+    a.coef[ci] = c;
+    a.keys[ci] = nzc ? key_bits(c) : 0ull;  // computed once: FP64 is scarce on this part
+  }
+  const unsigned b = __ballot_sync(0xffffffffu, valid && nzc);
   if ((threadIdx.x & 31) == 0 && b) atomicAdd(&nz, (unsigned)__popc(b));
   __syncthreads();
   if (threadIdx.x == 0 && nz) atomicAdd(&a.nnz[d], (unsigned long long)nz);
@@ -187,10 +192,20 @@ __device__ unsigned block_excl_scan(unsigned v, unsigned* total) {
 constexpr int kModeGE = 0;   // keep key_bits >= T
 constexpr int kModeTie = 1;  // keep key_bits > T, or == T with Mallat index <= I*
 
+constexpr int kCandCap = 2048;  // candidates moved to shared memory
+
 // One block per depth.  thr[2d] = T, thr[2d+1] = (mode << 32) | I*.
+// MSB-first radix select over the FP64 key bit patterns (keys are >= 0, so
+// their bit patterns order like the values), 11 bits per pass; once the
+// bucket holding the threshold has at most kCandCap members they are copied
+// to shared memory (with their Mallat indices) and the remaining passes run
+// there.  Equal keys at the threshold are resolved by a radix select on the
+// Mallat index (ascending).
 __global__ void __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
   __shared__ unsigned hist[4096];
-  __shared__ int s_found;
+  __shared__ unsigned long long ckey[kCandCap];
+  __shared__ unsigned cmi[kCandCap];
+  __shared__ int s_found, s_nc;
   __shared__ unsigned s_cum;
   const int d = blockIdx.x;
   const DepthMeta md = a.meta[d];
@@ -198,7 +213,7 @@ __global__ void __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
   const BoxIter it{md.tlo, nb, a.L, a.nwt};
   const int ntb = nb * nb, tsl = 1 << (2 * a.L);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const float2* c = a.coef + (long long)d * a.W * a.W;
+  const unsigned long long* kd = a.keys + (long long)d * a.W * a.W;
   const long long nnz = (long long)a.nnz[d];
   const long long k = min(nnz, a.target_dev[d]);
   if (threadIdx.x == 0) a.nr_dev[d] = k;
@@ -209,38 +224,51 @@ __global__ void __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
     }
     return;
   }
+  auto fail = [&]() {  // counts inconsistent with nnz: keep nothing, report
+    if (threadIdx.x == 0) {
+      a.thr[2 * d] = ~0ull;
+      a.thr[2 * d + 1] = (unsigned long long)kModeGE << 32;
+      a.nr_dev[d] = 0;
+      atomicCAS(a.status, 0, WASABI_E_RANGE);
+    }
+  };
   unsigned long long prefix = 0, hi_mask = 0;
   unsigned rem = (unsigned)k;
-  int shift = 64;
-  bool done = false;
+  int shift = 64, nc = 0;
+  bool done = false, in_list = false;
   while (shift > 0 && !done) {
     const int width = shift >= 11 ? 11 : shift;
     shift -= width;
     const unsigned nbins = 1u << width;
     for (unsigned i = threadIdx.x; i < nbins; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    for (int ti = warp; ti < ntb; ti += nwarps) {
-      int tx, ty;
-      it.tile(ti, &tx, &ty);
-      const float2* ct = c + it.coef_index(tx, ty, 0);
-      for (int slot = lane; slot < tsl; slot += 32) {
-        const unsigned long long kb = key_bits(ct[slot]);
-        if (kb != 0 && (kb & hi_mask) == prefix)
-          atomicAdd(&hist[(kb >> shift) & (nbins - 1)], 1u);
+    if (in_list) {
+      for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+        const unsigned long long kb = ckey[i];
+        if ((kb & hi_mask) == prefix) atomicAdd(&hist[(kb >> shift) & (nbins - 1)], 1u);
+      }
+    } else {
+      for (int ti = warp; ti < ntb; ti += nwarps) {
+        int tx, ty;
+        it.tile(ti, &tx, &ty);
+        const unsigned long long* kt = kd + it.coef_index(tx, ty, 0);
+        for (int slot = lane; slot < tsl; slot += 32) {
+          const unsigned long long kb = kt[slot];
+          if (kb != 0 && (kb & hi_mask) == prefix) atomicAdd(&hist[(kb >> shift) & (nbins - 1)], 1u);
+        }
       }
     }
     __syncthreads();
-    // Each thread owns 4 bins (2048 bins max -> threads 0..511 used); suffix
-    // sums from the top bin down find the bin holding the rem-th largest key.
-    const int t_rev = 1023 - threadIdx.x;  // thread 1023 owns the top bins
+    // Each thread owns 4 bins (threads 1023, 1022, ... own the top bins);
+    // suffix sums from the top find the bin holding the rem-th largest key.
+    const int t_rev = 1023 - threadIdx.x;
     unsigned local = 0;
     for (int j = 0; j < 4; ++j) {
       const unsigned b = 4u * t_rev + j;
       if (b < nbins) local += hist[b];
     }
     if (threadIdx.x == 0) s_found = -1;
-    const unsigned above = block_excl_scan(local, nullptr);  // sum over higher t_rev
-    unsigned cum = above;
+    unsigned cum = block_excl_scan(local, nullptr);
     for (int j = 3; j >= 0; --j) {
       const unsigned b = 4u * t_rev + j;
       if (b >= nbins) continue;
@@ -249,20 +277,36 @@ __global__ void __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
       cum += hb;
     }
     __syncthreads();
-    if (s_found < 0) {  // counts inconsistent with nnz: keep nothing, report
-      if (threadIdx.x == 0) {
-        a.thr[2 * d] = ~0ull;
-        a.thr[2 * d + 1] = (unsigned long long)kModeGE << 32;
-        a.nr_dev[d] = 0;
-        atomicCAS(a.status, 0, WASABI_E_RANGE);
-      }
-      return;
-    }
+    if (s_found < 0) { fail(); return; }
     const unsigned bstar = (unsigned)s_found;
+    const unsigned cnt_b = hist[bstar];
     rem -= s_cum;
     prefix |= (unsigned long long)bstar << shift;
     hi_mask |= (unsigned long long)(nbins - 1) << shift;
-    if (hist[bstar] == rem) done = true;
+    if (cnt_b == rem) {
+      done = true;
+    } else if (!in_list && cnt_b <= (unsigned)kCandCap && shift > 0) {
+      if (threadIdx.x == 0) s_nc = 0;
+      __syncthreads();
+      for (int ti = warp; ti < ntb; ti += nwarps) {
+        int tx, ty;
+        it.tile(ti, &tx, &ty);
+        const unsigned long long* kt = kd + it.coef_index(tx, ty, 0);
+        for (int slot = lane; slot < tsl; slot += 32) {
+          const unsigned long long kb = kt[slot];
+          if (kb != 0 && (kb & hi_mask) == prefix) {
+            const int i = atomicAdd(&s_nc, 1);
+            if (i < kCandCap) {
+              ckey[i] = kb;
+              cmi[i] = (unsigned)mallat_index(a.W, a.L, tx, ty, slot);
+            }
+          }
+        }
+      }
+      __syncthreads();
+      nc = min(s_nc, kCandCap);
+      in_list = true;
+    }
     __syncthreads();
   }
   if (done) {
@@ -277,23 +321,29 @@ __global__ void __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
   for (int ishift = 12; ishift >= 0; ishift -= 12) {
     for (unsigned i = threadIdx.x; i < 4096; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    for (int ti = warp; ti < ntb; ti += nwarps) {
-      int tx, ty;
-      it.tile(ti, &tx, &ty);
-      const float2* ct = c + it.coef_index(tx, ty, 0);
-      for (int slot = lane; slot < tsl; slot += 32) {
-        const unsigned long long kb = key_bits(ct[slot]);
-        if (kb != prefix) continue;
-        const unsigned mi = (unsigned)mallat_index(a.W, a.L, tx, ty, slot);
+    if (in_list) {
+      for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+        if (ckey[i] != prefix) continue;
+        const unsigned mi = cmi[i];
         if ((mi & ihi) == iprefix) atomicAdd(&hist[(mi >> ishift) & 4095u], 1u);
+      }
+    } else {
+      for (int ti = warp; ti < ntb; ti += nwarps) {
+        int tx, ty;
+        it.tile(ti, &tx, &ty);
+        const unsigned long long* kt = kd + it.coef_index(tx, ty, 0);
+        for (int slot = lane; slot < tsl; slot += 32) {
+          if (kt[slot] != prefix) continue;
+          const unsigned mi = (unsigned)mallat_index(a.W, a.L, tx, ty, slot);
+          if ((mi & ihi) == iprefix) atomicAdd(&hist[(mi >> ishift) & 4095u], 1u);
+        }
       }
     }
     __syncthreads();
     unsigned local = 0;
     for (int j = 0; j < 4; ++j) local += hist[4 * threadIdx.x + j];
     if (threadIdx.x == 0) s_found = -1;
-    const unsigned below = block_excl_scan(local, nullptr);
-    unsigned cum = below;
+    unsigned cum = block_excl_scan(local, nullptr);
     for (int j = 0; j < 4; ++j) {
       const unsigned b = 4u * threadIdx.x + j;
       const unsigned hb = hist[b];
@@ -301,15 +351,7 @@ __global__ void __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
       cum += hb;
     }
     __syncthreads();
-    if (s_found < 0) {
-      if (threadIdx.x == 0) {
-        a.thr[2 * d] = ~0ull;
-        a.thr[2 * d + 1] = (unsigned long long)kModeGE << 32;
-        a.nr_dev[d] = 0;
-        atomicCAS(a.status, 0, WASABI_E_RANGE);
-      }
-      return;
-    }
+    if (s_found < 0) { fail(); return; }
     rem -= s_cum;
     iprefix |= (unsigned)s_found << ishift;
     ihi |= 4095u << ishift;
@@ -341,12 +383,12 @@ __global__ void __launch_bounds__(256) tile_count_kernel(LutBuildArgs a) {
   int cnt = 0;
   if (tx >= md.tlo && tx <= md.thi && ty >= md.tlo && ty <= md.thi) {
     const unsigned long long T = a.thr[2 * d], aux = a.thr[2 * d + 1];
-    const float2* c = a.coef + (long long)d * a.W * a.W + ((long long)tile << (2 * a.L));
+    const unsigned long long* kt = a.keys + (long long)d * a.W * a.W + ((long long)tile << (2 * a.L));
     const int tsl = 1 << (2 * a.L);
     for (int j0 = 0; j0 < tsl; j0 += 32) {
       const int slot = j0 + lane;
       bool s = false;
-      if (slot < tsl) s = kept(key_bits(c[slot]), T, aux, a.W, a.L, tx, ty, slot);
+      if (slot < tsl) s = kept(kt[slot], T, aux, a.W, a.L, tx, ty, slot);
       cnt += __popc(__ballot_sync(0xffffffffu, s));
     }
   }
@@ -395,17 +437,22 @@ __global__ void __launch_bounds__(256) scatter_kernel(LutBuildArgs a) {
     float2 v = make_float2(0.f, 0.f);
     if (slot < tsl) {
       v = c[slot];
-      s = kept(key_bits(v), T, aux, a.W, a.L, tx, ty, slot);
+      s = kept(a.keys[(long long)d * a.W * a.W + ((long long)tile << (2 * a.L)) + slot], T, aux, a.W, a.L, tx, ty, slot);
     }
     const unsigned b = __ballot_sync(0xffffffffu, s);
     const int e = off + __popc(b & ((1u << lane) - 1u));
+    float cm = 0.f;
     if (s && e < md.base + md.cap) {
       int lev, band, ix, iy;
       slot_decode(a.L, slot, &lev, &band, &ix, &iy);
       a.pos[e] = pack_pos(tx, ty, lev, band, ix, iy);
       a.val[e] = v;
+      cm = fmaxf(fabsf(v.x), fabsf(v.y));
     }
     off += __popc(b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+    if (lane == 0 && cm > 0.f) atomicMax(reinterpret_cast<int*>(a.cmax), __float_as_int(cm));
   }
 }
 

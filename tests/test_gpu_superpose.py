@@ -178,3 +178,19 @@ def test_reduced_precision_forms(w, orc):
     assert errs["f32"] <= 1e-5
     assert errs["f16s"] <= 1e-3
     assert errs["bf16s"] <= 1e-2
+
+
+def test_fixed_point_is_deterministic_and_matches_float(w, orc, monkeypatch, c1):
+    """The exact fixed-point accumulator gives bit-identical buffers run to
+    run, and agrees with the FP32-atomic accumulator and the oracle."""
+    c, pts, zd, olut, lut = c1
+    p = w.pack_points(pts["x"], pts["y"], pts["a"], pts["d"])
+    a1 = w.superpose(lut, p, c.Nh, c.Nh).cpu().numpy()
+    a2 = w.superpose(lut, p, c.Nh, c.Nh).cpu().numpy()
+    assert np.array_equal(a1, a2)
+    monkeypatch.setenv("WASABI_ACC_FLOAT", "1")
+    f1 = w.superpose(lut, p, c.Nh, c.Nh).cpu().numpy()
+    w.sync_status()
+    psi = orc.superpose(olut, pts, c.Nh)
+    assert rel_l2(tile_major_to_mallat(f1, c.Nh, c.Nh, c.L), psi) <= TOL
+    assert rel_l2(a1, f1) <= TOL
