@@ -55,6 +55,10 @@ def lib_path() -> str:
     return _build.LIB
 
 
+# Variant builds (for example with profiling counters) live in another
+# directory, chosen by WASABI_BUILD_DIR at build and load time.
+
+
 def load(build_if_missing: bool = False):
     """Load libwasabi.so; raise if it is missing (no CPU fallback exists)."""
     global _lib

@@ -15,7 +15,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-OUT = os.path.join(HERE, "_build")
+OUT = os.environ.get("WASABI_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwasabi.so")
 ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -51,7 +51,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
     flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-             "-Xptxas", "-v", f"-I{os.path.join(ROOT, 'include')}"]
+             "-Xptxas", "-v", f"-I{os.path.join(ROOT, 'include')}",
+             *os.environ.get("WASABI_NVCC_EXTRA", "").split()]
 
     def compile_one(src: str) -> tuple[str, str]:
         obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")

@@ -18,6 +18,7 @@
 
 namespace wsb {
 int superpose_max_cell_rows();
+int superpose_min_threads();
 int direct_max_cell_rows();
 }  // namespace wsb
 
@@ -128,12 +129,14 @@ struct wasabi_lut {
   DepthMeta* meta_dev = nullptr;
   long long* nr_dev = nullptr;
   float* cmax = nullptr;
+  unsigned* levels = nullptr;  // bit l: a level-l coefficient is kept
+  int lmin = 1;                // finest kept level (host copy)
 
   LutView view() const {
     LutView v;
     v.D = D; v.W = W; v.L = L; v.nwt = nwt; v.dtype = dtype;
     v.pos = pos; v.val = val; v.val16 = val16; v.scale = scale;
-    v.tile_off = tile_off; v.meta = meta_dev; v.cmax = cmax;
+    v.tile_off = tile_off; v.meta = meta_dev; v.cmax = cmax; v.lmin = lmin;
     return v;
   }
 };
@@ -155,13 +158,13 @@ struct Carver {
 
 // Super-tile side and block size for a hologram (the autotuner's default).
 void superpose_config(const wasabi_lut* lut, int w, int h, int* cell, int* threads) {
-  int T = env_int("WASABI_SUPERPOSE_T", 128);
-  int nt = env_int("WASABI_SUPERPOSE_THREADS", 1024);
-  T = std::min(T, 128);  // the T x T accumulator lives in shared memory
-  T = std::max(T, 1 << lut->L);
+  int T = env_int("WASABI_SUPERPOSE_T", superpose_default_cell(lut->L, lut->lmin, lut->D));
+  int nt = env_int("WASABI_SUPERPOSE_THREADS", 512);
+  T = std::min(T, 256);
+  T = std::max(T, std::max(1 << lut->L, 32));
   T = (T >> lut->L) << lut->L;
-  while (T > (1 << lut->L) && superpose_smem_bytes(T, lut->L, lut->D) > 220 * 1024) T >>= 1;
-  nt = std::max(64, std::min(1024, nt / 32 * 32));
+  while (T > std::max(1 << lut->L, 32) && superpose_smem_bytes(T, lut->L, lut->lmin, lut->D) > 220 * 1024) T >>= 1;
+  nt = std::max(superpose_min_threads(), std::min(512, nt / 32 * 32));
   (void)w; (void)h;
   *cell = T;
   *threads = nt;
@@ -298,7 +301,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   if (base > INT_MAX) { delete lut; set_error("build_lut: table too large"); return WASABI_E_INVALID; }
   lut->total_cap = base;
   lut->reach = max_fr + (2 << levels);
-  const int ntpd = lut->nwt * lut->nwt + 1;
+  const int ntpd = 2 * lut->nwt * (lut->nwt + 1);  // per depth: rows x segments x (tiles + 1)
   const cudaStream_t s = (cudaStream_t)stream;
   int* status;
   int sms;
@@ -314,6 +317,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   c.take<DepthMeta>((size_t)n_depths);
   c.take<long long>((size_t)n_depths);                               // nr
   c.take<float>(1);                                                  // cmax
+  c.take<unsigned>(1);                                               // levels
   const size_t persist_bytes = align_up(c.off, 256);
   cudaError_t e = cudaMallocAsync(&lut->block, persist_bytes, s);
   if (e != cudaSuccess) { delete lut; set_error("build_lut: cudaMallocAsync: %s", cudaGetErrorString(e)); return WASABI_E_NOMEM; }
@@ -329,6 +333,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   lut->meta_dev = c.take<DepthMeta>((size_t)n_depths);
   lut->nr_dev = c.take<long long>((size_t)n_depths);
   lut->cmax = c.take<float>(1);
+  lut->levels = c.take<unsigned>(1);
 
   // Build scratch.
   Carver sc;
@@ -336,7 +341,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   sc.take<unsigned long long>((size_t)n_depths * window * window);
   sc.take<unsigned long long>((size_t)n_depths);
   sc.take<unsigned long long>((size_t)2 * n_depths);
-  sc.take<int>((size_t)n_depths * lut->nwt * lut->nwt);
+  sc.take<int>((size_t)n_depths * 2 * lut->nwt * lut->nwt);
   sc.take<double>((size_t)n_depths);
   sc.take<double>((size_t)n_depths);
   sc.take<long long>((size_t)n_depths);
@@ -358,13 +363,14 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   a.keys = sc.take<unsigned long long>((size_t)n_depths * window * window);
   a.nnz = sc.take<unsigned long long>((size_t)n_depths);
   a.thr = sc.take<unsigned long long>((size_t)2 * n_depths);
-  a.tile_cnt = sc.take<int>((size_t)n_depths * lut->nwt * lut->nwt);
+  a.tile_cnt = sc.take<int>((size_t)n_depths * 2 * lut->nwt * lut->nwt);
   double* z_dev = sc.take<double>((size_t)n_depths);
   double* R2_dev = sc.take<double>((size_t)n_depths);
   long long* target_dev = sc.take<long long>((size_t)n_depths);
   a.z_dev = z_dev; a.R2_dev = R2_dev; a.target_dev = target_dev;
   a.nr_dev = lut->nr_dev; a.pos = lut->pos; a.val = lut->val; a.val16 = lut->val16; a.scale = lut->scale;
-  a.tile_off = lut->tile_off; a.meta = lut->meta_dev; a.cmax = lut->cmax; a.status = status;
+  a.tile_off = lut->tile_off; a.meta = lut->meta_dev; a.cmax = lut->cmax; a.levels = lut->levels;
+  a.status = status;
 
   bool okc = true;
   okc = okc && cudaMemcpyAsync(z_dev, depths_host, sizeof(double) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
@@ -373,6 +379,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   okc = okc && cudaMemcpyAsync(lut->meta_dev, lut->meta.data(), sizeof(DepthMeta) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
   okc = okc && cudaMemsetAsync(a.nnz, 0, sizeof(unsigned long long) * n_depths, s) == cudaSuccess;
   okc = okc && cudaMemsetAsync(lut->cmax, 0, sizeof(float), s) == cudaSuccess;
+  okc = okc && cudaMemsetAsync(lut->levels, 0, sizeof(unsigned), s) == cudaSuccess;
   // The per-depth tables come from pageable host memory; make their upload
   // complete before the host vectors are released.
   okc = okc && cudaStreamSynchronize(s) == cudaSuccess;
@@ -388,6 +395,20 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
     cudaFreeAsync(lut->block, s);
     delete lut;
     return cuda_fail("build_lut: launch", e);
+  }
+  // The finest kept level sizes the superposition's accumulator: wait for the
+  // build and read it back.
+  unsigned lvmask = 0;
+  e = cudaMemcpyAsync(&lvmask, lut->levels, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(lut->block, s);
+    delete lut;
+    return cuda_fail("build_lut: readback", e);
+  }
+  lut->lmin = lut->L;  // an empty table needs only the coarsest slots
+  for (int l = 1; l <= lut->L; ++l) {
+    if (lvmask & (1u << l)) { lut->lmin = l; break; }
   }
   *out = lut;
   return WASABI_OK;
@@ -458,9 +479,11 @@ wasabi_status read_depth(const wasabi_lut* lut, int depth, std::vector<uint32_t>
 }
 
 int32_t pos_to_mallat(const wasabi_lut* lut, uint32_t p) {
-  const int tx = p & 511, ty = (p >> 9) & 511, lev = (p >> 18) & 7;
-  const int band = (p >> 21) & 3, ix = (p >> 23) & 15, iy = (int)(p >> 27);
-  return mallat_index(lut->W, lut->L, tx, ty, tile_slot(lut->L, lev, band, ix, iy));
+  const int P = p & 4095, Q = (p >> 12) & 4095, lev = (p >> 24) & 7, band = (p >> 27) & 3;
+  const int S = lut->W >> lev;
+  const int row = Q + ((band == 2 || band == 3) ? S : 0);
+  const int col = P + ((band == 1 || band == 3) ? S : 0);
+  return row * lut->W + col;
 }
 }  // namespace
 
@@ -504,7 +527,7 @@ wasabi_status wasabi_scratch_bytes(const wasabi_lut* lut, int64_t n, int holo_w,
     return WASABI_E_INVALID;
   }
   // The smallest cell the configuration can pick bounds every layout.
-  const int cell = std::max(1 << lut->L, std::min(64, 16 << lut->L));
+  const int cell = std::max(1 << lut->L, 32);
   *bytes_out = bin_layout(n, holo_w, holo_h, cell, nullptr).bytes;
   return WASABI_OK;
 }
@@ -544,7 +567,7 @@ wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points
   ba.ncx = b.ncx; ba.ncy = b.ncy; ba.reach = lut->reach;
   ba.cnt = b.cnt; ba.off = b.off; ba.cursor = b.cursor; ba.sorted = b.sorted; ba.status = status;
   ba.amax = reinterpret_cast<float*>(b.counter + 1);
-  cudaError_t e = cudaMemsetAsync(b.counter, 0, 2 * sizeof(int), s);  // tile counter, amax
+  cudaError_t e = cudaMemsetAsync(b.counter, 0, 32 * sizeof(int), s);  // counter, amax, timers
   if (e != cudaSuccess) return cuda_fail("superpose: memset", e);
   e = launch_binning(ba, s);
   if (e != cudaSuccess) return cuda_fail("superpose: binning", e);
@@ -554,14 +577,14 @@ wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points
   sa.w = holo_w; sa.h = holo_h; sa.ntx = holo_w >> lut->L; sa.nty = holo_h >> lut->L;
   sa.rule = rule; sa.reach = lut->reach; sa.counter = b.counter;
   sa.amax = ba.amax;
+  sa.timers = reinterpret_cast<unsigned long long*>(b.counter + 16);
   sa.acc_float = env_int("WASABI_ACC_FLOAT", 0) != 0;
   sa.wbuf = static_cast<float2*>(wbuf_dev); sa.status = status; sa.threads = threads;
-  const long long nst = (long long)((sa.ntx + (cell >> lut->L) - 1) / (cell >> lut->L)) *
-                        ((sa.nty + (cell >> lut->L) - 1) / (cell >> lut->L));
-  const size_t smem = superpose_smem_bytes(cell, lut->L, lut->D);
+  sa.nst = (long long)((sa.ntx + (cell >> lut->L) - 1) / (cell >> lut->L)) *
+           ((sa.nty + (cell >> lut->L) - 1) / (cell >> lut->L));
+  const size_t smem = superpose_smem_bytes(cell, lut->L, lut->lmin, lut->D);
   if (smem > 220 * 1024) { set_error("superpose: super-tile %d needs %zu B of shared memory", cell, smem); return WASABI_E_INVALID; }
-  const int per_sm = std::max(1, std::min(2048 / threads, (int)((227 * 1024) / (smem + 2048))));
-  sa.grid = (int)std::min<long long>(nst, (long long)sms * per_sm);
+  sa.grid = sms;
   e = launch_superpose(sa, s);
   return e == cudaSuccess ? WASABI_OK : cuda_fail("superpose: launch", e);
 }

@@ -3,9 +3,11 @@
 // Layout notes (the public contract is in include/wasabi.h):
 //  * LUT entries, per depth d, live at [meta[d].base, meta[d].base + nr[d]) of
 //    the pos/val arrays, ordered by window tile (row-major) and then by in-tile
-//    slot.  tile_off[d * (nwt*nwt + 1) + t] is the absolute index of window tile
-//    t's first entry; entry t + 1 is its end.
-//  * pos packs tx:9 | ty:9 | level:3 | band:2 | ix:4 | iy:4 (see pack_pos).
+//    slot.  tile_off[d * (nwt*nwt + 1) + t] is the absolute index of window
+//    tile t's first entry; entry t + 1 is its end.
+//  * pos packs the coefficient's window sub-band position p:12 | q:12 (in
+//    units of its level) | level:3 | band:2 (see pack_pos); its window tile is
+//    (p >> (L - level), q >> (L - level)).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,9 +21,8 @@ constexpr int kMaxDepths = 4096;
 constexpr int kMaxLevels = 5;
 constexpr int kMaxWindowTiles = 512;  // window / 2^levels
 
-__host__ __device__ inline uint32_t pack_pos(int tx, int ty, int lev, int band, int ix, int iy) {
-  return (uint32_t)tx | ((uint32_t)ty << 9) | ((uint32_t)lev << 18) | ((uint32_t)band << 21) |
-         ((uint32_t)ix << 23) | ((uint32_t)iy << 27);
+__host__ __device__ inline uint32_t pack_pos(int p, int q, int lev, int band) {
+  return (uint32_t)p | ((uint32_t)q << 12) | ((uint32_t)lev << 24) | ((uint32_t)band << 27);
 }
 
 // Slot of (level, band, ix, iy) inside a 2^L x 2^L tile (m = L - level).
@@ -70,6 +71,7 @@ struct LutView {
   const int32_t* tile_off;
   const DepthMeta* meta;
   const float* cmax;      // largest |re| or |im| of any kept coefficient
+  int lmin;               // finest level with a kept coefficient
 };
 
 // ------------------------------------------------------------------ launchers
@@ -99,6 +101,7 @@ struct LutBuildArgs {
   int32_t* tile_off;
   const DepthMeta* meta;
   float* cmax;              // out: largest |re| or |im| kept (zeroed by caller)
+  unsigned* levels;         // out: bit l set if a level-l coefficient is kept (zeroed by caller)
   int* status;
 };
 cudaError_t launch_lut_build(const LutBuildArgs& a, cudaStream_t s);
@@ -136,13 +139,16 @@ struct SuperposeArgs {
   int* counter;         // zeroed by caller
   const float* amax;    // largest |a| of the binned points
   int acc_float;        // 0: exact fixed-point accumulation, 1: FP32 atomics
+  unsigned long long* timers;  // 6 phase cycle counters (profiling builds only)
   float2* wbuf;
   int* status;
   int threads;          // block size
-  int grid;             // persistent CTAs
+  int grid;             // SMs: the launch puts as many CTAs on each as fit
+  long long nst;        // super-tiles
 };
 cudaError_t launch_superpose(const SuperposeArgs& a, cudaStream_t s);
-size_t superpose_smem_bytes(int cell, int L, int D);
+size_t superpose_smem_bytes(int cell, int L, int lmin, int D);
+int superpose_default_cell(int L, int lmin, int D);
 
 cudaError_t launch_inverse(const float2* wbuf, int w, int h, int L, float2* u, uint8_t* bits,
                            int* status, int num_sms, cudaStream_t s);

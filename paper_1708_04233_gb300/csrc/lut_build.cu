@@ -371,6 +371,10 @@ __device__ __forceinline__ bool kept(unsigned long long kb, unsigned long long T
   return (unsigned)mallat_index(W, L, tx, ty, slot) <= (unsigned)(aux & 0xffffffffu);
 }
 
+// Layout of the kept entries of one depth: window tiles row-major, each
+// tile's entries in slot order.  tile_off[d * (nwt*nwt + 1) + t] is the
+// absolute index of window tile t's first entry; t = nwt*nwt ends the depth.
+
 // One warp per window tile of the whole grid (tiles outside the box: 0).
 __global__ void __launch_bounds__(256) tile_count_kernel(LutBuildArgs a) {
   const int d = blockIdx.y;
@@ -428,32 +432,40 @@ __global__ void __launch_bounds__(256) scatter_kernel(LutBuildArgs a) {
   const int tx = tile % a.nwt, ty = tile / a.nwt;
   if (tx < md.tlo || tx > md.thi || ty < md.tlo || ty > md.thi) return;
   const unsigned long long T = a.thr[2 * d], aux = a.thr[2 * d + 1];
-  const float2* c = a.coef + (long long)d * a.W * a.W + ((long long)tile << (2 * a.L));
+  const long long cbase = (long long)d * a.W * a.W + ((long long)tile << (2 * a.L));
   int off = a.tile_off[(long long)d * (ntile + 1) + tile];
   const int tsl = 1 << (2 * a.L);
+  const unsigned lt = (1u << lane) - 1u;
+  float cm = 0.f;
+  unsigned levmask = 0;  // levels present among this tile's kept entries
   for (int j0 = 0; j0 < tsl; j0 += 32) {
     const int slot = j0 + lane;
     bool s = false;
     float2 v = make_float2(0.f, 0.f);
     if (slot < tsl) {
-      v = c[slot];
-      s = kept(a.keys[(long long)d * a.W * a.W + ((long long)tile << (2 * a.L)) + slot], T, aux, a.W, a.L, tx, ty, slot);
+      v = a.coef[cbase + slot];
+      s = kept(a.keys[cbase + slot], T, aux, a.W, a.L, tx, ty, slot);
     }
     const unsigned b = __ballot_sync(0xffffffffu, s);
-    const int e = off + __popc(b & ((1u << lane) - 1u));
-    float cm = 0.f;
+    const int e = off + __popc(b & lt);
     if (s && e < md.base + md.cap) {
       int lev, band, ix, iy;
       slot_decode(a.L, slot, &lev, &band, &ix, &iy);
-      a.pos[e] = pack_pos(tx, ty, lev, band, ix, iy);
+      const int m = a.L - lev;
+      a.pos[e] = pack_pos((tx << m) + ix, (ty << m) + iy, lev, band);
       a.val[e] = v;
-      cm = fmaxf(fabsf(v.x), fabsf(v.y));
+      cm = fmaxf(cm, fmaxf(fabsf(v.x), fabsf(v.y)));
+      levmask |= 1u << lev;
     }
     off += __popc(b);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
-    if (lane == 0 && cm > 0.f) atomicMax(reinterpret_cast<int*>(a.cmax), __float_as_int(cm));
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+    levmask |= __shfl_xor_sync(0xffffffffu, levmask, o);
+  }
+  if (lane == 0 && cm > 0.f) atomicMax(reinterpret_cast<int*>(a.cmax), __float_as_int(cm));
+  if (lane == 0 && levmask) atomicOr(a.levels, levmask);
 }
 
 // One warp per block of 32 consecutive entries of one depth.
