@@ -146,6 +146,9 @@ wasabi_status wasabi_lut_entries(const wasabi_lut* lut, int depth, int32_t* idx_
 wasabi_status wasabi_scratch_bytes(const wasabi_lut* lut, int64_t n, int holo_w, int holo_h,
                                    size_t* bytes_out);
 
+/* Size of the fixed scratch array behind wasabi_superpose_static: 32 MiB. */
+#define WASABI_STATIC_SCRATCH_BYTES (32 * 1024 * 1024)
+
 /* A4 + A5, superposition in the wavelet domain (Eq. (2)):
  *   psi = sum_j a_j sum_k c_{d_j,k} placed by the shift rule,
  * written to wbuf_dev (tile-major, holo_w * holo_h complex64, fully
@@ -156,6 +159,24 @@ wasabi_status wasabi_scratch_bytes(const wasabi_lut* lut, int64_t n, int holo_w,
 wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n,
                                int holo_w, int holo_h, int rule, void* wbuf_dev,
                                void* scratch_dev, size_t scratch_bytes, void* stream);
+
+/* wasabi_superpose without a scratch argument, for callers that cannot
+ * allocate device memory while they run: plug-ins whose host application
+ * owns all device memory, real-time loops that forbid allocation after
+ * start-up, and bindings that reach the C ABI but no CUDA allocator.  (The
+ * paper has no counterpart; this is an interface convenience.)
+ * Same arguments and result as wasabi_superpose, minus scratch.  The scratch
+ * is one file-scope device array of WASABI_STATIC_SCRATCH_BYTES that every
+ * device loading the library holds until the process exits; this call
+ * allocates nothing.  Problems whose wasabi_scratch_bytes() exceeds that size
+ * are rejected with WASABI_E_NOMEM (use wasabi_superpose then).
+ * The first call on a device looks the array's device address up (a
+ * synchronous runtime query): make that first call before any stream capture.
+ * All calls share the array and it keeps the previous call's contents (each
+ * call re-initialises what it reads); calls that overlap on the GPU race on
+ * it, so serialise them (one stream, or events between streams). */
+wasabi_status wasabi_superpose_static(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n,
+                                      int holo_w, int holo_h, int rule, void* wbuf_dev, void* stream);
 
 /* A6 + A7, inverse transformation (Sec. 1, step 3; Sec. 2 binary hologram):
  * the L-level inverse Haar of the tile-major wbuf_dev gives the field u.

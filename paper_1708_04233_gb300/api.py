@@ -145,6 +145,19 @@ def superpose(lut: Lut, points: torch.Tensor, w: int, h: int, rule: int = 0,
     return wbuf
 
 
+def superpose_static(lut: Lut, points: torch.Tensor, w: int, h: int, rule: int = 0,
+                     wbuf: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Eq. (2) through wasabi_superpose_static: no scratch argument; the
+    library's fixed device array is used, nothing is allocated by the call
+    (the output buffer is allocated here only when not given)."""
+    n = points.shape[0]
+    if wbuf is None:
+        wbuf = torch.empty(h * w, dtype=torch.complex64, device=points.device)
+    check(_lib().wasabi_superpose_static(lut.handle, _ptr(points) if n else C.c_void_p(None), n, w,
+                                         h, rule, _ptr(wbuf), _stream(stream)))
+    return wbuf
+
+
 def inverse_haar(wbuf: torch.Tensor, w: int, h: int, levels: int, u: torch.Tensor | None = None,
                  bits: torch.Tensor | None = None, want: str = "complex", stream=None):
     dev = wbuf.device
