@@ -328,27 +328,48 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
       }
       __syncthreads();
       PT_MARK(3);
-      // ---- visits: warp w takes [w*per, (w+1)*per), 32 at a time
+      // ---- visits: warp w takes [w*per, (w+1)*per), 32 at a time, kUnroll
+      // chunks per round: every chunk's range lookup (shared memory only) and
+      // LUT loads are issued before any of them is consumed.
       if (nvis > 0) {
+        constexpr int kUnroll = 4;
         const int vper = (nvis + nwarps - 1) / nwarps;
         const int v0 = warp * vper, v1 = min(nvis, v0 + vper);
         int rb = v0 < v1 ? last_le(S.rpre, 0, nranges - 1, v0) : 0;
-        for (int b = v0; b < v1; b += 32) {
-          const int i = b + lane;
-          // Range of visit i: rb plus the number of range starts in (b, i].
-          // Ranges are non-empty, so their starts are distinct.
-          const int f = rb + 1 + lane;
-          const int bnd = f <= nranges ? S.rpre[f] : 0x7fffffff;
-          const int mpos = bnd - b;
-          const unsigned bit = (mpos >= 0 && mpos < 32) ? (1u << mpos) : 0u;
-          const unsigned M = __reduce_or_sync(0xffffffffu, bit);
-          const int r = rb + __popc(M & ((2u << lane) - 1u));
-          rb = __shfl_sync(0xffffffffu, r, 31);
-          if (i >= v1) continue;
-          const int2 rec = S.rrec[r];
-          const int e = i + rec.x;
-          const uint32_t pp = __ldg(&lut.pos[e]);
-          const float2 v = lut_value<DT>(lut, e);
+        for (int b0 = v0; b0 < v1; b0 += 32 * kUnroll) {
+          int ee[kUnroll], sv[kUnroll];
+          uint32_t ppu[kUnroll];
+          float2 vvu[kUnroll];
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            const int b = b0 + 32 * u;
+            const int i = b + lane;
+            // Range of visit i: rb plus the number of range starts in (b, i].
+            // Ranges are non-empty, so their starts are distinct.
+            const int f = rb + 1 + lane;
+            const int bnd = f <= nranges ? S.rpre[f] : 0x7fffffff;
+            const int mpos = bnd - b;
+            const unsigned bit = (mpos >= 0 && mpos < 32) ? (1u << mpos) : 0u;
+            const unsigned M = __reduce_or_sync(0xffffffffu, bit);
+            const int r = min(rb + __popc(M & ((2u << lane) - 1u)), nranges - 1);
+            rb = __shfl_sync(0xffffffffu, r, 31);
+            const int2 rec = S.rrec[r];
+            ee[u] = i < v1 ? i + rec.x : -1;
+            sv[u] = rec.y;
+          }
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            if (ee[u] >= 0) {
+              ppu[u] = __ldg(&lut.pos[ee[u]]);
+              vvu[u] = lut_value<DT>(lut, ee[u]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+          if (ee[u] < 0) continue;
+          const int2 rec = make_int2(0, sv[u]);
+          const uint32_t pp = ppu[u];
+          const float2 v = vvu[u];
           const int lev = (pp >> 24) & 7;
           const int2 bs = S.sb[rec.y * (L + 1) + lev];
           const int m = L - lev;
@@ -369,6 +390,7 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
             atomicAdd(&S.acc[ai].x, amp * v.x);
             atomicAdd(&S.acc[ai].y, amp * v.y);
           }
+          }
         }
       }
       __syncthreads();
@@ -379,19 +401,26 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
     // buffer; slots of levels finer than lmin are zero.
     const float dq = ldexpf(1.0f, -sh);
     constexpr int Q4 = TSL / 2;  // float4 per tile
-    for (int g = tid; g < kx * ky * Q4; g += NT) {
-      const int tt = g / Q4, q = g - tt * Q4;  // Q4 is a power of two
-      const int j = tt / kx, t = tt - j * kx;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (2 * q < SL) {
-        const int src = (((j * k + t) << SLsh) >> 1) + q;
-        v = acc4[src];
-        if (fixed) {
-          const int4 iv = reinterpret_cast<const int4*>(acc4)[src];
-          v = make_float4((float)iv.x * dq, (float)iv.y * dq, (float)iv.z * dq, (float)iv.w * dq);
+    const int tpg = NT >= Q4 ? NT / Q4 : 1;  // tiles per pass
+    const int qstep = NT >= Q4 ? Q4 : NT;
+    int j = 0, t = NT >= Q4 ? tid / Q4 : 0;  // this thread's tile (row j, column t)
+    while (t >= kx) { t -= kx; ++j; }
+    while (j < ky) {
+      float4* dst = reinterpret_cast<float4*>(a.wbuf + ((size_t)(Sy + j) * a.ntx + Sx + t) * TSL);
+      const int src0 = ((j * k + t) << SLsh) >> 1;
+      for (int q = NT >= Q4 ? tid % Q4 : tid; q < Q4; q += qstep) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (2 * q < SL) {
+          v = acc4[src0 + q];
+          if (fixed) {
+            const int4 iv = reinterpret_cast<const int4*>(acc4)[src0 + q];
+            v = make_float4((float)iv.x * dq, (float)iv.y * dq, (float)iv.z * dq, (float)iv.w * dq);
+          }
         }
+        __stcs(dst + q, v);
       }
-      __stcs(reinterpret_cast<float4*>(a.wbuf + ((size_t)(Sy + j) * a.ntx + Sx + t) * TSL) + q, v);
+      t += tpg;
+      while (t >= kx) { t -= kx; ++j; }
     }
     PT_MARK(5);
   }
