@@ -32,8 +32,8 @@ from workloads import CONFIGS  # noqa: E402
 
 METRIC = "WASABI hologram Mpoint*coeff/s at 65536^2 (hologram s, HBM fraction)"
 UNIT = "Mpoint*coeff/s"
-KERNELS_PER_STEP = 11  # psf_haar, select, tile_count, tile_scan, scatter, quantize,
-#                        count, scan, scatter_points, superpose, inverse
+KERNELS_PER_STEP = 13  # psf_haar, select, tile_count, tile_scan, scatter, quantize,
+#                        init_single, zero, count, scan, scatter_points, superpose, inverse
 
 
 def _peaks():

@@ -188,6 +188,57 @@ wasabi_status wasabi_superpose_static(const wasabi_lut* lut, const wasabi_point*
 wasabi_status wasabi_inverse_haar(const void* wbuf_dev, int holo_w, int holo_h, int levels,
                                   void* u_dev, uint8_t* bits_dev, void* stream);
 
+/* ---- Batches: many holograms through one launch sequence (A10) ----------
+ * One job = one hologram with its own points, wavelet buffer and outputs, all
+ * sharing the LUT.  A batch runs every job through six launches (binning:
+ * zero, count, scan, scatter; superposition; inverse) whose grids do not
+ * depend on the batch; work items (super-tiles, strips) are claimed from a
+ * device-side job table.  With use_graph, the job-table upload and the six
+ * launches are captured into a CUDA graph on the first run on a stream and
+ * replayed by later runs (not on the legacy default stream).
+ * The batch object owns pinned host staging and the device job table; the
+ * caller owns the jobs' buffers and the scratch.  A run returns as soon as the
+ * work is enqueued; a later run on the same batch object first waits for the
+ * previous job-table upload. */
+typedef struct {
+  const wasabi_point* points_dev; /* n points (device) */
+  int64_t n;
+  int holo_w, holo_h;             /* multiples of 2^L; holo_w % 8 == 0 for bits */
+  int rule;                       /* wasabi_shift_rule */
+  void* wbuf_dev;                 /* tile-major wavelet buffer, holo_w * holo_h complex64, 256-B aligned */
+  void* u_dev;                    /* complex64 row-major output, or NULL */
+  uint8_t* bits_dev;              /* packed bits output, or NULL (both NULL: wavelet buffer only) */
+} wasabi_job;
+
+typedef struct wasabi_batch wasabi_batch;
+
+/* max_jobs <= 1024.  holo_side_hint picks the autotuned (or default)
+ * superposition configuration of that size class for the whole batch. */
+wasabi_status wasabi_batch_create(const wasabi_lut* lut, int max_jobs, int holo_side_hint, int use_graph,
+                                  wasabi_batch** out);
+/* Waits for the batch's last job-table upload, then frees it. */
+wasabi_status wasabi_batch_destroy(wasabi_batch* batch);
+/* The batch's super-tile side (pixels) and block size. */
+wasabi_status wasabi_batch_config(const wasabi_batch* batch, int* cell_out, int* threads_out);
+wasabi_status wasabi_batch_scratch_bytes(const wasabi_batch* batch, const wasabi_job* jobs_host, int njobs,
+                                         size_t* bytes_out);
+/* Superposition (Eq. (2)) and, for jobs that ask for it, inverse transform
+ * and binarisation (Sec. 1 step 3, Sec. 2) of every job; results equal the
+ * one-job calls.  jobs_host: njobs descriptors (host memory, read during the
+ * call).  E_INVALID / E_NOMEM on bad jobs or short scratch; device-side errors
+ * go to the status word. */
+wasabi_status wasabi_batch_run(wasabi_batch* batch, const wasabi_job* jobs_host, int njobs, void* scratch_dev,
+                               size_t scratch_bytes, void* stream);
+
+/* Autotuner: times the superposition of n synthetic points on a
+ * holo_side^2 hologram for super-tiles {64, 128, 256} x blocks {256, 384,
+ * 512} (those that fit), keeps the fastest in the LUT for that size class
+ * (holo_side rounded up to a power of two) and returns it.  Later
+ * superposition calls and batches of that class use it.  Synchronising;
+ * allocates temporary device memory. */
+wasabi_status wasabi_autotune(wasabi_lut* lut, int holo_side, int64_t n_points, void* stream, int* cell_out,
+                              int* threads_out);
+
 /* Eq. (1), the direct sum, on the GPU:
  *   u(x_h, y_h) = sum_j a_j exp(i 2 pi r_hj / lambda) [aperture],
  * r_hj = sqrt(((x_h - x_j)^2 + (y_h - y_j)^2) pitch^2 + z_{d_j}^2), with the

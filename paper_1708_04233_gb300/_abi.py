@@ -41,7 +41,20 @@ SIGNATURES = [
     ("wasabi_sync_status", _i, [_VP]),
     ("wasabi_haar_forward", _i, [_VP, _i, _i, _i, _VP, _VP]),
     ("wasabi_wbuf_to_mallat", _i, [_VP, _i, _i, _i, _VP, _VP]),
+    ("wasabi_batch_create", _i, [_VP, _i, _i, _i, C.POINTER(_VP)]),
+    ("wasabi_batch_destroy", _i, [_VP]),
+    ("wasabi_batch_config", _i, [_VP, C.POINTER(_i), C.POINTER(_i)]),
+    ("wasabi_batch_scratch_bytes", _i, [_VP, _VP, _i, C.POINTER(_sz)]),
+    ("wasabi_batch_run", _i, [_VP, _VP, _i, _VP, _sz, _VP]),
+    ("wasabi_autotune", _i, [_VP, _i, _i64, _VP, C.POINTER(_i), C.POINTER(_i)]),
 ]
+
+
+class Job(C.Structure):
+    """wasabi_job of include/wasabi.h."""
+    _fields_ = [("points_dev", C.c_void_p), ("n", C.c_int64), ("holo_w", C.c_int),
+                ("holo_h", C.c_int), ("rule", C.c_int), ("wbuf_dev", C.c_void_p),
+                ("u_dev", C.c_void_p), ("bits_dev", C.c_void_p)]
 
 _lib = None
 

@@ -202,6 +202,78 @@ def cgh_direct(lam: float, pitch: float, depths, points: torch.Tensor, w: int, h
     return u
 
 
+class Batch:
+    """Many holograms through one launch sequence (wasabi_batch_*).
+
+    A job is a dict: points (N x 4 int32 CUDA tensor), w, h, and optionally
+    rule, wbuf, want ("none" | "complex" | "bits" | "both"); run() allocates
+    missing buffers, returns the jobs with their wbuf / u / bits tensors and
+    keeps the scratch alive until the next run."""
+
+    def __init__(self, lut: Lut, max_jobs: int, side_hint: int = 4096, use_graph: bool = True):
+        self.lut = lut
+        self.max_jobs = max_jobs
+        h = C.c_void_p()
+        check(_lib().wasabi_batch_create(lut.handle, max_jobs, side_hint, int(use_graph), C.byref(h)))
+        self._h = h
+        self._keep = None
+
+    def config(self) -> tuple[int, int]:
+        c, t = C.c_int(), C.c_int()
+        check(_lib().wasabi_batch_config(self._h, C.byref(c), C.byref(t)))
+        return c.value, t.value
+
+    def run(self, jobs: list[dict], stream=None) -> list[dict]:
+        n = len(jobs)
+        arr = (_abi.Job * max(n, 1))()
+        out = []
+        for i, j in enumerate(jobs):
+            pts = j["points"]
+            dev = pts.device
+            w, h = j["w"], j["h"]
+            want = j.get("want", "bits")
+            wbuf = j.get("wbuf")
+            if wbuf is None:
+                wbuf = torch.empty(h * w, dtype=torch.complex64, device=dev)
+            u = j.get("u")
+            if u is None and want in ("complex", "both"):
+                u = torch.empty((h, w), dtype=torch.complex64, device=dev)
+            bits = j.get("bits")
+            if bits is None and want in ("bits", "both"):
+                bits = torch.empty((h * w + 7) // 8, dtype=torch.uint8, device=dev)
+            arr[i] = _abi.Job(pts.data_ptr() if pts.shape[0] else None, pts.shape[0], w, h,
+                              j.get("rule", 0), wbuf.data_ptr(),
+                              u.data_ptr() if u is not None else None,
+                              bits.data_ptr() if bits is not None else None)
+            out.append(dict(j, wbuf=wbuf, u=u, bits=bits))
+        need = C.c_size_t()
+        check(_lib().wasabi_batch_scratch_bytes(self._h, C.cast(arr, C.c_void_p), n, C.byref(need)))
+        dev = jobs[0]["points"].device if jobs else torch.device("cuda")
+        scratch = torch.empty(max(int(need.value), 256), dtype=torch.uint8, device=dev)
+        check(_lib().wasabi_batch_run(self._h, C.cast(arr, C.c_void_p), n, _ptr(scratch),
+                                      scratch.numel(), _stream(stream)))
+        self._keep = (scratch, out)
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            _lib().wasabi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(lut: Lut, side: int, n_points: int, stream=None) -> tuple[int, int]:
+    """Pick and store the fastest super-tile / block size for this size class."""
+    c, t = C.c_int(), C.c_int()
+    check(_lib().wasabi_autotune(lut.handle, side, n_points, _stream(stream), C.byref(c), C.byref(t)))
+    return c.value, t.value
+
+
 def sync_status(stream=None) -> None:
     """Wait for the stream and raise if a kernel recorded an error."""
     check(_lib().wasabi_sync_status(_stream(stream)))

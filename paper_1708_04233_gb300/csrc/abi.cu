@@ -15,10 +15,9 @@
 #include <cuda_fp16.h>
 
 #include "internal.cuh"
+#include "lut_object.h"
 
 namespace wsb {
-int superpose_max_cell_rows();
-int superpose_min_threads();
 int direct_max_cell_rows();
 }  // namespace wsb
 
@@ -42,6 +41,8 @@ int current_device() {
   cudaGetDevice(&dev);
   return dev;
 }
+
+}  // namespace
 
 // Status word address and SM count of the current device (looked up once).
 bool device_info(int** status, int* sms) {
@@ -67,6 +68,10 @@ bool device_info(int** status, int* sms) {
   }
   if (status) *status = g_status_ptr[dev];
   if (sms) *sms = g_num_sms[dev];
+  // Every entry point that launches passes through here first; its launch
+  // errors are read with cudaGetLastError, so an earlier, unrelated
+  // (non-sticky) error is cleared now.
+  cudaGetLastError();
   return true;
 }
 
@@ -75,7 +80,7 @@ wasabi_status cuda_fail(const char* what, cudaError_t e) {
   return WASABI_E_CUDA;
 }
 
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+namespace {
 
 // Support radius in pixels: z tan(asin(lambda / 2p)) / p.
 double support_radius(double lambda, double pitch, double z) {
@@ -110,70 +115,39 @@ int* device_status_ptr() {
 
 using namespace wsb;
 
-// ---------------------------------------------------------------- LUT object
-struct wasabi_lut {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  double lambda = 0, pitch = 0, gamma = 0;
-  int D = 0, W = 0, L = 0, nwt = 0, dtype = 0;
-  int reach = 0;  // pixels: footprint half-extent bound (max floor(R) + 2^(L+1))
-  std::vector<double> z, R;
-  std::vector<DepthMeta> meta;
-  long long total_cap = 0;
-  void* block = nullptr;  // one device allocation for all arrays below
-  uint32_t* pos = nullptr;
-  float2* val = nullptr;
-  uint32_t* val16 = nullptr;
-  float* scale = nullptr;
-  int32_t* tile_off = nullptr;
-  DepthMeta* meta_dev = nullptr;
-  long long* nr_dev = nullptr;
-  float* cmax = nullptr;
-  unsigned* levels = nullptr;  // bit l: a level-l coefficient is kept
-  int lmin = 1;                // finest kept level (host copy)
+namespace wsb {
 
-  LutView view() const {
-    LutView v;
-    v.D = D; v.W = W; v.L = L; v.nwt = nwt; v.dtype = dtype;
-    v.pos = pos; v.val = val; v.val16 = val16; v.scale = scale;
-    v.tile_off = tile_off; v.meta = meta_dev; v.cmax = cmax; v.lmin = lmin;
-    return v;
-  }
-};
-
-namespace {
-
-// Carves consecutive 256-byte-aligned regions out of one block.
-struct Carver {
-  size_t off = 0;
-  char* base = nullptr;
-  template <typename T>
-  T* take(size_t count) {
-    off = align_up(off, 256);
-    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
-    off += count * sizeof(T);
-    return p;
-  }
-};
-
-// Super-tile side and block size for a hologram (the autotuner's default).
 void superpose_config(const wasabi_lut* lut, int w, int h, int* cell, int* threads) {
-  int T = env_int("WASABI_SUPERPOSE_T", superpose_default_cell(lut->L, lut->lmin, lut->D));
-  int nt = env_int("WASABI_SUPERPOSE_THREADS", 512);
+  int T = superpose_default_cell(lut->L, lut->lmin, lut->D);
+  int nt = 512;
+  {
+    std::lock_guard<std::mutex> lk(lut->tune_mu);
+    const auto it = lut->tuned.find(size_class(w, h));
+    if (it != lut->tuned.end()) { T = it->second.first; nt = it->second.second; }
+  }
+  T = env_int("WASABI_SUPERPOSE_T", T);
+  nt = env_int("WASABI_SUPERPOSE_THREADS", nt);
   T = std::min(T, 256);
   T = std::max(T, std::max(1 << lut->L, 32));
   T = (T >> lut->L) << lut->L;
   while (T > std::max(1 << lut->L, 32) && superpose_smem_bytes(T, lut->L, lut->lmin, lut->D) > 220 * 1024) T >>= 1;
   nt = std::max(superpose_min_threads(), std::min(512, nt / 32 * 32));
-  (void)w; (void)h;
   *cell = T;
   *threads = nt;
 }
 
+}  // namespace wsb
+
+namespace {
+
+// Scratch of a one-job call: the job table, the batch totals, the cell
+// arrays and the binned points.
 struct BinLayout {
   int cell, ncx, ncy;
   size_t bytes;
-  int *cnt, *off, *cursor, *counter;
+  JobDev* jobs;
+  BatchDev* batch;
+  int *cnt, *off, *cursor;
   wasabi_point* sorted;
 };
 
@@ -185,14 +159,43 @@ BinLayout bin_layout(int64_t n, int w, int h, int cell, void* base) {
   const size_t ncells = (size_t)b.ncx * b.ncy;
   Carver c;
   c.base = static_cast<char*>(base);
+  b.jobs = c.take<JobDev>(1);
+  b.batch = c.take<BatchDev>(1);
   b.cnt = c.take<int>(ncells + 1);
   b.off = c.take<int>(ncells + 1);
   b.cursor = c.take<int>(ncells);
-  b.counter = c.take<int>(64);
   b.sorted = c.take<wasabi_point>((size_t)std::max<int64_t>(n, 1));
   b.bytes = align_up(c.off, 256);
   return b;
 }
+
+// Device address of a field of the device-resident batch totals.
+template <typename T>
+T* batch_field(BatchDev* b, size_t offset) {
+  return reinterpret_cast<T*>(reinterpret_cast<char*>(b) + offset);
+}
+
+JobDev make_job(const wasabi_lut* lut, const wasabi_point* pts, int64_t n, int w, int h, int rule,
+                int cell, float2* wbuf, float2* u, uint8_t* bits) {
+  JobDev J;
+  std::memset(&J, 0, sizeof J);
+  J.pts = pts;
+  J.wbuf = wbuf;
+  J.u = u;
+  J.bits = bits;
+  J.n = n;
+  J.w = w;
+  J.h = h;
+  J.ntx = w >> lut->L;
+  J.nty = h >> lut->L;
+  J.ncx = (w + cell - 1) / cell;
+  J.ncy = (h + cell - 1) / cell;
+  J.ncells = J.ncx * J.ncy;
+  J.rule = rule;
+  return J;
+}
+
+int super_tiles(int ntx, int nty, int k) { return ((ntx + k - 1) / k) * ((nty + k - 1) / k); }
 
 }  // namespace
 
@@ -535,6 +538,18 @@ wasabi_status wasabi_scratch_bytes(const wasabi_lut* lut, int64_t n, int holo_w,
 wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n, int holo_w,
                                int holo_h, int rule, void* wbuf_dev, void* scratch_dev, size_t scratch_bytes,
                                void* stream) {
+  if (!lut) { set_error("superpose: NULL argument"); return WASABI_E_INVALID; }
+  int cell, threads;
+  superpose_config(lut, holo_w, holo_h, &cell, &threads);
+  return superpose_impl(lut, points_dev, n, holo_w, holo_h, rule, wbuf_dev, scratch_dev, scratch_bytes,
+                        (cudaStream_t)stream, cell, threads);
+}
+
+}  // extern "C"
+
+wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n, int holo_w,
+                                  int holo_h, int rule, void* wbuf_dev, void* scratch_dev, size_t scratch_bytes,
+                                  cudaStream_t stream, int cell, int threads) {
   if (!lut || n < 0 || (n > 0 && !points_dev) || !wbuf_dev || !scratch_dev) {
     set_error("superpose: NULL argument");
     return WASABI_E_INVALID;
@@ -550,8 +565,11 @@ wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points
   int* status;
   int sms;
   if (!device_info(&status, &sms)) return WASABI_E_CUDA;
-  int cell, threads;
-  superpose_config(lut, holo_w, holo_h, &cell, &threads);
+  if (cell < std::max(1 << lut->L, 32) || cell > 256 || cell % (1 << lut->L) ||
+      threads < superpose_min_threads() || threads > 512 || threads % 32) {
+    set_error("superpose: bad configuration (super-tile %d, %d threads)", cell, threads);
+    return WASABI_E_INVALID;
+  }
   BinLayout b = bin_layout(n, holo_w, holo_h, cell, scratch_dev);
   size_t need = 0;
   wasabi_scratch_bytes(lut, n, holo_w, holo_h, &need);
@@ -561,33 +579,30 @@ wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points
   }
   const int rows = (cell + 2 * lut->reach) / cell + 2;
   if (rows > superpose_max_cell_rows()) { set_error("superpose: window too large for the super-tile"); return WASABI_E_INVALID; }
+  const size_t smem = superpose_smem_bytes(cell, lut->L, lut->lmin, lut->D);
+  if (smem > 220 * 1024) { set_error("superpose: super-tile %d needs %zu B of shared memory", cell, smem); return WASABI_E_INVALID; }
   const cudaStream_t s = (cudaStream_t)stream;
+  JobDev J = make_job(lut, points_dev, n, holo_w, holo_h, rule, cell, static_cast<float2*>(wbuf_dev),
+                      nullptr, nullptr);
+  J.sorted = b.sorted; J.cnt = b.cnt; J.off = b.off; J.cursor = b.cursor;
+  cudaError_t e = launch_init_single(J, b.jobs, b.batch, super_tiles(J.ntx, J.nty, cell >> lut->L), 0, s);
+  if (e != cudaSuccess) return cuda_fail("superpose: init", e);
   BinArgs ba;
-  ba.pts = points_dev; ba.n = n; ba.D = lut->D; ba.w = holo_w; ba.h = holo_h; ba.cell = cell;
-  ba.ncx = b.ncx; ba.ncy = b.ncy; ba.reach = lut->reach;
-  ba.cnt = b.cnt; ba.off = b.off; ba.cursor = b.cursor; ba.sorted = b.sorted; ba.status = status;
-  ba.amax = reinterpret_cast<float*>(b.counter + 1);
-  cudaError_t e = cudaMemsetAsync(b.counter, 0, 32 * sizeof(int), s);  // counter, amax, timers
-  if (e != cudaSuccess) return cuda_fail("superpose: memset", e);
+  ba.jobs = b.jobs; ba.batch = b.batch; ba.D = lut->D; ba.cell = cell; ba.reach = lut->reach;
+  ba.track_amax = 1; ba.status = status;
+  ba.grid = sms * 4;
   e = launch_binning(ba, s);
   if (e != cudaSuccess) return cuda_fail("superpose: binning", e);
   SuperposeArgs sa;
   sa.lut = lut->view();
-  sa.sorted = b.sorted; sa.cell_off = b.off; sa.ncx = b.ncx; sa.ncy = b.ncy; sa.cell = cell;
-  sa.w = holo_w; sa.h = holo_h; sa.ntx = holo_w >> lut->L; sa.nty = holo_h >> lut->L;
-  sa.rule = rule; sa.reach = lut->reach; sa.counter = b.counter;
-  sa.amax = ba.amax;
-  sa.timers = reinterpret_cast<unsigned long long*>(b.counter + 16);
+  sa.jobs = b.jobs; sa.batch = b.batch; sa.cell = cell; sa.reach = lut->reach;
   sa.acc_float = env_int("WASABI_ACC_FLOAT", 0) != 0;
-  sa.wbuf = static_cast<float2*>(wbuf_dev); sa.status = status; sa.threads = threads;
-  sa.nst = (long long)((sa.ntx + (cell >> lut->L) - 1) / (cell >> lut->L)) *
-           ((sa.nty + (cell >> lut->L) - 1) / (cell >> lut->L));
-  const size_t smem = superpose_smem_bytes(cell, lut->L, lut->lmin, lut->D);
-  if (smem > 220 * 1024) { set_error("superpose: super-tile %d needs %zu B of shared memory", cell, smem); return WASABI_E_INVALID; }
-  sa.grid = sms;
+  sa.status = status; sa.threads = threads; sa.grid = sms;
   e = launch_superpose(sa, s);
   return e == cudaSuccess ? WASABI_OK : cuda_fail("superpose: launch", e);
 }
+
+extern "C" {
 
 wasabi_status wasabi_inverse_haar(const void* wbuf_dev, int holo_w, int holo_h, int levels, void* u_dev,
                                   uint8_t* bits_dev, void* stream) {
@@ -606,8 +621,22 @@ wasabi_status wasabi_inverse_haar(const void* wbuf_dev, int holo_w, int holo_h, 
   int* status;
   int sms;
   if (!device_info(&status, &sms)) return WASABI_E_CUDA;
-  const cudaError_t e = launch_inverse(static_cast<const float2*>(wbuf_dev), holo_w, holo_h, levels,
-                                       static_cast<float2*>(u_dev), bits_dev, status, sms, (cudaStream_t)stream);
+  InverseArgs ia;
+  std::memset(&ia, 0, sizeof ia);
+  ia.jobs = nullptr;
+  ia.batch = nullptr;
+  ia.job0.wbuf = const_cast<float2*>(static_cast<const float2*>(wbuf_dev));
+  ia.job0.u = static_cast<float2*>(u_dev);
+  ia.job0.bits = bits_dev;
+  ia.job0.w = holo_w;
+  ia.job0.h = holo_h;
+  ia.job0.ntx = holo_w >> levels;
+  ia.job0.nty = holo_h >> levels;
+  ia.ninv0 = inverse_strips(holo_w, holo_h, levels);
+  ia.L = levels;
+  ia.status = status;
+  ia.num_sms = sms;
+  const cudaError_t e = launch_inverse(ia, (cudaStream_t)stream);
   return e == cudaSuccess ? WASABI_OK : cuda_fail("inverse_haar: launch", e);
 }
 
@@ -671,20 +700,24 @@ wasabi_status cgh_direct(double lambda, double pitch, const double* depths_host,
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail("cgh_direct: upload", e);
   const int reach = aperture ? (int)std::floor(Rmax) + 1 : (INT_MAX / 4);
+  JobDev J;
+  std::memset(&J, 0, sizeof J);
+  J.pts = points_dev; J.sorted = b.sorted; J.cnt = b.cnt; J.off = b.off; J.cursor = b.cursor;
+  J.n = n; J.w = holo_w; J.h = holo_h; J.ncx = b.ncx; J.ncy = b.ncy; J.ncells = b.ncx * b.ncy;
+  e = launch_init_single(J, b.jobs, b.batch, 0, 0, s);
+  if (e != cudaSuccess) return cuda_fail("cgh_direct: init", e);
   BinArgs ba;
-  ba.pts = points_dev; ba.n = n; ba.D = n_depths; ba.w = holo_w; ba.h = holo_h; ba.cell = cell;
-  ba.ncx = b.ncx; ba.ncy = b.ncy; ba.reach = reach;
-  ba.cnt = b.cnt; ba.off = b.off; ba.cursor = b.cursor; ba.sorted = b.sorted; ba.status = status;
-  ba.amax = nullptr;
-  e = launch_binning(ba, s);
+  ba.jobs = b.jobs; ba.batch = b.batch; ba.D = n_depths; ba.cell = cell; ba.reach = reach;
+  ba.track_amax = 0; ba.status = status;
+  ba.grid = sms * 4;
+  e = launch_binning(ba, s);  // also zeroes the tile counter
   if (e != cudaSuccess) return cuda_fail("cgh_direct: binning", e);
-  e = cudaMemsetAsync(b.counter, 0, sizeof(int), s);
-  if (e != cudaSuccess) return cuda_fail("cgh_direct: memset", e);
   DirectArgs da;
-  da.lambda = lambda; da.pitch = pitch; da.sorted = b.sorted; da.cell_off = b.off;
-  da.ncx = b.ncx; da.ncy = b.ncy; da.cell = cell; da.w = holo_w; da.h = holo_h; da.D = n_depths;
+  da.lambda = lambda; da.pitch = pitch; da.jobs = b.jobs;
+  da.cell = cell; da.w = holo_w; da.h = holo_h; da.D = n_depths;
   da.beta_dev = beta_dev; da.nlim_dev = nlim_dev; da.alpha = pl * pl; da.reach = reach;
-  da.counter = b.counter; da.u = static_cast<float2*>(u_dev); da.status = status;
+  da.counter = batch_field<int>(b.batch, offsetof(BatchDev, counter));
+  da.u = static_cast<float2*>(u_dev); da.status = status;
   const long long ntiles = (long long)((holo_w + 31) / 32) * ((holo_h + 31) / 32);
   da.grid = (int)std::min<long long>(ntiles, (long long)sms * 8);
   e = launch_direct(da, s);

@@ -1,12 +1,14 @@
 // Point preparation and spatial binning.
 //
 // quantize_kernel: depth index per point (Sec. 1, step 1 depth discretisation).
-// Binning (count -> scan -> scatter): points are grouped by the cell x cell
-// pixel cell that holds them, cells row-major, so that a consumer working on
-// one region reads each row of nearby cells as one contiguous range.  Points
-// whose footprint cannot reach the hologram (more than `reach` pixels
-// outside it) and points with an invalid depth are left out; the latter
-// record WASABI_E_RANGE.
+// Binning of a batch of holograms (zero -> count -> scan -> scatter): each
+// job's points are grouped by the cell x cell pixel cell that holds them,
+// cells row-major, so that a consumer working on one region reads each row of
+// nearby cells as one contiguous range.  Points whose footprint cannot reach
+// their hologram (more than `reach` pixels outside it) and points with an
+// invalid depth are left out; the latter record WASABI_E_RANGE.  All sizes
+// are read from the device-side batch tables, so the launch shapes do not
+// depend on the batch.
 #include "internal.cuh"
 
 namespace wsb {
@@ -36,89 +38,135 @@ __global__ void quantize_kernel(const int32_t* __restrict__ x, const int32_t* __
   out[i] = p;
 }
 
-struct CellOf {
-  int w, h, cell, ncx, reach, D;
-  // Cell of a point, or -1 if the point is left out.
-  __device__ __forceinline__ int operator()(const wasabi_point& p) const {
-    if (p.d >= (uint32_t)D) return -1;
-    if (p.x < -reach || p.x >= w + reach || p.y < -reach || p.y >= h + reach) return -1;
-    const int cx = min(max(p.x, 0), w - 1) / cell;
-    const int cy = min(max(p.y, 0), h - 1) / cell;
-    return cy * ncx + cx;
-  }
-};
+__global__ void init_single_kernel(JobDev job, JobDev* jobs, BatchDev* b, int nsp, int ninv) {
+  jobs[0] = job;
+  b->njobs = 1;
+  b->nsp = nsp;
+  b->ninv = ninv;
+  b->npts = job.n;
+}
 
-__global__ void count_kernel(BinArgs b, CellOf cf) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= b.n) return;
-  const wasabi_point p = b.pts[i];
-  if (p.d >= (uint32_t)b.D) atomicCAS(b.status, 0, WASABI_E_RANGE);
-  const int c = cf(p);
-  if (c >= 0) {
-    atomicAdd(&b.cnt[c], 1);
-    // Non-negative floats order like their bit patterns.
-    if (b.amax) atomicMax(reinterpret_cast<int*>(b.amax), __float_as_int(fabsf(p.a)));
+// Cell of a point of job J, or -1 if the point is left out.
+__device__ __forceinline__ int cell_of(const JobDev& J, const wasabi_point& p, int cell, int reach, int D) {
+  if (p.d >= (uint32_t)D) return -1;
+  if (p.x < -reach || p.x >= J.w + reach || p.y < -reach || p.y >= J.h + reach) return -1;
+  const int cx = min(max(p.x, 0), J.w - 1) / cell;
+  const int cy = min(max(p.y, 0), J.h - 1) / cell;
+  return cy * J.ncx + cx;
+}
+
+// Zeroes every job's cell counts (sizes from the job table) and the batch's
+// counters.
+__global__ void zero_kernel(BinArgs b) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int nj = b.batch->njobs;
+  for (int j = 0; j < nj; ++j) {
+    const JobDev& J = b.jobs[j];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= J.ncells; i += stride)
+      J.cnt[i] = 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    b.batch->counter = 0;
+    b.batch->amax = 0.f;
+    for (int t = 0; t < 6; ++t) b.batch->timers[t] = 0;
   }
 }
 
-// Single-block exclusive scan of ncells counts into off[0..ncells] and
-// cursor[0..ncells): chunks of 4096 counts, each thread a coalesced int4,
-// one block scan per chunk, a running carry between chunks.
-__global__ void __launch_bounds__(1024) scan_kernel(BinArgs b, int ncells) {
+// Loads the jobs' first-point indices into shared memory.
+__device__ __forceinline__ int load_pt0(const BinArgs& b, long long* spt0) {
+  const int nj = min(b.batch->njobs, kMaxJobs);
+  for (int j = threadIdx.x; j < nj; j += blockDim.x) spt0[j] = b.jobs[j].pt0;
+  __syncthreads();
+  return nj;
+}
+
+__global__ void __launch_bounds__(256) count_kernel(BinArgs b) {
+  __shared__ long long spt0[kMaxJobs];
+  const int nj = load_pt0(b, spt0);
+  const long long npts = b.batch->npts;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < npts; g += stride) {
+    const JobDev& J = b.jobs[job_of(spt0, nj, g)];
+    const wasabi_point p = J.pts[g - J.pt0];
+    if (p.d >= (uint32_t)b.D) atomicCAS(b.status, 0, WASABI_E_RANGE);
+    const int c = cell_of(J, p, b.cell, b.reach, b.D);
+    if (c >= 0) {
+      atomicAdd(&J.cnt[c], 1);
+      // Non-negative floats order like their bit patterns.
+      if (b.track_amax) atomicMax(reinterpret_cast<int*>(&b.batch->amax), __float_as_int(fabsf(p.a)));
+    }
+  }
+}
+
+// Exclusive scan of each job's cell counts into off[0..ncells] and
+// cursor[0..ncells): one block per job at a time, chunks of 4096 counts, each
+// thread a coalesced group of four, a running carry between chunks.
+__global__ void __launch_bounds__(1024) scan_kernel(BinArgs b) {
   __shared__ unsigned warp_sum[32];
   __shared__ unsigned s_carry;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  for (int base = 0; base < ncells; base += 4096) {
-    const int i0 = base + 4 * threadIdx.x;
-    int c[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) c[j] = i0 + j < ncells ? b.cnt[i0 + j] : 0;
-    const unsigned local = (unsigned)(c[0] + c[1] + c[2] + c[3]);
-    unsigned x = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sum[wid] = x;
+  const int nj = b.batch->njobs;
+  for (int j = blockIdx.x; j < nj; j += gridDim.x) {
+    const JobDev& J = b.jobs[j];
+    const int ncells = J.ncells;
+    if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
-    if (wid == 0) {
-      unsigned w = warp_sum[lane];
+    for (int base = 0; base < ncells; base += 4096) {
+      const int i0 = base + 4 * threadIdx.x;
+      int c[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[q] = i0 + q < ncells ? J.cnt[i0 + q] : 0;
+      const unsigned local = (unsigned)(c[0] + c[1] + c[2] + c[3]);
+      unsigned x = local;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
-      warp_sum[lane] = w;
-    }
-    __syncthreads();
-    const unsigned carry = s_carry;
-    unsigned run = carry + (wid ? warp_sum[wid - 1] : 0u) + x - local;
+      if (lane == 31) warp_sum[wid] = x;
+      __syncthreads();
+      if (wid == 0) {
+        unsigned w = warp_sum[lane];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (i0 + j < ncells) {
-        b.off[i0 + j] = (int)run;
-        b.cursor[i0 + j] = (int)run;
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+          if (lane >= o) w += y;
+        }
+        warp_sum[lane] = w;
       }
-      run += (unsigned)c[j];
+      __syncthreads();
+      const unsigned carry = s_carry;
+      unsigned run = carry + (wid ? warp_sum[wid - 1] : 0u) + x - local;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (i0 + q < ncells) {
+          J.off[i0 + q] = (int)run;
+          J.cursor[i0 + q] = (int)run;
+        }
+        run += (unsigned)c[q];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_carry = carry + warp_sum[31];
+      __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) s_carry = carry + warp_sum[31];
+    if (threadIdx.x == 0) J.off[ncells] = (int)s_carry;
     __syncthreads();
   }
-  if (threadIdx.x == 0) b.off[ncells] = (int)s_carry;
 }
 
-__global__ void scatter_points_kernel(BinArgs b, CellOf cf) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= b.n) return;
-  const wasabi_point p = b.pts[i];
-  const int c = cf(p);
-  if (c < 0) return;
-  const int slot = atomicAdd(&b.cursor[c], 1);
-  b.sorted[slot] = p;
+__global__ void __launch_bounds__(256) scatter_points_kernel(BinArgs b) {
+  __shared__ long long spt0[kMaxJobs];
+  const int nj = load_pt0(b, spt0);
+  const long long npts = b.batch->npts;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < npts; g += stride) {
+    const JobDev& J = b.jobs[job_of(spt0, nj, g)];
+    const wasabi_point p = J.pts[g - J.pt0];
+    const int c = cell_of(J, p, b.cell, b.reach, b.D);
+    if (c < 0) continue;
+    const int slot = atomicAdd(&J.cursor[c], 1);
+    J.sorted[slot] = p;
+  }
 }
 
 }  // namespace
@@ -132,23 +180,23 @@ cudaError_t launch_quantize(const int32_t* x, const int32_t* y, const double* z,
   return cudaGetLastError();
 }
 
+cudaError_t launch_init_single(const JobDev& job, JobDev* jobs_dev, BatchDev* batch_dev, int nsp,
+                               int ninv, cudaStream_t s) {
+  init_single_kernel<<<1, 1, 0, s>>>(job, jobs_dev, batch_dev, nsp, ninv);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_binning(const BinArgs& b, cudaStream_t s) {
-  const int ncells = b.ncx * b.ncy;
-  const CellOf cf{b.w, b.h, b.cell, b.ncx, b.reach, b.D};
-  cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * (size_t)(ncells + 1), s);
+  const unsigned grid = (unsigned)(b.grid > 0 ? b.grid : 1);
+  zero_kernel<<<grid, 256, 0, s>>>(b);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)((b.n + 255) / 256);
-  if (b.n > 0) {
-    count_kernel<<<grid, 256, 0, s>>>(b, cf);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  scan_kernel<<<1, 1024, 0, s>>>(b, ncells);
+  count_kernel<<<grid, 256, 0, s>>>(b);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (b.n > 0) {
-    scatter_points_kernel<<<grid, 256, 0, s>>>(b, cf);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  scan_kernel<<<(unsigned)(b.grid > 0 ? (b.grid + 7) / 8 : 1), 1024, 0, s>>>(b);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  scatter_points_kernel<<<grid, 256, 0, s>>>(b);
+  return cudaGetLastError();
 }
 
 }  // namespace wsb

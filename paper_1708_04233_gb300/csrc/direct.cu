@@ -34,6 +34,10 @@ __global__ void __launch_bounds__(kNT) direct_kernel(DirectArgs a) {
   __shared__ int s_tile, s_n, s_nrows, s_total;
   __shared__ int s_rowstart[kMaxRows], s_rowpre[kMaxRows + 1];
   const int tid = threadIdx.x;
+  const JobDev& J = a.jobs[0];
+  const int ncx = J.ncx, ncy = J.ncy;
+  const int* cell_off = J.off;
+  const wasabi_point* sorted = J.sorted;
   const int ntx = (a.w + kTile - 1) / kTile, nty = (a.h + kTile - 1) / kTile;
   const int ntiles = ntx * nty;
   const int col = tid & 31, row0 = tid >> 5;  // pixels (col, row0 + 8 q), q < 4
@@ -47,18 +51,18 @@ __global__ void __launch_bounds__(kNT) direct_kernel(DirectArgs a) {
     const int X1 = min(X0 + kTile, a.w), Y1 = min(Y0 + kTile, a.h);
 
     const int cx0 = max(0, floor_div(X0 - a.reach, a.cell));
-    const int cx1 = min(a.ncx - 1, floor_div(X1 - 1 + a.reach, a.cell));
+    const int cx1 = min(ncx - 1, floor_div(X1 - 1 + a.reach, a.cell));
     const int cy0 = max(0, floor_div(Y0 - a.reach, a.cell));
-    const int cy1 = min(a.ncy - 1, floor_div(Y1 - 1 + a.reach, a.cell));
+    const int cy1 = min(ncy - 1, floor_div(Y1 - 1 + a.reach, a.cell));
     if (tid == 0) {
       const int nrows = (cx0 <= cx1 && cy0 <= cy1) ? cy1 - cy0 + 1 : 0;
       int run = 0;
       for (int r = 0; r < nrows; ++r) {
-        const int c0 = (cy0 + r) * a.ncx;
-        const int s0 = a.cell_off[c0 + cx0];
+        const int c0 = (cy0 + r) * ncx;
+        const int s0 = cell_off[c0 + cx0];
         s_rowstart[r] = s0;
         s_rowpre[r] = run;
-        run += a.cell_off[c0 + cx1 + 1] - s0;
+        run += cell_off[c0 + cx1 + 1] - s0;
       }
       s_rowpre[nrows] = run;
       s_nrows = nrows;
@@ -75,7 +79,7 @@ __global__ void __launch_bounds__(kNT) direct_kernel(DirectArgs a) {
       if (i < total) {
         int r = 0;
         while (r + 1 < nrows && s_rowpre[r + 1] <= i) ++r;
-        const int4 p = __ldg(reinterpret_cast<const int4*>(a.sorted) + s_rowstart[r] + (i - s_rowpre[r]));
+        const int4 p = __ldg(reinterpret_cast<const int4*>(sorted) + s_rowstart[r] + (i - s_rowpre[r]));
         const long long nlim = __ldg(&a.nlim_dev[p.w]);
         const long long ddx = p.x < X0 ? X0 - p.x : (p.x > X1 - 1 ? p.x - (X1 - 1) : 0);
         const long long ddy = p.y < Y0 ? Y0 - p.y : (p.y > Y1 - 1 ? p.y - (Y1 - 1) : 0);

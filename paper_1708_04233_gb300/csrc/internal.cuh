@@ -111,63 +111,113 @@ cudaError_t launch_quantize(const int32_t* x, const int32_t* y, const double* z,
                             int64_t n, double zmin, double zmax, double dz, int D,
                             wasabi_point* out, int* status, cudaStream_t s);
 
+// ------------------------------------------------------------------- batches
+// A batch is a table of holograms ("jobs") processed by one fixed-shape
+// launch sequence: zero -> count -> scan -> scatter (binning) -> superpose ->
+// inverse.  Everything that varies between batches lives in device memory
+// (the job table and the BatchDev totals), so the sequence can be captured
+// once in a CUDA graph and replayed; a single hologram is a batch of one.
+constexpr int kMaxJobs = 1024;
+
+struct JobDev {
+  const wasabi_point* pts;  // input points (n)
+  wasabi_point* sorted;     // binned points (n), scratch
+  int* cnt;                 // ncells + 1 cell counts, scratch (zeroed by zero_kernel)
+  int* off;                 // ncells + 1 cell offsets, scratch
+  int* cursor;              // ncells scatter cursors, scratch
+  float2* wbuf;             // tile-major wavelet buffer (w * h)
+  float2* u;                // inverse output, complex row-major (or null)
+  uint8_t* bits;            // inverse output, packed bits (or null)
+  long long n;              // points
+  long long pt0;            // first point of this job in the batch's point numbering
+  int w, h, ntx, nty;       // pixels and 2^L x 2^L tiles
+  int ncx, ncy;             // binning cells of cell x cell pixels
+  int rule;                 // shift rule
+  int sp0;                  // first superposition item (super-tile) of this job
+  int inv0;                 // first inverse item (strip) of this job
+  int ncells;               // ncx * ncy
+};
+
+struct BatchDev {
+  int njobs;
+  int nsp;                  // superposition items (super-tiles) over all jobs
+  int ninv;                 // inverse items (strips) over all jobs
+  int pad;
+  long long npts;           // points over all jobs
+  int counter;              // superposition work counter (zeroed by zero_kernel)
+  float amax;               // largest |a| over binned points (zeroed by zero_kernel)
+  unsigned long long timers[6];  // phase cycle counters (profiling builds only)
+};
+
+// Index of the job holding `item`: binary search over the jobs' first items.
+template <typename T>
+__device__ __forceinline__ int job_of(const T* starts, int njobs, T item) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 struct BinArgs {
-  const wasabi_point* pts;
-  int64_t n;
+  const JobDev* jobs;       // device job table
+  BatchDev* batch;          // device totals
   int D;
-  int w, h;        // hologram pixels
-  int cell;        // cell side (pixels)
-  int ncx, ncy;
-  int reach;       // pixels: a point farther than this outside the hologram is dropped
-  int* cnt;        // ncells + 1 (zeroed here)
-  float* amax;     // largest |a| of the binned points (zeroed by caller)
-  int* off;        // ncells + 1
-  int* cursor;     // ncells
-  wasabi_point* sorted;
+  int cell;                 // cell side (pixels)
+  int reach;                // pixels: a point farther than this outside the hologram is dropped
+  int track_amax;           // record the largest |a| (superposition uses it)
   int* status;
+  int grid;                 // blocks of the grid-stride kernels
 };
 cudaError_t launch_binning(const BinArgs& b, cudaStream_t s);
 
 struct SuperposeArgs {
   LutView lut;
-  const wasabi_point* sorted;
-  const int* cell_off;
-  int ncx, ncy, cell;   // cell == super-tile side T (pixels)
-  int w, h, ntx, nty;
-  int rule;
+  const JobDev* jobs;
+  BatchDev* batch;
+  int cell;             // super-tile side T (pixels) == binning cell
   int reach;            // pixels
-  int* counter;         // zeroed by caller
-  const float* amax;    // largest |a| of the binned points
   int acc_float;        // 0: exact fixed-point accumulation, 1: FP32 atomics
-  unsigned long long* timers;  // 6 phase cycle counters (profiling builds only)
-  float2* wbuf;
   int* status;
   int threads;          // block size
   int grid;             // SMs: the launch puts as many CTAs on each as fit
-  long long nst;        // super-tiles
 };
 cudaError_t launch_superpose(const SuperposeArgs& a, cudaStream_t s);
 size_t superpose_smem_bytes(int cell, int L, int lmin, int D);
 int superpose_default_cell(int L, int lmin, int D);
 
-cudaError_t launch_inverse(const float2* wbuf, int w, int h, int L, float2* u, uint8_t* bits,
-                           int* status, int num_sms, cudaStream_t s);
+struct InverseArgs {
+  const JobDev* jobs;       // device job table, or null: job0 is the only job
+  const BatchDev* batch;    // totals (with a job table)
+  JobDev job0;              // the job of a one-job call (kernel parameter)
+  int ninv0;                // its strips
+  int L;
+  int* status;
+  int num_sms;
+};
+cudaError_t launch_inverse(const InverseArgs& a, cudaStream_t s);
+// Strips of one hologram as the inverse kernel cuts it (256 pixels x 2^L rows).
+int inverse_strips(int w, int h, int L);
+
+// Writes one job and the batch totals of a one-job batch into device memory.
+cudaError_t launch_init_single(const JobDev& job, JobDev* jobs_dev, BatchDev* batch_dev, int nsp,
+                               int ninv, cudaStream_t s);
 cudaError_t launch_haar_forward(const float2* u, int w, int h, int L, float2* wbuf, cudaStream_t s);
 cudaError_t launch_wbuf_to_mallat(const float2* wbuf, int w, int h, int L, float2* out,
                                   cudaStream_t s);
 
 struct DirectArgs {
   double lambda, pitch;
-  const wasabi_point* sorted;
-  const int* cell_off;
-  int ncx, ncy, cell;
+  const JobDev* jobs;   // one job: its binned points and cells
+  int cell;
   int w, h;
   int D;
   const double* beta_dev;     // D: (z_d / lambda)^2
   const long long* nlim_dev;  // D: ceil(R_d^2) (aperture) or LLONG_MAX
   double alpha;               // (pitch / lambda)^2
   int reach;
-  int* counter;
+  int* counter;               // zeroed by caller
   float2* u;
   int* status;
   int grid;

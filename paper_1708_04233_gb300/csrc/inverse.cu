@@ -83,19 +83,20 @@ struct InvCfg {
 };
 
 template <int L>
-__global__ void __launch_bounds__(InvCfg<L>::NT) inverse_kernel(const float2* __restrict__ wbuf, int w,
-                                                                int h, float2* __restrict__ u,
-                                                                uint8_t* __restrict__ bits, int* status) {
+__global__ void __launch_bounds__(InvCfg<L>::NT) inverse_kernel(const __grid_constant__ InverseArgs a) {
   using C = InvCfg<L>;
   extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_inv0[kMaxJobs];
   float2* ring = reinterpret_cast<float2*>(smem);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * C::STAGE_BYTES);
 
-  const int ntx = w >> L, nty = h >> L;
-  const int spr = (ntx + C::G - 1) / C::G;  // strips per tile row
-  const long long nstrips = (long long)spr * nty;
+  // Items are the strips of all jobs: item -> (job, strip) by the jobs' first items.
+  const int nj = a.jobs ? min(a.batch->njobs, kMaxJobs) : 1;
+  const long long nitems = a.jobs ? a.batch->ninv : a.ninv0;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const long long count = nstrips > blockIdx.x ? (nstrips - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long long count = nitems > blockIdx.x ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  int* status = a.status;
+  for (int j = tid; j < nj; j += blockDim.x) s_inv0[j] = a.jobs ? a.jobs[j].inv0 : 0;
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
@@ -103,12 +104,25 @@ __global__ void __launch_bounds__(InvCfg<L>::NT) inverse_kernel(const float2* __
   }
   __syncthreads();
 
+  // Job, tile row and strip column of the CTA's i-th item.
+  auto locate = [&](long long i, int* ty, int* sx) -> const JobDev& {
+    const int item = (int)(blockIdx.x + i * gridDim.x);
+    const int j = job_of(s_inv0, nj, item);
+    const JobDev& J = a.jobs ? a.jobs[j] : a.job0;
+    const int spr = (J.ntx + C::G - 1) / C::G;  // strips per tile row
+    const int ls = item - s_inv0[j];
+    *ty = ls / spr;
+    *sx = ls - *ty * spr;
+    return J;
+  };
+
   auto issue = [&](long long i, int stage) {  // warp 0 only
-    const long long sidx = blockIdx.x + i * gridDim.x;
-    const int ty = (int)(sidx / spr), sx = (int)(sidx % spr);
+    int ty, sx;
+    const JobDev& J = locate(i, &ty, &sx);
+    const int ntx = J.ntx;
     const int tx0 = sx * C::G;
     const int gv = min(C::G, ntx - tx0);
-    const float2* src = wbuf + ((size_t)ty * ntx + tx0) * C::TSL;
+    const float2* src = J.wbuf + ((size_t)ty * ntx + tx0) * C::TSL;
     float2* dst = ring + (size_t)stage * C::G * C::STRIDE;
     if (lane == 0) mbar_expect_tx(&full[stage], (unsigned)(gv * C::TSL * sizeof(float2)));
     __syncwarp();
@@ -135,9 +149,12 @@ __global__ void __launch_bounds__(InvCfg<L>::NT) inverse_kernel(const float2* __
       timed_out = true;
       break;
     }
-    const long long sidx = blockIdx.x + i * gridDim.x;
-    const int ty = (int)(sidx / spr), sx = (int)(sidx % spr);
-    const int gv = min(C::G, ntx - sx * C::G);
+    int ty, sx;
+    const JobDev& J = locate(i, &ty, &sx);
+    const int w = J.w;
+    float2* u = J.u;
+    uint8_t* bits = J.bits;
+    const int gv = min(C::G, J.ntx - sx * C::G);
     const bool valid = g < gv;
     const float2* c = ring + (size_t)stage * C::G * C::STRIDE + (size_t)(valid ? g : 0) * C::STRIDE;
 
@@ -292,8 +309,7 @@ __global__ void wbuf_to_mallat_kernel(const float2* __restrict__ wbuf, int w, in
 }
 
 template <int L>
-cudaError_t launch_inv_l(const float2* wbuf, int w, int h, float2* u, uint8_t* bits, int* status,
-                         int num_sms, cudaStream_t s) {
+cudaError_t launch_inv_l(const InverseArgs& a, cudaStream_t s) {
   using C = InvCfg<L>;
   cudaError_t e = cudaFuncSetAttribute(inverse_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)C::SMEM);
@@ -302,11 +318,19 @@ cudaError_t launch_inv_l(const float2* wbuf, int w, int h, float2* u, uint8_t* b
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, inverse_kernel<L>, C::NT, C::SMEM);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  const long long nstrips = (long long)(((w >> L) + C::G - 1) / C::G) * (h >> L);
-  const long long grid = std::min<long long>(nstrips, (long long)num_sms * per_sm);
+  // One job: no more CTAs than strips.  A job table: a fixed grid (the item
+  // count lives on the device), so the launch can be replayed from a graph.
+  long long grid = (long long)a.num_sms * per_sm;
+  if (!a.jobs) grid = std::min<long long>(grid, a.ninv0);
   if (grid <= 0) return cudaSuccess;
-  inverse_kernel<L><<<(unsigned)grid, C::NT, C::SMEM, s>>>(wbuf, w, h, u, bits, status);
+  inverse_kernel<L><<<(unsigned)grid, C::NT, C::SMEM, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int L>
+int strips_l(int w, int h) {
+  using C = InvCfg<L>;
+  return (((w >> L) + C::G - 1) / C::G) * (h >> L);
 }
 
 template <int L>
@@ -318,14 +342,23 @@ cudaError_t launch_fwd_l(const float2* u, int w, int h, float2* wbuf, cudaStream
 
 }  // namespace
 
-cudaError_t launch_inverse(const float2* wbuf, int w, int h, int L, float2* u, uint8_t* bits,
-                           int* status, int num_sms, cudaStream_t s) {
-  switch (L) {
-    case 2: return launch_inv_l<2>(wbuf, w, h, u, bits, status, num_sms, s);
-    case 3: return launch_inv_l<3>(wbuf, w, h, u, bits, status, num_sms, s);
-    case 4: return launch_inv_l<4>(wbuf, w, h, u, bits, status, num_sms, s);
-    case 5: return launch_inv_l<5>(wbuf, w, h, u, bits, status, num_sms, s);
+cudaError_t launch_inverse(const InverseArgs& a, cudaStream_t s) {
+  switch (a.L) {
+    case 2: return launch_inv_l<2>(a, s);
+    case 3: return launch_inv_l<3>(a, s);
+    case 4: return launch_inv_l<4>(a, s);
+    case 5: return launch_inv_l<5>(a, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+int inverse_strips(int w, int h, int L) {
+  switch (L) {
+    case 2: return strips_l<2>(w, h);
+    case 3: return strips_l<3>(w, h);
+    case 4: return strips_l<4>(w, h);
+    case 5: return strips_l<5>(w, h);
+    default: return 0;
   }
 }
 

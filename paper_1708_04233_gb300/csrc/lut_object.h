@@ -1,0 +1,84 @@
+// Host-side objects shared by the C-ABI translation units (abi.cu, batch.cu).
+#pragma once
+
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "internal.cuh"
+
+// A device-resident look-up table (library-owned; see wasabi_build_lut).
+struct wasabi_lut {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double lambda = 0, pitch = 0, gamma = 0;
+  int D = 0, W = 0, L = 0, nwt = 0, dtype = 0;
+  int reach = 0;  // pixels: footprint half-extent bound (max floor(R) + 2^(L+1))
+  std::vector<double> z, R;
+  std::vector<wsb::DepthMeta> meta;
+  long long total_cap = 0;
+  void* block = nullptr;  // one device allocation for all arrays below
+  uint32_t* pos = nullptr;
+  float2* val = nullptr;
+  uint32_t* val16 = nullptr;
+  float* scale = nullptr;
+  int32_t* tile_off = nullptr;
+  wsb::DepthMeta* meta_dev = nullptr;
+  long long* nr_dev = nullptr;
+  float* cmax = nullptr;
+  unsigned* levels = nullptr;  // bit l: a level-l coefficient is kept
+  int lmin = 1;                // finest kept level (host copy)
+  // Autotuned superposition configurations: hologram size class -> (super-tile, threads).
+  mutable std::mutex tune_mu;
+  std::map<int, std::pair<int, int>> tuned;
+
+  wsb::LutView view() const {
+    wsb::LutView v;
+    v.D = D; v.W = W; v.L = L; v.nwt = nwt; v.dtype = dtype;
+    v.pos = pos; v.val = val; v.val16 = val16; v.scale = scale;
+    v.tile_off = tile_off; v.meta = meta_dev; v.cmax = cmax; v.lmin = lmin;
+    return v;
+  }
+};
+
+namespace wsb {
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Carves consecutive 256-byte-aligned regions out of one block.
+struct Carver {
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename T>
+  T* take(size_t count) {
+    off = align_up(off, 256);
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// Size class of a hologram for tuning: its longer side rounded up to a power of two.
+inline int size_class(int w, int h) {
+  int s = 1;
+  const int m = w > h ? w : h;
+  while (s < m) s <<= 1;
+  return s;
+}
+
+// Super-tile side and block size for a hologram: an environment override,
+// else the autotuned choice for its size class, else the default.
+void superpose_config(const wasabi_lut* lut, int w, int h, int* cell, int* threads);
+
+// wasabi_superpose with an explicit configuration.
+wasabi_status superpose_impl(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n, int holo_w,
+                             int holo_h, int rule, void* wbuf_dev, void* scratch_dev, size_t scratch_bytes,
+                             cudaStream_t s, int cell, int threads);
+
+bool device_info(int** status, int* sms);
+wasabi_status cuda_fail(const char* what, cudaError_t e);
+int superpose_min_threads();
+int superpose_max_cell_rows();
+
+}  // namespace wsb

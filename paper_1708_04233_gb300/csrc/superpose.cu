@@ -175,14 +175,15 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
   const int W2 = lut.W / 2;
   const int ntpd = lut.nwt * lut.nwt + 1;  // tile_off entries per depth
-  const int half = a.rule == WASABI_SHIFT_FLOOR ? 0 : 1;
+  __shared__ int s_sp0[kMaxJobs];
+  const int nj = min(a.batch->njobs, kMaxJobs), nsp = a.batch->nsp;
+  for (int j = tid; j < nj; j += NT) s_sp0[j] = a.jobs[j].sp0;
   for (int d = tid; d < lut.D; d += NT) {
     const DepthMeta m = lut.meta[d];
     S.dbox[d] = make_int2(m.tlo, m.thi);
   }
-  const int nstx = (a.ntx + k - 1) / k, nsty = (a.nty + k - 1) / k;
-  const int nst = nstx * nsty;
-  const float amax_cmax = __ldg(a.amax) * __ldg(lut.cmax);
+  int* counter = &a.batch->counter;
+  const float amax_cmax = a.batch->amax * __ldg(lut.cmax);
   float4* acc4 = reinterpret_cast<float4*>(S.acc);
   int* acci = reinterpret_cast<int*>(S.acc);
   const bool fixed = !a.acc_float;
@@ -190,36 +191,45 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
   long long pt[6] = {0, 0, 0, 0, 0, 0};
   long long pt_last = clock64();
 #endif
-  int next = 0;  // thread 0: the super-tile claimed for the next iteration
-  if (tid == 0) next = atomicAdd(a.counter, 1);
+  int next = 0;  // thread 0: the item claimed for the next iteration
+  if (tid == 0) next = atomicAdd(counter, 1);
 
   for (;;) {
     __syncthreads();
     if (tid == 0) {
       s_st = next;
-      next = atomicAdd(a.counter, 1);  // claim the next super-tile early
+      next = atomicAdd(counter, 1);  // claim the next item early
     }
     __syncthreads();
     PT_MARK(0);
-    const int st = s_st;
-    if (st >= nst) break;
+    const int item = s_st;
+    if (item >= nsp) break;
+    // Item -> (job, super-tile).
+    const JobDev& J = a.jobs[job_of(s_sp0, nj, item)];
+    const int ntx = J.ntx, nty = J.nty, ncx = J.ncx, ncy = J.ncy;
+    const int half = J.rule == WASABI_SHIFT_FLOOR ? 0 : 1;
+    const int* cell_off = J.off;
+    const wasabi_point* sorted = J.sorted;
+    float2* wbuf = J.wbuf;
+    const int nstx = (ntx + k - 1) / k;
+    const int st = item - J.sp0;
     const int Sx = (st % nstx) * k, Sy = (st / nstx) * k;
-    const int kx = min(k, a.ntx - Sx), ky = min(k, a.nty - Sy);
+    const int kx = min(k, ntx - Sx), ky = min(k, nty - Sy);
 
     for (int i = tid; i < (k * k * SL) / 2; i += NT) acc4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     // Cell rows within reach of the super-tile, one thread per row.
     const int X0 = Sx << L, X1 = (Sx + kx) << L, Y0 = Sy << L, Y1 = (Sy + ky) << L;
     const int cx0 = max(0, floor_div(X0 - a.reach, a.cell));
-    const int cx1 = min(a.ncx - 1, floor_div(X1 - 1 + a.reach, a.cell));
+    const int cx1 = min(ncx - 1, floor_div(X1 - 1 + a.reach, a.cell));
     const int cy0 = max(0, floor_div(Y0 - a.reach, a.cell));
-    const int cy1 = min(a.ncy - 1, floor_div(Y1 - 1 + a.reach, a.cell));
+    const int cy1 = min(ncy - 1, floor_div(Y1 - 1 + a.reach, a.cell));
     const int ncrows = (cx0 <= cx1 && cy0 <= cy1) ? cy1 - cy0 + 1 : 0;
     if (tid < ncrows) {
-      const int c0 = (cy0 + tid) * a.ncx;
-      const int s0 = __ldg(&a.cell_off[c0 + cx0]);
+      const int c0 = (cy0 + tid) * ncx;
+      const int s0 = __ldg(&cell_off[c0 + cx0]);
       s_rowstart[tid] = s0;
-      s_rowpre[tid] = __ldg(&a.cell_off[c0 + cx1 + 1]) - s0;
+      s_rowpre[tid] = __ldg(&cell_off[c0 + cx1 + 1]) - s0;
     }
     __syncthreads();
     if (warp == 0) {  // exclusive prefix over <= 128 rows, 4 per lane
@@ -261,7 +271,7 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
       if (tid < CH && c0 + tid < total) {
         const int i = c0 + tid;
         const int r = last_le(s_rowpre, 0, ncrows - 1, i);
-        const int4 p = __ldg(reinterpret_cast<const int4*>(a.sorted) + s_rowstart[r] + (i - s_rowpre[r]));
+        const int4 p = __ldg(reinterpret_cast<const int4*>(sorted) + s_rowstart[r] + (i - s_rowpre[r]));
         const int2 bx = S.dbox[p.w];
         const int X = p.x - W2, Y = p.y - W2;
         const int Ax = X >> L, Ay = Y >> L;  // arithmetic shifts: floor division
@@ -406,7 +416,7 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
     int j = 0, t = NT >= Q4 ? tid / Q4 : 0;  // this thread's tile (row j, column t)
     while (t >= kx) { t -= kx; ++j; }
     while (j < ky) {
-      float4* dst = reinterpret_cast<float4*>(a.wbuf + ((size_t)(Sy + j) * a.ntx + Sx + t) * TSL);
+      float4* dst = reinterpret_cast<float4*>(wbuf + ((size_t)(Sy + j) * ntx + Sx + t) * TSL);
       const int src0 = ((j * k + t) << SLsh) >> 1;
       for (int q = NT >= Q4 ? tid % Q4 : tid; q < Q4; q += qstep) {
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -425,8 +435,8 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
     PT_MARK(5);
   }
 #ifdef WASABI_PHASE_TIMERS
-  if (tid == 0 && a.timers)
-    for (int i = 0; i < 6; ++i) atomicAdd(&a.timers[i], (unsigned long long)pt[i]);
+  if (tid == 0)
+    for (int i = 0; i < 6; ++i) atomicAdd(&a.batch->timers[i], (unsigned long long)pt[i]);
 #endif
 }
 
@@ -439,8 +449,9 @@ cudaError_t launch_t(const SuperposeArgs& a, cudaStream_t s) {
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, superpose_kernel<L, DT>, a.threads, smem);
   if (e != cudaSuccess) return e;
-  const long long grid = std::min<long long>((long long)a.grid * std::max(per_sm, 1), a.nst);
-  if (grid <= 0) return cudaSuccess;
+  // A fixed grid (independent of the batch, so the launch can be replayed
+  // from a graph): CTAs without work exit at their first claim.
+  const long long grid = (long long)a.grid * std::max(per_sm, 1);
   superpose_kernel<L, DT><<<(unsigned)grid, a.threads, smem, s>>>(a);
   return cudaGetLastError();
 }
