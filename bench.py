@@ -32,8 +32,6 @@ from workloads import CONFIGS  # noqa: E402
 
 METRIC = "WASABI hologram Mpoint*coeff/s at 65536^2 (hologram s, HBM fraction)"
 UNIT = "Mpoint*coeff/s"
-KERNELS_PER_STEP = 13  # psf_haar, select, tile_count, tile_scan, scatter, quantize,
-#                        init_single, zero, count, scan, scatter_points, superpose, inverse
 
 
 def _peaks():
@@ -50,7 +48,9 @@ def _workload_desc(c):
                         f"{c.D} depths, W={c.W}, L={c.L}, keep={c.gamma}",
             "Nh": c.Nh, "N": c.N, "lambda_m": c.lam, "pitch_m": c.pitch, "z_range_m": [c.zmin, c.zmax],
             "depths": c.D, "window": c.W, "levels": c.L, "keep_ratio": c.gamma, "output": c.output,
-            "lut_dtype": c.lut_dtype, "l2": "inputs larger than L2 (34.4 GB wavelet buffer per step)"}
+            "lut_dtype": c.lut_dtype, "l2": (f"{'outputs larger than L2' if c.Nh * c.Nh // 8 > 129e6 else 'NOT larger than L2'} "
+                   f"({c.Nh}^2: {c.Nh * c.Nh / 8e9:.3g} GB of bits per step; "
+                   f"{c.Nh * c.Nh * 8e-9:.3g} GB wavelet buffer in the two-pass form)")}
 
 
 class ClockSampler:
@@ -182,39 +182,44 @@ def run_gpu(args, c):
     z = torch.from_numpy(pts["z"]).to(dev)
     a = torch.from_numpy(pts["a"]).to(dev)
     pbuf = torch.empty((N, 4), dtype=torch.int32, device=dev)
-    wbuf = torch.empty(c.Nh * c.Nh, dtype=torch.complex64, device=dev)
     bits = torch.empty(c.Nh * c.Nh // 8, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
+    fused = args.path == "fused"
+    wbuf = None if fused else torch.empty(c.Nh * c.Nh, dtype=torch.complex64, device=dev)
 
-    ev = {k: [] for k in ("lut", "superpose", "inverse")}
+    ev = {k: [] for k in (("lut", "hologram") if fused else ("lut", "superpose", "inverse"))}
 
-    def step(record=False, xs=x, ys=y, zs=z, as_=a):
+    def step(record=False, xs=x, ys=y, zs=z, as_=a, two_pass=not fused, wb=None):
         with torch.cuda.stream(stream):
-            e0 = torch.cuda.Event(enable_timing=True) if record else None
-            if record:
-                e0.record(stream)
+            marks = []
+
+            def mark():
+                if record:
+                    e = torch.cuda.Event(enable_timing=True)
+                    e.record(stream)
+                    marks.append(e)
+            mark()
             lut = w.build_lut(c.lam, c.pitch, depths, c.W, c.L, c.gamma, dtype=c.lut_dtype, stream=stream)
             w.quantize_points(xs, ys, zs, as_, c.zmin, c.zmax, c.D, out=pbuf, stream=stream)
-            if record:
-                e1 = torch.cuda.Event(enable_timing=True)
-                e1.record(stream)
+            mark()
             if step.scratch is None:
                 step.scratch = torch.empty(w.scratch_bytes(lut, N, c.Nh, c.Nh), dtype=torch.uint8, device=dev)
-            w.superpose(lut, pbuf, c.Nh, c.Nh, rule=0, wbuf=wbuf, scratch=step.scratch, stream=stream)
+            if two_pass:
+                w.superpose(lut, pbuf, c.Nh, c.Nh, rule=0, wbuf=wb if wb is not None else wbuf,
+                            scratch=step.scratch, stream=stream)
+                mark()
+                w.inverse_haar(wb if wb is not None else wbuf, c.Nh, c.Nh, c.L, bits=bits, want="bits",
+                               stream=stream)
+            else:
+                w.hologram(lut, pbuf, c.Nh, c.Nh, want="bits", rule=0, bits=bits, scratch=step.scratch,
+                           stream=stream)
+            mark()
             if record:
-                e2 = torch.cuda.Event(enable_timing=True)
-                e2.record(stream)
-            w.inverse_haar(wbuf, c.Nh, c.Nh, c.L, bits=bits, want="bits", stream=stream)
-            if record:
-                e3 = torch.cuda.Event(enable_timing=True)
-                e3.record(stream)
-                ev["lut"].append((e0, e1))
-                ev["superpose"].append((e1, e2))
-                ev["inverse"].append((e2, e3))
-            step.last_lut = lut
+                step.marks.append(marks)
             lut.close()
             return lut
     step.scratch = None
+    step.marks = []
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -244,6 +249,10 @@ def run_gpu(args, c):
         barrier()
     w.sync_status(stream)
     ms = t0.elapsed_time(t1) / args.steps
+    for marks in step.marks:
+        for k, (e0, e1) in zip(ev, zip(marks, marks[1:])):
+            ev[k].append((e0, e1))
+    step.marks = []
     if world > 1:
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -278,17 +287,48 @@ def run_gpu(args, c):
     h2d = sum(t.numel() * t.element_size() for t in (hx, hy, hz, ha))
     d2h = hbits.numel()
 
+    # The two-pass form (superposition into the 34 GB wavelet buffer, then the
+    # separate inverse kernel): the inverse kernel's HBM fraction.
+    two = None
+    if fused and not args.no_two_pass:
+        wb = torch.empty(c.Nh * c.Nh, dtype=torch.complex64, device=dev)
+        for _ in range(2):
+            step(two_pass=True, wb=wb)
+        barrier()
+        n2 = max(3, min(args.steps, 10))
+        for _ in range(n2):
+            step(record=True, two_pass=True, wb=wb)
+        barrier()
+        w.sync_status(stream)
+        st = {k: float(np.mean([m[i].elapsed_time(m[i + 1]) for m in step.marks]))
+              for i, k in enumerate(("lut", "superpose", "inverse"))}
+        step.marks = []
+        del wb
+        torch.cuda.empty_cache()
+        two = {"ms_per_step": sum(st.values()), "stages_ms": st, "steps": n2}
+    elif not fused:
+        two = {"ms_per_step": ms, "stages_ms": stage_ms, "steps": args.steps}
+
     inv_bytes = c.Nh * c.Nh * 8 + c.Nh * c.Nh // 8
-    sup_bytes = c.Nh * c.Nh * 8 + N * 16
-    inv_gbs = inv_bytes / (stage_ms["inverse"] * 1e-3) / 1e9
-    sup_gbs = sup_bytes / (stage_ms["superpose"] * 1e-3) / 1e9
-    dom = "inverse" if stage_ms["inverse"] >= stage_ms["superpose"] else "superpose"
-    ach = inv_gbs if dom == "inverse" else sup_gbs
-    roof = {"kernel": "inverse_kernel<4> (fused inverse Haar + binarise)" if dom == "inverse"
-            else "superpose_kernel<4,f32> (+ binning, one ABI call)",
-            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "peak_source": peak_kind, "traffic": None,
-            "algorithmic_bytes": inv_bytes if dom == "inverse" else sup_bytes}
+    if two is not None:
+        inv_gbs = inv_bytes / (two["stages_ms"]["inverse"] * 1e-3) / 1e9
+        two["inverse_hbm"] = {"kernel": "inverse_kernel<4> (inverse Haar + binarisation)",
+                              "algorithmic_bytes": inv_bytes, "gbs": inv_gbs, "frac": inv_gbs / peak,
+                              "peak": peak, "peak_source": peak_kind}
+    hot_ms = stage_ms["hologram" if fused else "superpose"]
+    # Dominant kernel: the superposition (with the fused inverse + binarisation
+    # epilogue in the fused form).  It is a shared-memory scatter-add: two
+    # 32-bit shared-memory atomic adds per point-coefficient (real, imaginary).
+    # Peak: one 32-bit access per bank per clock, 32 banks x 152 SMs x max SM clock.
+    smem_peak = 32 * 152 * 2070e6 / 1e9  # Gop/s
+    ach = 2 * units / (hot_ms * 1e-3) / 1e9
+    roof = {"kernel": ("superpose_kernel<4,f32> with fused inverse + binarisation" if fused
+                       else "superpose_kernel<4,f32>") + " (+ binning kernels, one ABI call)",
+            "bound": "alu", "achieved": ach, "peak": smem_peak, "unit": "Gop/s", "frac": ach / smem_peak,
+            "peak_source": "derived: 32 banks x 152 SMs x 2070 MHz (shared-memory 32-bit ops)",
+            "algorithmic_ops": 2 * units, "traffic": None}
+    lut_kernels = 5 + (0 if c.lut_dtype in ("f32", 0) else 1)
+    per_step = lut_kernels + 1 + 6 + (0 if fused else 1)
 
     if rank == 0:
         out = {"metric": METRIC, "value": units * world / (ms * 1e-3) / 1e6, "unit": UNIT,
@@ -298,13 +338,13 @@ def run_gpu(args, c):
                "config": dict(_workload_desc(c), parallelism=f"replicas x{world}"),
                "hologram_s": ms * 1e-3, "point_coeff_per_step": units,
                "stages_ms": stage_ms,
-               "superpose_mpc_s": units / (stage_ms["superpose"] * 1e-3) / 1e6,
-               "hbm": {"inverse_gbs": inv_gbs, "inverse_frac": inv_gbs / peak,
-                       "superpose_write_gbs": sup_gbs, "superpose_frac": sup_gbs / peak},
+               "path": args.path,
+               "superpose_mpc_s": units / (hot_ms * 1e-3) / 1e6,
                "roofline": roof,
+               "two_pass": two,
                "e2e": {"value": units * world / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
                        "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-               "gpu_launches": KERNELS_PER_STEP * args.steps,
+               "gpu_launches": per_step * args.steps,
                "clocks": clk.summary()}
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = oracle_sample(c, pts, os.cpu_count() or 1)
@@ -322,8 +362,17 @@ def main():
     ap.add_argument("--impl", default="wasabi", choices=["wasabi", "reference"])
     ap.add_argument("--config", default="C3", choices=["C2", "C3", "C4"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--path", default="fused", choices=["fused", "two-pass"],
+                    help="fused: wasabi_hologram; two-pass: wasabi_superpose + wasabi_inverse_haar")
+    ap.add_argument("--nh", type=int, default=0,
+                    help="profiling cases: hologram side (points scaled by area, same density)")
+    ap.add_argument("--no-two-pass", action="store_true",
+                    help="skip the secondary two-pass measurement (inverse kernel HBM fraction)")
     args = ap.parse_args()
     c = CONFIGS[args.config]
+    if args.nh:
+        c = c.scaled(Nh=args.nh, N=max(1, c.N * args.nh * args.nh // (c.Nh * c.Nh)),
+                     name=f"{c.name}-scaled")
     if args.impl == "reference":
         run_reference(args, c)
     else:

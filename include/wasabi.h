@@ -114,8 +114,9 @@ wasabi_status wasabi_quantize_points(const int32_t* x_dev, const int32_t* y_dev,
  * dtype selects how superposition reads the values: FP32, or FP16 / BF16 with
  * one FP32 scale per 32 consecutive entries (scale = max |re|, |im| of the
  * block; stored value = value / scale, rounded to nearest).
- * Allocates device memory (stream-ordered) and enqueues the build on stream;
- * *out is usable by later work on the same stream at once.
+ * Allocates device memory (stream-ordered), enqueues the build on stream and
+ * waits for it to finish (the library reads back which levels hold kept
+ * coefficients, which sizes the superposition's accumulator).
  * E_INVALID on bad arguments, E_NOMEM, E_CUDA. */
 wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths_host,
                                int n_depths, int window, int levels, double keep_ratio,
@@ -188,14 +189,31 @@ wasabi_status wasabi_superpose_static(const wasabi_lut* lut, const wasabi_point*
 wasabi_status wasabi_inverse_haar(const void* wbuf_dev, int holo_w, int holo_h, int levels,
                                   void* u_dev, uint8_t* bits_dev, void* stream);
 
+/* A4 + A5 + A6 + A7 in one pass: superposition (Eq. (2)) fused with the
+ * inverse transformation (Sec. 1, step 3) and binarisation (Sec. 2).  Each
+ * super-tile's wavelet coefficients are accumulated in shared memory and
+ * inverse-transformed there, so the wavelet buffer is never written to (or
+ * read back from) device memory unless asked for.  Outputs as in
+ * wasabi_inverse_haar: u_dev (complex64 row-major, 16-byte aligned) and/or
+ * bits_dev (packed, 4-byte aligned, holo_w % 8 == 0); at least one of them.
+ * wbuf_dev may be NULL; when given, it also receives the tile-major wavelet
+ * buffer as wasabi_superpose writes it.  The pixels equal those of
+ * wasabi_superpose followed by wasabi_inverse_haar.  Needs levels >= 2;
+ * scratch as for wasabi_superpose. */
+wasabi_status wasabi_hologram(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n,
+                              int holo_w, int holo_h, int rule, void* wbuf_dev, void* u_dev,
+                              uint8_t* bits_dev, void* scratch_dev, size_t scratch_bytes, void* stream);
+
 /* ---- Batches: many holograms through one launch sequence (A10) ----------
  * One job = one hologram with its own points, wavelet buffer and outputs, all
- * sharing the LUT.  A batch runs every job through six launches (binning:
- * zero, count, scan, scatter; superposition; inverse) whose grids do not
- * depend on the batch; work items (super-tiles, strips) are claimed from a
- * device-side job table.  With use_graph, the job-table upload and the six
- * launches are captured into a CUDA graph on the first run on a stream and
- * replayed by later runs (not on the legacy default stream).
+ * sharing the LUT.  A batch runs every job through five launches (binning:
+ * zero, count, scan, scatter; superposition with the fused inverse of
+ * wasabi_hologram) whose grids do not depend on the batch; work items
+ * (super-tiles) are claimed from a device-side job table.  With use_graph,
+ * the job-table upload and the five launches are captured into a CUDA graph
+ * on the first run on a stream and replayed by later runs (not on the legacy
+ * default stream).  The graph holds the LUT's device pointers: destroy the
+ * batch before the LUT.
  * The batch object owns pinned host staging and the device job table; the
  * caller owns the jobs' buffers and the scratch.  A run returns as soon as the
  * work is enqueued; a later run on the same batch object first waits for the
@@ -205,9 +223,10 @@ typedef struct {
   int64_t n;
   int holo_w, holo_h;             /* multiples of 2^L; holo_w % 8 == 0 for bits */
   int rule;                       /* wasabi_shift_rule */
-  void* wbuf_dev;                 /* tile-major wavelet buffer, holo_w * holo_h complex64, 256-B aligned */
-  void* u_dev;                    /* complex64 row-major output, or NULL */
-  uint8_t* bits_dev;              /* packed bits output, or NULL (both NULL: wavelet buffer only) */
+  void* wbuf_dev;                 /* tile-major wavelet buffer, holo_w * holo_h complex64, 256-B aligned,
+                                     or NULL when only u / bits are wanted */
+  void* u_dev;                    /* complex64 row-major output (16-B aligned), or NULL */
+  uint8_t* bits_dev;              /* packed bits output (4-B aligned), or NULL; not all three NULL */
 } wasabi_job;
 
 typedef struct wasabi_batch wasabi_batch;

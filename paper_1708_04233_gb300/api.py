@@ -174,9 +174,27 @@ def inverse_haar(wbuf: torch.Tensor, w: int, h: int, levels: int, u: torch.Tenso
 
 
 def hologram(lut: Lut, points: torch.Tensor, w: int, h: int, want: str = "complex", rule: int = 0,
-             stream=None):
-    wbuf = superpose(lut, points, w, h, rule, stream=stream)
-    return inverse_haar(wbuf, w, h, lut.levels, want=want, stream=stream)
+             u: torch.Tensor | None = None, bits: torch.Tensor | None = None,
+             wbuf: torch.Tensor | None = None, scratch: torch.Tensor | None = None, stream=None):
+    """Eq. (2) fused with the inverse transform and binarisation
+    (wasabi_hologram): want = "complex" | "bits" | "both".  A given wbuf also
+    receives the tile-major wavelet buffer."""
+    n = points.shape[0]
+    dev = points.device
+    if want in ("complex", "both") and u is None:
+        u = torch.empty((h, w), dtype=torch.complex64, device=dev)
+    if want in ("bits", "both") and bits is None:
+        bits = torch.empty((h * w + 7) // 8, dtype=torch.uint8, device=dev)
+    if scratch is None:
+        scratch = torch.empty(scratch_bytes(lut, n, w, h), dtype=torch.uint8, device=dev)
+    check(_lib().wasabi_hologram(lut.handle, _ptr(points) if n else C.c_void_p(None), n, w, h, rule,
+                                 _ptr(wbuf), _ptr(u), _ptr(bits), _ptr(scratch), scratch.numel(),
+                                 _stream(stream)))
+    if want == "complex":
+        return u
+    if want == "bits":
+        return bits
+    return u, bits
 
 
 def cgh_direct_scratch_bytes(n: int, w: int, h: int) -> int:

@@ -129,8 +129,10 @@ void superpose_config(const wasabi_lut* lut, int w, int h, int* cell, int* threa
   nt = env_int("WASABI_SUPERPOSE_THREADS", nt);
   T = std::min(T, 256);
   T = std::max(T, std::max(1 << lut->L, 32));
-  T = (T >> lut->L) << lut->L;
-  while (T > std::max(1 << lut->L, 32) && superpose_smem_bytes(T, lut->L, lut->lmin, lut->D) > 220 * 1024) T >>= 1;
+  // A multiple of 32 pixels (one word of the packed binary output) and of 2^L.
+  const int unit = std::max(1 << lut->L, 32);
+  T = std::max(unit, T / unit * unit);
+  while (T > unit && superpose_smem_bytes(T, lut->L, lut->lmin, lut->D) > 220 * 1024) T = std::max(unit, T / 2 / unit * unit);
   nt = std::max(superpose_min_threads(), std::min(512, nt / 32 * 32));
   *cell = T;
   *threads = nt;
@@ -541,19 +543,38 @@ wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points
   if (!lut) { set_error("superpose: NULL argument"); return WASABI_E_INVALID; }
   int cell, threads;
   superpose_config(lut, holo_w, holo_h, &cell, &threads);
-  return superpose_impl(lut, points_dev, n, holo_w, holo_h, rule, wbuf_dev, scratch_dev, scratch_bytes,
-                        (cudaStream_t)stream, cell, threads);
+  if (!wbuf_dev) { set_error("superpose: NULL wavelet buffer"); return WASABI_E_INVALID; }
+  return superpose_impl(lut, points_dev, n, holo_w, holo_h, rule, wbuf_dev, nullptr, nullptr, scratch_dev,
+                        scratch_bytes, (cudaStream_t)stream, cell, threads);
+}
+
+wasabi_status wasabi_hologram(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n, int holo_w,
+                              int holo_h, int rule, void* wbuf_dev, void* u_dev, uint8_t* bits_dev,
+                              void* scratch_dev, size_t scratch_bytes, void* stream) {
+  if (!lut) { set_error("hologram: NULL argument"); return WASABI_E_INVALID; }
+  if (!u_dev && !bits_dev) { set_error("hologram: need u_dev or bits_dev"); return WASABI_E_INVALID; }
+  int cell, threads;
+  superpose_config(lut, holo_w, holo_h, &cell, &threads);
+  return superpose_impl(lut, points_dev, n, holo_w, holo_h, rule, wbuf_dev, u_dev, bits_dev, scratch_dev,
+                        scratch_bytes, (cudaStream_t)stream, cell, threads);
 }
 
 }  // extern "C"
 
 wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n, int holo_w,
-                                  int holo_h, int rule, void* wbuf_dev, void* scratch_dev, size_t scratch_bytes,
-                                  cudaStream_t stream, int cell, int threads) {
-  if (!lut || n < 0 || (n > 0 && !points_dev) || !wbuf_dev || !scratch_dev) {
+                                  int holo_h, int rule, void* wbuf_dev, void* u_dev, uint8_t* bits_dev,
+                                  void* scratch_dev, size_t scratch_bytes, cudaStream_t stream, int cell,
+                                  int threads) {
+  if (!lut || n < 0 || (n > 0 && !points_dev) || (!wbuf_dev && !u_dev && !bits_dev) || !scratch_dev) {
     set_error("superpose: NULL argument");
     return WASABI_E_INVALID;
   }
+  if ((u_dev || bits_dev) && lut->L < 2) {
+    set_error("hologram: the fused inverse needs levels >= 2");
+    return WASABI_E_INVALID;
+  }
+  if (bits_dev && holo_w % 8) { set_error("hologram: bits output needs holo_w %% 8 == 0"); return WASABI_E_INVALID; }
+  if (((uintptr_t)u_dev & 15) || ((uintptr_t)bits_dev & 3)) { set_error("hologram: misaligned output"); return WASABI_E_INVALID; }
   const int ts = 1 << lut->L;
   if (holo_w < ts || holo_h < ts || holo_w % ts || holo_h % ts || holo_w > (1 << 29) || holo_h > (1 << 29)) {
     set_error("superpose: holo_w and holo_h must be multiples of 2^L = %d", ts);
@@ -565,7 +586,7 @@ wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* poi
   int* status;
   int sms;
   if (!device_info(&status, &sms)) return WASABI_E_CUDA;
-  if (cell < std::max(1 << lut->L, 32) || cell > 256 || cell % (1 << lut->L) ||
+  if (cell < std::max(1 << lut->L, 32) || cell > 256 || cell % std::max(1 << lut->L, 32) ||
       threads < superpose_min_threads() || threads > 512 || threads % 32) {
     set_error("superpose: bad configuration (super-tile %d, %d threads)", cell, threads);
     return WASABI_E_INVALID;
@@ -583,7 +604,7 @@ wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* poi
   if (smem > 220 * 1024) { set_error("superpose: super-tile %d needs %zu B of shared memory", cell, smem); return WASABI_E_INVALID; }
   const cudaStream_t s = (cudaStream_t)stream;
   JobDev J = make_job(lut, points_dev, n, holo_w, holo_h, rule, cell, static_cast<float2*>(wbuf_dev),
-                      nullptr, nullptr);
+                      static_cast<float2*>(u_dev), bits_dev);
   J.sorted = b.sorted; J.cnt = b.cnt; J.off = b.off; J.cursor = b.cursor;
   cudaError_t e = launch_init_single(J, b.jobs, b.batch, super_tiles(J.ntx, J.nty, cell >> lut->L), 0, s);
   if (e != cudaSuccess) return cuda_fail("superpose: init", e);

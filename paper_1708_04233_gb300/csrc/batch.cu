@@ -1,10 +1,11 @@
 // Batched hologram synthesis (many jobs, one launch sequence) and the
 // autotuner of the superposition's super-tile and block sizes.
 //
-// A batch runs every job through the same six launches -- zero, count, scan,
-// scatter (binning), superpose, inverse -- whose grids do not depend on the
-// batch: the work items (super-tiles and strips of all jobs) are claimed from
-// the device-side job table.  The launch sequence, together with the upload
+// A batch runs every job through the same five launches -- zero, count, scan,
+// scatter (binning) and superpose, whose epilogue also runs the inverse
+// transform and binarisation of each finished super-tile -- with grids that
+// do not depend on the batch: the work items (super-tiles of all jobs) are
+// claimed from the device-side job table.  The launch sequence, together with the upload
 // of the job table from pinned host memory, is captured once into a CUDA
 // graph and replayed for every later batch (when the caller's stream allows
 // capture).
@@ -45,7 +46,8 @@ size_t job_scratch(const wasabi_job& j, int cell) {
 
 wasabi_status check_job(const wasabi_lut* lut, const wasabi_job& j, int idx) {
   const int ts = 1 << lut->L;
-  if (j.n < 0 || (j.n > 0 && !j.points_dev) || !j.wbuf_dev || j.holo_w < ts || j.holo_h < ts ||
+  if (j.n < 0 || (j.n > 0 && !j.points_dev) || (!j.wbuf_dev && !j.u_dev && !j.bits_dev) || j.holo_w < ts ||
+      j.holo_h < ts ||
       j.holo_w % ts || j.holo_h % ts || j.holo_w > (1 << 29) || j.holo_h > (1 << 29) ||
       (j.rule != WASABI_SHIFT_FLOOR && j.rule != WASABI_SHIFT_NEAREST)) {
     set_error("batch: job %d has bad arguments", idx);
@@ -66,7 +68,7 @@ wasabi_status check_job(const wasabi_lut* lut, const wasabi_job& j, int idx) {
   return WASABI_OK;
 }
 
-// Enqueues the upload and the six launches of a batch on s.  Under stream
+// Enqueues the upload and the five launches of a batch on s.  Under stream
 // capture the record of `staged` becomes an external event node, so the host
 // can wait on it after each replay.
 cudaError_t enqueue_batch(wasabi_batch* b, cudaStream_t s, int* status, int sms, bool capturing) {
@@ -87,12 +89,6 @@ cudaError_t enqueue_batch(wasabi_batch* b, cudaStream_t s, int* status, int sms,
   sa.jobs = b->jobs_dev; sa.batch = b->batch_dev; sa.cell = b->cell; sa.reach = lut->reach;
   sa.acc_float = 0; sa.status = status; sa.threads = b->threads; sa.grid = sms;
   if ((e = launch_superpose(sa, s)) != cudaSuccess) return e;
-  if (lut->L >= 2) {
-    InverseArgs ia;
-    std::memset(&ia, 0, sizeof ia);
-    ia.jobs = b->jobs_dev; ia.batch = b->batch_dev; ia.L = lut->L; ia.status = status; ia.num_sms = sms;
-    if ((e = launch_inverse(ia, s)) != cudaSuccess) return e;
-  }
   return cudaSuccess;
 }
 
@@ -223,7 +219,7 @@ wasabi_status wasabi_batch_run(wasabi_batch* b, const wasabi_job* jobs, int njob
   Carver c;
   c.base = static_cast<char*>(scratch_dev);
   long long pt0 = 0;
-  int sp0 = 0, inv0 = 0;
+  int sp0 = 0;
   for (int i = 0; i < njobs; ++i) {
     const wasabi_job& j = jobs[i];
     JobDev& J = b->staging_jobs[i];
@@ -247,16 +243,13 @@ wasabi_status wasabi_batch_run(wasabi_batch* b, const wasabi_job* jobs, int njob
     J.sorted = c.take<wasabi_point>((size_t)std::max<int64_t>(j.n, 1));
     J.pt0 = pt0;
     J.sp0 = sp0;
-    J.inv0 = inv0;
     pt0 += j.n;
     sp0 += ((J.ntx + k - 1) / k) * ((J.nty + k - 1) / k);
-    if (j.u_dev || j.bits_dev) inv0 += inverse_strips(j.holo_w, j.holo_h, lut->L);
   }
   BatchDev& B = *b->staging_batch;
   std::memset(&B, 0, sizeof B);
   B.njobs = njobs;
   B.nsp = sp0;
-  B.ninv = inv0;
   B.npts = pt0;
   const cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
@@ -320,10 +313,10 @@ wasabi_status wasabi_autotune(wasabi_lut* lut, int holo_side, int64_t n_points, 
     for (int nt : tcounts) {
       if (nt < superpose_min_threads()) continue;
       float ms = 0.f;
-      bool ok = superpose_impl(lut, pts, n_points, side, side, 0, wbuf, scratch, sbytes, s, cell, nt) == WASABI_OK;
+      bool ok = superpose_impl(lut, pts, n_points, side, side, 0, wbuf, nullptr, nullptr, scratch, sbytes, s, cell, nt) == WASABI_OK;
       ok = ok && cudaEventRecord(t0, s) == cudaSuccess;
       for (int r = 0; r < 3 && ok; ++r)
-        ok = superpose_impl(lut, pts, n_points, side, side, 0, wbuf, scratch, sbytes, s, cell, nt) == WASABI_OK;
+        ok = superpose_impl(lut, pts, n_points, side, side, 0, wbuf, nullptr, nullptr, scratch, sbytes, s, cell, nt) == WASABI_OK;
       ok = ok && cudaEventRecord(t1, s) == cudaSuccess && cudaEventSynchronize(t1) == cudaSuccess &&
            cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess;
       if (ok && ms < best) { best = ms; best_cell = cell; best_threads = nt; }

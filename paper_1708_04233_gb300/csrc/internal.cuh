@@ -119,6 +119,19 @@ cudaError_t launch_quantize(const int32_t* x, const int32_t* y, const double* z,
 // once in a CUDA graph and replayed; a single hologram is a batch of one.
 constexpr int kMaxJobs = 1024;
 
+// One inverse Haar step (Sec. 1, step 3; the transpose of the forward step),
+// picking output (ax, ay) of the 2x2 block:
+//   x00 = ((s + LH) + (HL + HH)) / 2     x01 = ((s - LH) + (HL - HH)) / 2
+//   x10 = ((s + LH) - (HL + HH)) / 2     x11 = ((s - LH) - (HL - HH)) / 2
+__device__ __forceinline__ float ipick1(float s, float lh, float hl, float hh, int ax, int ay) {
+  const float t1 = ax ? s - lh : s + lh;
+  const float t2 = ax ? hl - hh : hl + hh;
+  return (ay ? t1 - t2 : t1 + t2) * 0.5f;
+}
+__device__ __forceinline__ float2 ipick(float2 s, float2 lh, float2 hl, float2 hh, int ax, int ay) {
+  return make_float2(ipick1(s.x, lh.x, hl.x, hh.x, ax, ay), ipick1(s.y, lh.y, hl.y, hh.y, ax, ay));
+}
+
 struct JobDev {
   const wasabi_point* pts;  // input points (n)
   wasabi_point* sorted;     // binned points (n), scratch

@@ -59,18 +59,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   return true;
 }
 
-// One inverse Haar step, picking output (ax, ay) of the 2x2 block:
-//   x00 = ((s + LH) + (HL + HH)) / 2     x01 = ((s - LH) + (HL - HH)) / 2
-//   x10 = ((s + LH) - (HL + HH)) / 2     x11 = ((s - LH) - (HL - HH)) / 2
-__device__ __forceinline__ float ipick1(float s, float lh, float hl, float hh, int ax, int ay) {
-  const float t1 = ax ? s - lh : s + lh;
-  const float t2 = ax ? hl - hh : hl + hh;
-  return (ay ? t1 - t2 : t1 + t2) * 0.5f;
-}
-__device__ __forceinline__ float2 ipick(float2 s, float2 lh, float2 hl, float2 hh, int ax, int ay) {
-  return make_float2(ipick1(s.x, lh.x, hl.x, hh.x, ax, ay), ipick1(s.y, lh.y, hl.y, hh.y, ax, ay));
-}
-
 template <int L>
 struct InvCfg {
   static constexpr int TS = 1 << L;

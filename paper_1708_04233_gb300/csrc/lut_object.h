@@ -71,10 +71,11 @@ inline int size_class(int w, int h) {
 // else the autotuned choice for its size class, else the default.
 void superpose_config(const wasabi_lut* lut, int w, int h, int* cell, int* threads);
 
-// wasabi_superpose with an explicit configuration.
+// wasabi_superpose / wasabi_hologram with an explicit configuration: any of
+// the wavelet buffer, the complex field and the packed bits may be written.
 wasabi_status superpose_impl(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n, int holo_w,
-                             int holo_h, int rule, void* wbuf_dev, void* scratch_dev, size_t scratch_bytes,
-                             cudaStream_t s, int cell, int threads);
+                             int holo_h, int rule, void* wbuf_dev, void* u_dev, uint8_t* bits_dev,
+                             void* scratch_dev, size_t scratch_bytes, cudaStream_t s, int cell, int threads);
 
 bool device_info(int** status, int* sms);
 wasabi_status cuda_fail(const char* what, cudaError_t e);

@@ -36,6 +36,9 @@ namespace {
 constexpr int kMaxCellRows = 128;
 constexpr int kRangeCap = 2048;  // LUT ranges per batch
 constexpr int kPerMax = 8;       // range slots per thread (block size >= 256)
+// Accumulator tiles are SL + kTilePad complex apart, so that the tiles a warp
+// reads in the inverse epilogue start in different shared-memory banks.
+constexpr int kTilePad = 4;
 
 __device__ __forceinline__ int floor_div(int a, int b) {
   const int q = a / b;
@@ -114,13 +117,14 @@ __host__ __device__ inline size_t smem_layout(int T, int L, int lmin, int D, Sme
   const int k = T >> L;
   const int P = survivor_cap(k);
   const size_t SL = (size_t)1 << (2 * (L - lmin + 1));
+  const size_t TSTR = SL + kTilePad;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
     off = (off + bytes + 15) & ~(size_t)15;
     return base ? base + o : nullptr;
   };
-  unsigned char* p0 = take((size_t)k * k * SL * sizeof(float2));
+  unsigned char* p0 = take((size_t)k * k * TSTR * sizeof(float2));
   unsigned char* p1 = take((size_t)P * sizeof(int4));
   unsigned char* p2 = take((size_t)P * (L + 1) * sizeof(int2));
   unsigned char* p3 = take((size_t)kRangeCap * sizeof(int2));
@@ -154,6 +158,143 @@ __host__ __device__ inline size_t smem_layout(int T, int L, int lmin, int D, Sme
   } while (0)
 #endif
 
+// Inverse transform (Sec. 1, step 3) and binarisation (Sec. 2) of a finished
+// super-tile, straight from the shared-memory accumulator: the wavelet
+// buffer never goes to global memory.  Slots of levels finer than lmin were
+// never accumulated and read as zero.  Each thread rebuilds 4 x 4 pixel
+// blocks in the add order of the separate inverse kernel, from the same FP32
+// coefficient values that kernel would read, so the two paths give the same
+// pixels bit for bit.  Eight consecutive lanes cover 32 pixels of a row,
+// which is one 32-bit word of the packed binary hologram (the super-tile side
+// is a multiple of 32).
+template <int L>
+__device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed, float dq, int SLsh, int lmin, int k,
+                                                  int kx, int ky, int Sx, int Sy, const JobDev& J, int tid,
+                                                  int NT) {
+  if constexpr (L >= 2) {
+    constexpr int TS = 1 << L;
+    const int SL = 1 << SLsh;
+    const int TSTR = SL + kTilePad;
+    const int bpr = (k << L) >> 2;           // 4 x 4 blocks per super-tile row
+    const int total = bpr * ((ky << L) >> 2);
+    const int xvalid = (kx << L) >> 2;       // block columns inside the hologram
+    const int w = J.w;
+    float2* u = J.u;
+    uint8_t* bits = J.bits;
+    const int lane = tid & 31;
+    const int X0 = Sx << L, Y0 = Sy << L;
+    const int xend = (Sx + kx) << L;
+    const int* acci = reinterpret_cast<const int*>(acc);
+    auto coef = [&](int tb, int slot) -> float2 {
+      if (slot >= SL) return make_float2(0.f, 0.f);
+      if (fixed) {
+        const int2 q = reinterpret_cast<const int2*>(acci)[tb + slot];
+        return make_float2((float)q.x * dq, (float)q.y * dq);
+      }
+      return acc[tb + slot];
+    };
+    for (int b0 = 0; b0 < total; b0 += NT) {  // uniform trip count: whole warps shuffle
+      const int b = b0 + tid;
+      const int brow = b / bpr, bcol = b - brow * bpr;
+      const bool inrow = b < total;
+      const bool valid = inrow && bcol < xvalid;
+      const int px0 = 4 * bcol, py0 = 4 * brow;  // block origin in the super-tile
+      const int tb = valid ? ((py0 >> L) * k + (px0 >> L)) * TSTR : 0;
+      const int bx = (px0 & (TS - 1)) >> 2, by = (py0 & (TS - 1)) >> 2;
+      float2 s1[2][2] = {{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}};
+      if (valid) {  // the block's four level-1 scaling values
+        // Levels L .. 3: the block lies inside one level-(l-1) cell.
+        float2 s = coef(tb, 0);
+#pragma unroll
+        for (int l = L; l >= 3; --l) {
+          const int m = L - l;
+          const int o = (((4 * by) >> l) << m) + ((4 * bx) >> l);
+          const float2 lh = coef(tb, (1 << (2 * m)) + o), hl = coef(tb, (2 << (2 * m)) + o),
+                       hh = coef(tb, (3 << (2 * m)) + o);
+          s = ipick(s, lh, hl, hh, ((4 * bx) >> (l - 1)) & 1, ((4 * by) >> (l - 1)) & 1);
+        }
+        // Level 2 at (bx, by) -> four level-1 scaling values.
+        const int m = L - 2;
+        const int o = (by << m) + bx;
+        const float2 lh = coef(tb, (1 << (2 * m)) + o), hl = coef(tb, (2 << (2 * m)) + o),
+                     hh = coef(tb, (3 << (2 * m)) + o);
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
+          for (int ax = 0; ax < 2; ++ax) s1[ay][ax] = ipick(s, lh, hl, hh, ax, ay);
+      }
+      const int x0 = X0 + px0;
+      const int xw = X0 + 32 * (bcol >> 3);  // first pixel of this lane group's bit word
+      // Stores one pixel row of the block: complex values and/or its four bits
+      // (eight lanes OR their nibbles into the word at xw).
+      auto put_row = [&](int y, float2 p0, float2 p1, float2 p2, float2 p3) {
+        if (u != nullptr && valid) {
+          float4* dst = reinterpret_cast<float4*>(u + (size_t)y * w + x0);
+          __stcs(dst, make_float4(p0.x, p0.y, p1.x, p1.y));
+          __stcs(dst + 1, make_float4(p2.x, p2.y, p3.x, p3.y));
+        }
+        if (bits != nullptr) {
+          unsigned nib = 0;
+          if (valid)
+            nib = (p0.x > 0.f ? 1u : 0u) | (p1.x > 0.f ? 2u : 0u) | (p2.x > 0.f ? 4u : 0u) | (p3.x > 0.f ? 8u : 0u);
+          unsigned v = nib << (4 * (lane & 7));
+          v |= __shfl_xor_sync(0xffffffffu, v, 1);
+          v |= __shfl_xor_sync(0xffffffffu, v, 2);
+          v |= __shfl_xor_sync(0xffffffffu, v, 4);
+          if ((lane & 7) == 0 && inrow && xw < xend) {
+            const size_t byte0 = ((size_t)y * w + xw) >> 3;
+            if (xw + 32 <= xend && (w & 31) == 0) {
+              *reinterpret_cast<unsigned*>(bits + byte0) = v;
+            } else {
+              const int nb = min(4, (xend - xw) >> 3);
+              for (int q = 0; q < nb; ++q) bits[byte0 + q] = (uint8_t)(v >> (8 * q));
+            }
+          }
+        }
+      };
+      const int y0 = Y0 + py0;
+      if (lmin >= 2) {
+        // No level-1 details: the level-1 step gives s1 / 2 for all four
+        // pixels of each 2 x 2 group (the same values, up to the sign of a
+        // zero, as the step with zero details).
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay) {
+          float2 pa = make_float2(0.f, 0.f), pb = pa;
+          if (valid) {
+            pa = make_float2(s1[ay][0].x * 0.5f, s1[ay][0].y * 0.5f);
+            pb = make_float2(s1[ay][1].x * 0.5f, s1[ay][1].y * 0.5f);
+          }
+          put_row(y0 + 2 * ay, pa, pa, pb, pb);
+          put_row(y0 + 2 * ay + 1, pa, pa, pb, pb);
+        }
+      } else {
+        // Level 1, one pair of pixel rows at a time -> 2 x 4 pixels.
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay) {
+          float2 px[2][4];
+#pragma unroll
+          for (int ax = 0; ax < 2; ++ax) {
+            float2 l1 = make_float2(0.f, 0.f), h1 = l1, d1 = l1;
+            if (valid) {
+              const int m = L - 1;
+              const int o = ((2 * by + ay) << m) + 2 * bx + ax;
+              l1 = coef(tb, (1 << (2 * m)) + o);
+              h1 = coef(tb, (2 << (2 * m)) + o);
+              d1 = coef(tb, (3 << (2 * m)) + o);
+            }
+#pragma unroll
+            for (int qy = 0; qy < 2; ++qy)
+#pragma unroll
+              for (int qx = 0; qx < 2; ++qx) px[qy][2 * ax + qx] = ipick(s1[ay][ax], l1, h1, d1, qx, qy);
+          }
+          put_row(y0 + 2 * ay, px[0][0], px[0][1], px[0][2], px[0][3]);
+          put_row(y0 + 2 * ay + 1, px[1][0], px[1][1], px[1][2], px[1][3]);
+        }
+      }
+    }
+  }
+}
+
 template <int L, int DT>
 __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
   constexpr int TSL = 1 << (2 * L);
@@ -164,6 +305,7 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
   const int lmin = a.lut.lmin;
   const int SLsh = 2 * (L - lmin + 1);  // log2 of accumulator slots per tile
   const int SL = 1 << SLsh;
+  const int TSTR = SL + kTilePad;  // accumulator tile stride (complex)
   Smem S;
   smem_layout(T, L, lmin, a.lut.D, &S, smem);
   __shared__ int s_st, s_n, s_total;
@@ -216,7 +358,7 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
     const int Sx = (st % nstx) * k, Sy = (st / nstx) * k;
     const int kx = min(k, ntx - Sx), ky = min(k, nty - Sy);
 
-    for (int i = tid; i < (k * k * SL) / 2; i += NT) acc4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < (k * k * TSTR) / 2; i += NT) acc4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     // Cell rows within reach of the super-tile, one thread per row.
     const int X0 = Sx << L, X1 = (Sx + kx) << L, Y0 = Sy << L, Y1 = (Sy + ky) << L;
@@ -389,7 +531,7 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
           if ((unsigned)relx >= (unsigned)kx || (unsigned)rely >= (unsigned)ky) continue;
           const int mk = (1 << m) - 1;
           const int slot = ((int)((pp >> 27) & 3u) << (2 * m)) | ((Qrel & mk) << m) | (Prel & mk);
-          const int ai = ((rely * k + relx) << SLsh) + slot;
+          const int ai = (rely * k + relx) * TSTR + slot;
           const float amp = __int_as_float(S.sp[rec.y].w);
           if (fixed) {
             // a_j c in FP32, exact scaling by 2^sh (folded into amp), rounded
@@ -407,31 +549,35 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
       PT_MARK(4);
     }
 
+    const float dq = ldexpf(1.0f, -sh);
     // Write the super-tile: each tile's TSL slots are contiguous in the
     // buffer; slots of levels finer than lmin are zero.
-    const float dq = ldexpf(1.0f, -sh);
-    constexpr int Q4 = TSL / 2;  // float4 per tile
-    const int tpg = NT >= Q4 ? NT / Q4 : 1;  // tiles per pass
-    const int qstep = NT >= Q4 ? Q4 : NT;
-    int j = 0, t = NT >= Q4 ? tid / Q4 : 0;  // this thread's tile (row j, column t)
-    while (t >= kx) { t -= kx; ++j; }
-    while (j < ky) {
-      float4* dst = reinterpret_cast<float4*>(wbuf + ((size_t)(Sy + j) * ntx + Sx + t) * TSL);
-      const int src0 = ((j * k + t) << SLsh) >> 1;
-      for (int q = NT >= Q4 ? tid % Q4 : tid; q < Q4; q += qstep) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (2 * q < SL) {
-          v = acc4[src0 + q];
-          if (fixed) {
-            const int4 iv = reinterpret_cast<const int4*>(acc4)[src0 + q];
-            v = make_float4((float)iv.x * dq, (float)iv.y * dq, (float)iv.z * dq, (float)iv.w * dq);
-          }
-        }
-        __stcs(dst + q, v);
-      }
-      t += tpg;
+    if (wbuf != nullptr) {
+      constexpr int Q4 = TSL / 2;  // float4 per tile
+      const int tpg = NT >= Q4 ? NT / Q4 : 1;  // tiles per pass
+      const int qstep = NT >= Q4 ? Q4 : NT;
+      int j = 0, t = NT >= Q4 ? tid / Q4 : 0;  // this thread's tile (row j, column t)
       while (t >= kx) { t -= kx; ++j; }
+      while (j < ky) {
+        float4* dst = reinterpret_cast<float4*>(wbuf + ((size_t)(Sy + j) * ntx + Sx + t) * TSL);
+        const int src0 = ((j * k + t) * TSTR) >> 1;
+        for (int q = NT >= Q4 ? tid % Q4 : tid; q < Q4; q += qstep) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (2 * q < SL) {
+            v = acc4[src0 + q];
+            if (fixed) {
+              const int4 iv = reinterpret_cast<const int4*>(acc4)[src0 + q];
+              v = make_float4((float)iv.x * dq, (float)iv.y * dq, (float)iv.z * dq, (float)iv.w * dq);
+            }
+          }
+          __stcs(dst + q, v);
+        }
+        t += tpg;
+        while (t >= kx) { t -= kx; ++j; }
+      }
     }
+    if (L >= 2 && (J.u != nullptr || J.bits != nullptr))
+      supertile_inverse<L>(S.acc, fixed, dq, SLsh, lmin, k, kx, ky, Sx, Sy, J, tid, NT);
     PT_MARK(5);
   }
 #ifdef WASABI_PHASE_TIMERS
