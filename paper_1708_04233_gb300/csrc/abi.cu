@@ -323,6 +323,11 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   c.take<long long>((size_t)n_depths);                               // nr
   c.take<float>(1);                                                  // cmax
   c.take<unsigned>(1);                                               // levels
+  {
+    const int unit = std::max(1 << levels, 32);  // super-tile sides: multiples of 32 and of 2^L
+    for (int T = unit; T <= 256 && lut->ncode < kMaxCodes; T += unit) lut->code_k[lut->ncode++] = T >> levels;
+  }
+  c.take<uint32_t>((size_t)lut->ncode * (size_t)base);              // plane codes
   const size_t persist_bytes = align_up(c.off, 256);
   cudaError_t e = cudaMallocAsync(&lut->block, persist_bytes, s);
   if (e != cudaSuccess) { delete lut; set_error("build_lut: cudaMallocAsync: %s", cudaGetErrorString(e)); return WASABI_E_NOMEM; }
@@ -339,6 +344,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   lut->nr_dev = c.take<long long>((size_t)n_depths);
   lut->cmax = c.take<float>(1);
   lut->levels = c.take<unsigned>(1);
+  lut->code = c.take<uint32_t>((size_t)lut->ncode * (size_t)base);
 
   // Build scratch.
   Carver sc;
@@ -375,6 +381,8 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   a.z_dev = z_dev; a.R2_dev = R2_dev; a.target_dev = target_dev;
   a.nr_dev = lut->nr_dev; a.pos = lut->pos; a.val = lut->val; a.val16 = lut->val16; a.scale = lut->scale;
   a.tile_off = lut->tile_off; a.meta = lut->meta_dev; a.cmax = lut->cmax; a.levels = lut->levels;
+  a.code = lut->code; a.ncode = lut->ncode; a.total = base;
+  for (int i = 0; i < kMaxCodes; ++i) a.code_k[i] = lut->code_k[i];
   a.status = status;
 
   bool okc = true;
@@ -615,7 +623,7 @@ wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* poi
   e = launch_binning(ba, s);
   if (e != cudaSuccess) return cuda_fail("superpose: binning", e);
   SuperposeArgs sa;
-  sa.lut = lut->view();
+  sa.lut = lut->view(cell >> lut->L);
   sa.jobs = b.jobs; sa.batch = b.batch; sa.cell = cell; sa.reach = lut->reach;
   sa.acc_float = env_int("WASABI_ACC_FLOAT", 0) != 0;
   sa.status = status; sa.threads = threads; sa.grid = sms;

@@ -85,7 +85,7 @@ cudaError_t enqueue_batch(wasabi_batch* b, cudaStream_t s, int* status, int sms,
   ba.track_amax = 1; ba.status = status; ba.grid = sms * 4;
   if ((e = launch_binning(ba, s)) != cudaSuccess) return e;
   SuperposeArgs sa;
-  sa.lut = lut->view();
+  sa.lut = lut->view(b->cell >> lut->L);
   sa.jobs = b->jobs_dev; sa.batch = b->batch_dev; sa.cell = b->cell; sa.reach = lut->reach;
   sa.acc_float = 0; sa.status = status; sa.threads = b->threads; sa.grid = sms;
   if ((e = launch_superpose(sa, s)) != cudaSuccess) return e;

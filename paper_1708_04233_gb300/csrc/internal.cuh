@@ -25,6 +25,35 @@ __host__ __device__ inline uint32_t pack_pos(int p, int q, int lev, int band) {
   return (uint32_t)p | ((uint32_t)q << 12) | ((uint32_t)lev << 24) | ((uint32_t)band << 27);
 }
 
+// Superposition accumulator of one super-tile of k x k tiles (shared memory):
+// per kept level l, square planes of side G_l = (k + 2) 2^(L-l) cells -- the
+// super-tile plus a guard band one tile wide on every side -- four at level L
+// (approximation and three details), three at finer levels, coarse levels
+// first.  A coefficient's plane code is (l << 29) | (band plane * G_l^2 +
+// q G_l + p) with (p, q) its window-relative position: adding a survivor's
+// per-level base (its shift of Eq. (2), the guard and the level's offset)
+// gives the accumulator index, with no bounds test (every visited coefficient
+// lands inside the guard band by construction of the LUT ranges).
+__host__ __device__ inline int plane_side(int k, int L, int l) { return (k + 2) << (L - l); }
+__host__ __device__ inline int plane_count(int L, int l) { return l == L ? 4 : 3; }
+__host__ __device__ inline uint32_t plane_code(uint32_t pos, int L, int k) {
+  const int p = (int)(pos & 4095u), q = (int)((pos >> 12) & 4095u);
+  const int lev = (int)((pos >> 24) & 7u), band = (int)((pos >> 27) & 3u);
+  if (lev < 1 || lev > L) return 0;  // unused capacity: never visited
+  const int G = plane_side(k, L, lev);
+  const int bi = lev == L ? band : band - 1;
+  return ((uint32_t)lev << 29) | (uint32_t)(bi * G * G + q * G + p);
+}
+// Accumulator size (complex elements) for levels lmin..L.
+__host__ __device__ inline int plane_total(int k, int L, int lmin) {
+  int n = 0;
+  for (int l = lmin; l <= L; ++l) n += plane_count(L, l) * plane_side(k, L, l) * plane_side(k, L, l);
+  return n;
+}
+// Most plane codes a LUT keeps: one per super-tile width k the superposition
+// can use (super-tiles are multiples of 32 pixels, at most 256).
+constexpr int kMaxCodes = 8;
+
 // Slot of (level, band, ix, iy) inside a 2^L x 2^L tile (m = L - level).
 __host__ __device__ inline int tile_slot(int L, int lev, int band, int ix, int iy) {
   const int m = L - lev;
@@ -72,6 +101,7 @@ struct LutView {
   const DepthMeta* meta;
   const float* cmax;      // largest |re| or |im| of any kept coefficient
   int lmin;               // finest level with a kept coefficient
+  const uint32_t* code;   // plane codes for the launch's super-tile width (see plane_code)
 };
 
 // ------------------------------------------------------------------ launchers
@@ -102,6 +132,10 @@ struct LutBuildArgs {
   const DepthMeta* meta;
   float* cmax;              // out: largest |re| or |im| kept (zeroed by caller)
   unsigned* levels;         // out: bit l set if a level-l coefficient is kept (zeroed by caller)
+  uint32_t* code;           // out: ncode x total plane codes (see plane_code)
+  int ncode;
+  int code_k[kMaxCodes];    // super-tile width (tiles) of each code array
+  long long total;          // LUT entries (all depths' capacities)
   int* status;
 };
 cudaError_t launch_lut_build(const LutBuildArgs& a, cudaStream_t s);

@@ -495,6 +495,15 @@ __global__ void __launch_bounds__(256) encode_kernel(LutBuildArgs a) {
   if (lane == 0) a.scale[e >> 5] = s;
 }
 
+// Plane codes of every LUT entry for each super-tile width (plane_code).
+__global__ void plane_code_kernel(LutBuildArgs a) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.total) return;
+  const uint32_t p = a.pos[e];
+  const int c = blockIdx.y;
+  a.code[c * a.total + e] = plane_code(p, a.L, a.code_k[c]);
+}
+
 template <int L>
 cudaError_t launch_psf_haar(const LutBuildArgs& a, int max_nb, cudaStream_t s) {
   constexpr int TSL = 1 << (2 * L);
@@ -534,6 +543,11 @@ cudaError_t launch_lut_build(const LutBuildArgs& a, cudaStream_t s) {
     const long long blocks = (a.max_cap + 31) / 32;
     const dim3 egrid((unsigned)((blocks + 7) / 8), (unsigned)a.D);
     encode_kernel<<<egrid, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (a.ncode > 0 && a.total > 0) {
+    const dim3 cgrid((unsigned)((a.total + 255) / 256), (unsigned)a.ncode);
+    plane_code_kernel<<<cgrid, 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

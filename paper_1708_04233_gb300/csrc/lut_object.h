@@ -28,6 +28,9 @@ struct wasabi_lut {
   long long* nr_dev = nullptr;
   float* cmax = nullptr;
   unsigned* levels = nullptr;  // bit l: a level-l coefficient is kept
+  uint32_t* code = nullptr;    // ncode x total_cap plane codes, one array per super-tile width
+  int ncode = 0;
+  int code_k[wsb::kMaxCodes] = {};
   int lmin = 1;                // finest kept level (host copy)
   // Autotuned superposition configurations: hologram size class -> (super-tile, threads).
   mutable std::mutex tune_mu;
@@ -38,6 +41,14 @@ struct wasabi_lut {
     v.D = D; v.W = W; v.L = L; v.nwt = nwt; v.dtype = dtype;
     v.pos = pos; v.val = val; v.val16 = val16; v.scale = scale;
     v.tile_off = tile_off; v.meta = meta_dev; v.cmax = cmax; v.lmin = lmin;
+    v.code = nullptr;
+    return v;
+  }
+  // The view for super-tiles of k x k tiles (null codes if k is not built).
+  wsb::LutView view(int k) const {
+    wsb::LutView v = view();
+    for (int i = 0; i < ncode; ++i)
+      if (code_k[i] == k) v.code = code + (size_t)i * total_cap;
     return v;
   }
 };

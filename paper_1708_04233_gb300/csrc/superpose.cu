@@ -1,27 +1,31 @@
-// Superposition in the wavelet domain (Eq. (2)), owner-computes form.
+// Superposition in the wavelet domain (Eq. (2)), owner-computes form, with
+// the inverse transform and binarisation fused into its epilogue.
 //
-// The hologram's tile-major wavelet buffer is cut into super-tiles of T x T
-// pixels (k = T / 2^L tiles a side).  Persistent CTAs (several per SM, so
-// that one CTA's latency-bound phases overlap another's) claim super-tiles
-// from a global counter; for each one a CTA
-//   1. zeroes its shared-memory accumulator: k*k tiles x SL slots, where SL
-//      covers only the levels the LUT actually holds (levels finer than the
-//      finest kept level are known to stay zero);
+// The hologram is cut into super-tiles of T x T pixels (k = T / 2^L tiles a
+// side).  Persistent CTAs (two per SM, so that one CTA's latency-bound
+// phases overlap the other's) claim super-tiles from a global counter; for
+// each one a CTA
+//   1. zeroes its shared-memory accumulator: one plane per kept (level, band)
+//      covering the super-tile and a guard band one tile wide (levels finer
+//      than the LUT's finest kept level are known to stay zero);
 //   2. scans the binned points of the cell rows within reach and keeps the
 //      survivors whose footprint (window-tile box of their depth, shifted,
-//      plus one tile of carry) meets the super-tile, with the per-level
-//      shift of Eq. (2) relative to the super-tile origin;
+//      plus one tile of carry) meets the super-tile; for each kept level it
+//      folds the point's shift of Eq. (2) into one accumulator base;
 //   3. turns every survivor into one LUT range per window-tile row that can
 //      land in the super-tile (contiguous by construction of the LUT); one
 //      block-wide scan both drops empty ranges and prefix-sums their lengths
 //      into a flat list of coefficient visits;
 //   4. splits the visits evenly over the warps; each warp walks a contiguous
 //      slice 32 visits at a time (coalesced LUT loads), finds each lane's
-//      range with one shared-memory load and a warp OR-reduction, applies the
-//      shift rule and adds a_j * c into shared memory;
-//   5. writes the finished super-tile once with streaming vector stores,
-//      zeros for the slots of absent levels.
-// Every buffer element is written exactly once: no global atomics and no
+//      range with one shared-memory load and a warp OR-reduction, and adds
+//      a_j * c at base + plane code (no bounds test: coefficients that land
+//      outside the super-tile fall into the guard band and are dropped);
+//   5. writes the finished super-tile once: to the tile-major wavelet buffer
+//      (streaming vector stores, zeros for absent levels) and/or, through the
+//      inverse transform in shared memory, as the complex field or the packed
+//      binary hologram.
+// Every output element is written exactly once: no global atomics and no
 // zeroing pass.  Shared-memory atomics resolve collisions between survivors.
 #include <algorithm>
 
@@ -36,9 +40,9 @@ namespace {
 constexpr int kMaxCellRows = 128;
 constexpr int kRangeCap = 2048;  // LUT ranges per batch
 constexpr int kPerMax = 8;       // range slots per thread (block size >= 256)
-// Accumulator tiles are SL + kTilePad complex apart, so that the tiles a warp
-// reads in the inverse epilogue start in different shared-memory banks.
-constexpr int kTilePad = 4;
+// Dynamic shared memory per CTA that still lets two CTAs share an SM (with
+// the kernel's static shared memory and the per-CTA reservation).
+constexpr size_t kTwoCtaSmem = 104 * 1024;
 
 __device__ __forceinline__ int floor_div(int a, int b) {
   const int q = a / b;
@@ -100,9 +104,9 @@ __device__ __forceinline__ int last_le(const int* pre, int lo, int hi, int v) {
 }
 
 struct Smem {
-  float2* acc;   // k*k tiles x SL slots
-  int4* sp;      // survivors: Ax, Ay, depth, amplitude bits (times 2^sh in fixed point)
-  int2* sb;      // survivors: per level l, shift_l(x - W/2) - Sx 2^(L-l) and the same in y
+  float2* acc;   // accumulator planes (plane_total complex), see plane_code
+  int4* sp;      // survivors: Ax, Ay, depth, unused
+  int2* svb;     // survivors x kept levels: accumulator base of the level, amplitude bits
   int2* rrec;    // ranges: LUT offset minus visit prefix, survivor
   int* rpre;     // ranges: visit prefix (kRangeCap + 1)
   int2* dbox;    // depths: tlo, thi
@@ -116,24 +120,22 @@ __host__ __device__ inline int survivor_cap(int k) {
 __host__ __device__ inline size_t smem_layout(int T, int L, int lmin, int D, Smem* s, unsigned char* base) {
   const int k = T >> L;
   const int P = survivor_cap(k);
-  const size_t SL = (size_t)1 << (2 * (L - lmin + 1));
-  const size_t TSTR = SL + kTilePad;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
     off = (off + bytes + 15) & ~(size_t)15;
     return base ? base + o : nullptr;
   };
-  unsigned char* p0 = take((size_t)k * k * TSTR * sizeof(float2));
+  unsigned char* p0 = take((size_t)plane_total(k, L, lmin) * sizeof(float2));
   unsigned char* p1 = take((size_t)P * sizeof(int4));
-  unsigned char* p2 = take((size_t)P * (L + 1) * sizeof(int2));
+  unsigned char* p2 = take((size_t)P * (L - lmin + 1) * sizeof(int2));
   unsigned char* p3 = take((size_t)kRangeCap * sizeof(int2));
   unsigned char* p4 = take((size_t)(kRangeCap + 1) * sizeof(int));
   unsigned char* p5 = take((size_t)D * sizeof(int2));
   if (s) {
     s->acc = reinterpret_cast<float2*>(p0);
     s->sp = reinterpret_cast<int4*>(p1);
-    s->sb = reinterpret_cast<int2*>(p2);
+    s->svb = reinterpret_cast<int2*>(p2);
     s->rrec = reinterpret_cast<int2*>(p3);
     s->rpre = reinterpret_cast<int*>(p4);
     s->dbox = reinterpret_cast<int2*>(p5);
@@ -160,21 +162,24 @@ __host__ __device__ inline size_t smem_layout(int T, int L, int lmin, int D, Sme
 
 // Inverse transform (Sec. 1, step 3) and binarisation (Sec. 2) of a finished
 // super-tile, straight from the shared-memory accumulator: the wavelet
-// buffer never goes to global memory.  Slots of levels finer than lmin were
-// never accumulated and read as zero.  Each thread rebuilds 4 x 4 pixel
-// blocks in the add order of the separate inverse kernel, from the same FP32
+// buffer never goes to global memory.  Levels finer than lmin were never
+// accumulated and read as zero.  Each thread rebuilds 4 x 4 pixel blocks in
+// the add order of the separate inverse kernel, from the same FP32
 // coefficient values that kernel would read, so the two paths give the same
-// pixels bit for bit.  Eight consecutive lanes cover 32 pixels of a row,
-// which is one 32-bit word of the packed binary hologram (the super-tile side
-// is a multiple of 32).
-template <int L>
-__device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed, float dq, int SLsh, int lmin, int k,
-                                                  int kx, int ky, int Sx, int Sy, const JobDev& J, int tid,
+// pixels.  Eight consecutive lanes cover 32 pixels of a row, which is one
+// 32-bit word of the packed binary hologram (the super-tile side is a
+// multiple of 32), and read neighbouring accumulator cells (no bank
+// conflicts).  lvC[l], lvG[l], lvPS[l]: index of the level's first
+// super-tile cell (past the guard), plane side and plane size.
+// RE_ONLY (bits output alone): only real parts are read and transformed; the
+// inverse transform acts on real and imaginary parts separately, so Re u is
+// unchanged.
+template <int L, bool RE_ONLY>
+__device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed, float dq, int lmin, int k,
+                                                  int kx, int ky, int Sx, int Sy, const JobDev& J,
+                                                  const int* lvC, const int* lvG, const int* lvPS, int tid,
                                                   int NT) {
   if constexpr (L >= 2) {
-    constexpr int TS = 1 << L;
-    const int SL = 1 << SLsh;
-    const int TSTR = SL + kTilePad;
     const int bpr = (k << L) >> 2;           // 4 x 4 blocks per super-tile row
     const int total = bpr * ((ky << L) >> 2);
     const int xvalid = (kx << L) >> 2;       // block columns inside the hologram
@@ -185,13 +190,16 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
     const int X0 = Sx << L, Y0 = Sy << L;
     const int xend = (Sx + kx) << L;
     const int* acci = reinterpret_cast<const int*>(acc);
-    auto coef = [&](int tb, int slot) -> float2 {
-      if (slot >= SL) return make_float2(0.f, 0.f);
+    // Coefficient of level l, band plane bi, at super-tile cell (cx, cy).
+    auto coef = [&](int l, int bi, int cx, int cy) -> float2 {
+      if (l < lmin) return make_float2(0.f, 0.f);
+      const int i = lvC[l] + bi * lvPS[l] + cy * lvG[l] + cx;
+      if (RE_ONLY) return make_float2(fixed ? (float)acci[2 * i] * dq : acc[i].x, 0.f);
       if (fixed) {
-        const int2 q = reinterpret_cast<const int2*>(acci)[tb + slot];
+        const int2 q = reinterpret_cast<const int2*>(acci)[i];
         return make_float2((float)q.x * dq, (float)q.y * dq);
       }
-      return acc[tb + slot];
+      return acc[i];
     };
     for (int b0 = 0; b0 < total; b0 += NT) {  // uniform trip count: whole warps shuffle
       const int b = b0 + tid;
@@ -199,25 +207,21 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
       const bool inrow = b < total;
       const bool valid = inrow && bcol < xvalid;
       const int px0 = 4 * bcol, py0 = 4 * brow;  // block origin in the super-tile
-      const int tb = valid ? ((py0 >> L) * k + (px0 >> L)) * TSTR : 0;
-      const int bx = (px0 & (TS - 1)) >> 2, by = (py0 & (TS - 1)) >> 2;
       float2 s1[2][2] = {{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}};
       if (valid) {  // the block's four level-1 scaling values
         // Levels L .. 3: the block lies inside one level-(l-1) cell.
-        float2 s = coef(tb, 0);
+        float2 s = coef(L, 0, px0 >> L, py0 >> L);
 #pragma unroll
         for (int l = L; l >= 3; --l) {
-          const int m = L - l;
-          const int o = (((4 * by) >> l) << m) + ((4 * bx) >> l);
-          const float2 lh = coef(tb, (1 << (2 * m)) + o), hl = coef(tb, (2 << (2 * m)) + o),
-                       hh = coef(tb, (3 << (2 * m)) + o);
-          s = ipick(s, lh, hl, hh, ((4 * bx) >> (l - 1)) & 1, ((4 * by) >> (l - 1)) & 1);
+          const int cx = px0 >> l, cy = py0 >> l;
+          const int bi = l == L ? 1 : 0;  // plane of band 1 at this level
+          const float2 lh = coef(l, bi, cx, cy), hl = coef(l, bi + 1, cx, cy), hh = coef(l, bi + 2, cx, cy);
+          s = ipick(s, lh, hl, hh, (px0 >> (l - 1)) & 1, (py0 >> (l - 1)) & 1);
         }
-        // Level 2 at (bx, by) -> four level-1 scaling values.
-        const int m = L - 2;
-        const int o = (by << m) + bx;
-        const float2 lh = coef(tb, (1 << (2 * m)) + o), hl = coef(tb, (2 << (2 * m)) + o),
-                     hh = coef(tb, (3 << (2 * m)) + o);
+        // Level 2 at the block's own cell -> four level-1 scaling values.
+        const int b2 = L == 2 ? 1 : 0;
+        const float2 lh = coef(2, b2, px0 >> 2, py0 >> 2), hl = coef(2, b2 + 1, px0 >> 2, py0 >> 2),
+                     hh = coef(2, b2 + 2, px0 >> 2, py0 >> 2);
 #pragma unroll
         for (int ay = 0; ay < 2; ++ay)
 #pragma unroll
@@ -225,30 +229,32 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
       }
       const int x0 = X0 + px0;
       const int xw = X0 + 32 * (bcol >> 3);  // first pixel of this lane group's bit word
-      // Stores one pixel row of the block: complex values and/or its four bits
-      // (eight lanes OR their nibbles into the word at xw).
-      auto put_row = [&](int y, float2 p0, float2 p1, float2 p2, float2 p3) {
-        if (u != nullptr && valid) {
+      // One pixel row of the block: complex values, and its bit word (eight
+      // lanes OR their nibbles into the word at xw).
+      auto put_u = [&](int y, float2 p0, float2 p1, float2 p2, float2 p3) {
+        if (!RE_ONLY && u != nullptr && valid) {
           float4* dst = reinterpret_cast<float4*>(u + (size_t)y * w + x0);
           __stcs(dst, make_float4(p0.x, p0.y, p1.x, p1.y));
           __stcs(dst + 1, make_float4(p2.x, p2.y, p3.x, p3.y));
         }
-        if (bits != nullptr) {
-          unsigned nib = 0;
-          if (valid)
-            nib = (p0.x > 0.f ? 1u : 0u) | (p1.x > 0.f ? 2u : 0u) | (p2.x > 0.f ? 4u : 0u) | (p3.x > 0.f ? 8u : 0u);
-          unsigned v = nib << (4 * (lane & 7));
-          v |= __shfl_xor_sync(0xffffffffu, v, 1);
-          v |= __shfl_xor_sync(0xffffffffu, v, 2);
-          v |= __shfl_xor_sync(0xffffffffu, v, 4);
-          if ((lane & 7) == 0 && inrow && xw < xend) {
-            const size_t byte0 = ((size_t)y * w + xw) >> 3;
-            if (xw + 32 <= xend && (w & 31) == 0) {
-              *reinterpret_cast<unsigned*>(bits + byte0) = v;
-            } else {
-              const int nb = min(4, (xend - xw) >> 3);
-              for (int q = 0; q < nb; ++q) bits[byte0 + q] = (uint8_t)(v >> (8 * q));
-            }
+      };
+      auto word = [&](float r0, float r1, float r2, float r3) -> unsigned {
+        unsigned nib = 0;
+        if (valid) nib = (r0 > 0.f ? 1u : 0u) | (r1 > 0.f ? 2u : 0u) | (r2 > 0.f ? 4u : 0u) | (r3 > 0.f ? 8u : 0u);
+        unsigned v = nib << (4 * (lane & 7));
+        v |= __shfl_xor_sync(0xffffffffu, v, 1);
+        v |= __shfl_xor_sync(0xffffffffu, v, 2);
+        v |= __shfl_xor_sync(0xffffffffu, v, 4);
+        return v;
+      };
+      auto put_bits = [&](int y, unsigned v) {
+        if ((lane & 7) == 0 && inrow && xw < xend) {
+          const size_t byte0 = ((size_t)y * w + xw) >> 3;
+          if (xw + 32 <= xend && (w & 31) == 0) {
+            *reinterpret_cast<unsigned*>(bits + byte0) = v;
+          } else {
+            const int nb = min(4, (xend - xw) >> 3);
+            for (int q = 0; q < nb; ++q) bits[byte0 + q] = (uint8_t)(v >> (8 * q));
           }
         }
       };
@@ -264,8 +270,13 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
             pa = make_float2(s1[ay][0].x * 0.5f, s1[ay][0].y * 0.5f);
             pb = make_float2(s1[ay][1].x * 0.5f, s1[ay][1].y * 0.5f);
           }
-          put_row(y0 + 2 * ay, pa, pa, pb, pb);
-          put_row(y0 + 2 * ay + 1, pa, pa, pb, pb);
+          put_u(y0 + 2 * ay, pa, pa, pb, pb);
+          put_u(y0 + 2 * ay + 1, pa, pa, pb, pb);
+          if (bits != nullptr) {  // both rows of the pair are equal
+            const unsigned v = word(pa.x, pa.x, pb.x, pb.x);
+            put_bits(y0 + 2 * ay, v);
+            put_bits(y0 + 2 * ay + 1, v);
+          }
         }
       } else {
         // Level 1, one pair of pixel rows at a time -> 2 x 4 pixels.
@@ -276,41 +287,47 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
           for (int ax = 0; ax < 2; ++ax) {
             float2 l1 = make_float2(0.f, 0.f), h1 = l1, d1 = l1;
             if (valid) {
-              const int m = L - 1;
-              const int o = ((2 * by + ay) << m) + 2 * bx + ax;
-              l1 = coef(tb, (1 << (2 * m)) + o);
-              h1 = coef(tb, (2 << (2 * m)) + o);
-              d1 = coef(tb, (3 << (2 * m)) + o);
+              const int cx = (px0 >> 1) + ax, cy = (py0 >> 1) + ay;
+              l1 = coef(1, 0, cx, cy);
+              h1 = coef(1, 1, cx, cy);
+              d1 = coef(1, 2, cx, cy);
             }
 #pragma unroll
             for (int qy = 0; qy < 2; ++qy)
 #pragma unroll
               for (int qx = 0; qx < 2; ++qx) px[qy][2 * ax + qx] = ipick(s1[ay][ax], l1, h1, d1, qx, qy);
           }
-          put_row(y0 + 2 * ay, px[0][0], px[0][1], px[0][2], px[0][3]);
-          put_row(y0 + 2 * ay + 1, px[1][0], px[1][1], px[1][2], px[1][3]);
+#pragma unroll
+          for (int qy = 0; qy < 2; ++qy) {
+            put_u(y0 + 2 * ay + qy, px[qy][0], px[qy][1], px[qy][2], px[qy][3]);
+            if (bits != nullptr) put_bits(y0 + 2 * ay + qy, word(px[qy][0].x, px[qy][1].x, px[qy][2].x, px[qy][3].x));
+          }
         }
       }
     }
   }
 }
 
+
 template <int L, int DT>
 __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
   constexpr int TSL = 1 << (2 * L);
+  static_assert(TSL <= kRangeCap, "the write-out slot table lives in the range records");
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = a.cell;
   const int k = T >> L;
   const int P = survivor_cap(k);
   const int lmin = a.lut.lmin;
-  const int SLsh = 2 * (L - lmin + 1);  // log2 of accumulator slots per tile
-  const int SL = 1 << SLsh;
-  const int TSTR = SL + kTilePad;  // accumulator tile stride (complex)
+  const int NLV = L - lmin + 1;  // kept levels
+  const int NA = plane_total(k, L, lmin);  // accumulator size (complex)
   Smem S;
   smem_layout(T, L, lmin, a.lut.D, &S, smem);
   __shared__ int s_st, s_n, s_total;
   __shared__ int s_rowstart[kMaxCellRows], s_rowpre[kMaxCellRows + 1];
   __shared__ unsigned long long warp_buf[32];
+  // Per level l: index of the first super-tile cell past the guard, plane
+  // side, plane size (see plane_code).
+  __shared__ int lvC[8], lvG[8], lvPS[8];
 
   const LutView& lut = a.lut;
   const int NT = blockDim.x;
@@ -323,6 +340,16 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
   for (int d = tid; d < lut.D; d += NT) {
     const DepthMeta m = lut.meta[d];
     S.dbox[d] = make_int2(m.tlo, m.thi);
+  }
+  if (tid == 0) {
+    int base = 0;
+    for (int l = L; l >= 1; --l) {
+      const int G = plane_side(k, L, l), g = 1 << (L - l);
+      lvG[l] = G;
+      lvPS[l] = G * G;
+      lvC[l] = base + g * G + g;
+      if (l >= lmin) base += plane_count(L, l) * G * G;
+    }
   }
   int* counter = &a.batch->counter;
   const float amax_cmax = a.batch->amax * __ldg(lut.cmax);
@@ -358,7 +385,7 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
     const int Sx = (st % nstx) * k, Sy = (st / nstx) * k;
     const int kx = min(k, ntx - Sx), ky = min(k, nty - Sy);
 
-    for (int i = tid; i < (k * k * TSTR) / 2; i += NT) acc4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < NA / 2; i += NT) acc4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     // Cell rows within reach of the super-tile, one thread per row.
     const int X0 = Sx << L, X1 = (Sx + kx) << L, Y0 = Sy << L, Y1 = (Sy + ky) << L;
@@ -421,13 +448,14 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
             Ay + bx.y + 1 >= Sy) {
           const int s = atomicAdd(&s_n, 1);
           const float amp = __int_as_float(p.z) * (fixed ? qs : 1.0f);
-          S.sp[s] = make_int4(Ax, Ay, p.w, __float_as_int(amp));
+          S.sp[s] = make_int4(Ax, Ay, p.w, 0);
           // shift_l(X) of Eq. (2): floor((X + half * 2^(l-1)) / 2^l), made
-          // relative to the super-tile origin in level-l units.
+          // relative to the super-tile origin in level-l units, folded with
+          // the level's accumulator offset into one base per level.
           for (int l = lmin; l <= L; ++l) {
             const int hb = half << (l - 1);
-            S.sb[s * (L + 1) + l] =
-                make_int2(((X + hb) >> l) - (Sx << (L - l)), ((Y + hb) >> l) - (Sy << (L - l)));
+            const int ox = ((X + hb) >> l) - (Sx << (L - l)), oy = ((Y + hb) >> l) - (Sy << (L - l));
+            S.svb[s * NLV + (l - lmin)] = make_int2(lvC[l] + oy * lvG[l] + ox, __float_as_int(amp));
           }
         }
       }
@@ -512,36 +540,27 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
             if (ee[u] >= 0) {
-              ppu[u] = __ldg(&lut.pos[ee[u]]);
+              ppu[u] = __ldg(&lut.code[ee[u]]);
               vvu[u] = lut_value<DT>(lut, ee[u]);
             }
           }
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
-          if (ee[u] < 0) continue;
-          const int2 rec = make_int2(0, sv[u]);
-          const uint32_t pp = ppu[u];
-          const float2 v = vvu[u];
-          const int lev = (pp >> 24) & 7;
-          const int2 bs = S.sb[rec.y * (L + 1) + lev];
-          const int m = L - lev;
-          const int Prel = (int)(pp & 4095u) + bs.x;
-          const int Qrel = (int)((pp >> 12) & 4095u) + bs.y;
-          const int relx = Prel >> m, rely = Qrel >> m;
-          if ((unsigned)relx >= (unsigned)kx || (unsigned)rely >= (unsigned)ky) continue;
-          const int mk = (1 << m) - 1;
-          const int slot = ((int)((pp >> 27) & 3u) << (2 * m)) | ((Qrel & mk) << m) | (Prel & mk);
-          const int ai = (rely * k + relx) * TSTR + slot;
-          const float amp = __int_as_float(S.sp[rec.y].w);
-          if (fixed) {
-            // a_j c in FP32, exact scaling by 2^sh (folded into amp), rounded
-            // to the nearest integer; the integer sums are exact.
-            atomicAdd(&acci[2 * ai], __float2int_rn(amp * v.x));
-            atomicAdd(&acci[2 * ai + 1], __float2int_rn(amp * v.y));
-          } else {
-            atomicAdd(&S.acc[ai].x, amp * v.x);
-            atomicAdd(&S.acc[ai].y, amp * v.y);
-          }
+            if (ee[u] < 0) continue;
+            const uint32_t pe = ppu[u];
+            const float2 v = vvu[u];
+            const int2 sb = S.svb[sv[u] * NLV + (int)(pe >> 29) - lmin];
+            const int ai = (int)(pe & 0x1fffffffu) + sb.x;
+            const float amp = __int_as_float(sb.y);
+            if (fixed) {
+              // a_j c in FP32, exact scaling by 2^sh (folded into amp), rounded
+              // to the nearest integer; the integer sums are exact.
+              atomicAdd(&acci[2 * ai], __float2int_rn(amp * v.x));
+              atomicAdd(&acci[2 * ai + 1], __float2int_rn(amp * v.y));
+            } else {
+              atomicAdd(&S.acc[ai].x, amp * v.x);
+              atomicAdd(&S.acc[ai].y, amp * v.y);
+            }
           }
         }
       }
@@ -550,34 +569,49 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
     }
 
     const float dq = ldexpf(1.0f, -sh);
-    // Write the super-tile: each tile's TSL slots are contiguous in the
-    // buffer; slots of levels finer than lmin are zero.
+    // Write the super-tile's tiles to the tile-major buffer: each tile's TSL
+    // slots are contiguous there; slots of levels finer than lmin are zero.
+    // Slot -> accumulator offset table (in the free range records): offset of
+    // the slot's cell for tile (0, 0), plane side and m = L - level.
     if (wbuf != nullptr) {
-      constexpr int Q4 = TSL / 2;  // float4 per tile
-      const int tpg = NT >= Q4 ? NT / Q4 : 1;  // tiles per pass
-      const int qstep = NT >= Q4 ? Q4 : NT;
-      int j = 0, t = NT >= Q4 ? tid / Q4 : 0;  // this thread's tile (row j, column t)
-      while (t >= kx) { t -= kx; ++j; }
-      while (j < ky) {
-        float4* dst = reinterpret_cast<float4*>(wbuf + ((size_t)(Sy + j) * ntx + Sx + t) * TSL);
-        const int src0 = ((j * k + t) * TSTR) >> 1;
-        for (int q = NT >= Q4 ? tid % Q4 : tid; q < Q4; q += qstep) {
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (2 * q < SL) {
-            v = acc4[src0 + q];
+      int2* tab = S.rrec;
+      for (int q = tid; q < TSL; q += NT) {
+        int lev, band, ix, iy;
+        slot_decode(L, q, &lev, &band, &ix, &iy);
+        const int bi = lev == L ? band : band - 1;
+        tab[q] = lev >= lmin ? make_int2(lvC[lev] + bi * lvPS[lev] + iy * lvG[lev] + ix, (lvG[lev] << 8) | (L - lev))
+                             : make_int2(-1, 0);
+      }
+      __syncthreads();
+      const int nq = kx * ky * (TSL / 2);  // pairs of slots
+      for (int i = tid; i < nq; i += NT) {
+        const int tile = i / (TSL / 2), q = i - tile * (TSL / 2);
+        const int tj = tile / kx, tt = tile - tj * kx;
+        float v[4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int2 e = tab[2 * q + h];
+          float2 c = make_float2(0.f, 0.f);
+          if (e.x >= 0) {
+            const int ci = e.x + ((tj * (e.y >> 8) + tt) << (e.y & 255));
             if (fixed) {
-              const int4 iv = reinterpret_cast<const int4*>(acc4)[src0 + q];
-              v = make_float4((float)iv.x * dq, (float)iv.y * dq, (float)iv.z * dq, (float)iv.w * dq);
+              const int2 iv = reinterpret_cast<const int2*>(acci)[ci];
+              c = make_float2((float)iv.x * dq, (float)iv.y * dq);
+            } else {
+              c = S.acc[ci];
             }
           }
-          __stcs(dst + q, v);
+          v[2 * h] = c.x;
+          v[2 * h + 1] = c.y;
         }
-        t += tpg;
-        while (t >= kx) { t -= kx; ++j; }
+        float4* dst = reinterpret_cast<float4*>(wbuf + ((size_t)(Sy + tj) * ntx + Sx + tt) * TSL) + q;
+        __stcs(dst, make_float4(v[0], v[1], v[2], v[3]));
       }
     }
-    if (L >= 2 && (J.u != nullptr || J.bits != nullptr))
-      supertile_inverse<L>(S.acc, fixed, dq, SLsh, lmin, k, kx, ky, Sx, Sy, J, tid, NT);
+    if (L >= 2 && J.u != nullptr)
+      supertile_inverse<L, false>(S.acc, fixed, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid, NT);
+    else if (L >= 2 && J.bits != nullptr)
+      supertile_inverse<L, true>(S.acc, fixed, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid, NT);
     PT_MARK(5);
   }
 #ifdef WASABI_PHASE_TIMERS
@@ -618,20 +652,21 @@ size_t superpose_smem_bytes(int cell, int L, int lmin, int D) {
   return smem_layout(cell, L, lmin, D, nullptr, nullptr);
 }
 
-// Largest super-tile side (at most 256 pixels) whose accumulator fits in
-// 32 KB, so that two CTAs share an SM.
+// Largest power-of-two super-tile side (at most 256 pixels) whose shared
+// memory lets two CTAs share an SM.
 int superpose_default_cell(int L, int lmin, int D) {
-  (void)D;
+  const int unit = (1 << L) > 32 ? (1 << L) : 32;
   int T = 256;
-  while (T > (1 << L) && (((size_t)T * T * sizeof(float2)) >> (2 * (lmin - 1))) > 32 * 1024) T >>= 1;
-  return T < (1 << L) ? (1 << L) : T;
+  while (T > unit && superpose_smem_bytes(T, L, lmin, D) > kTwoCtaSmem) T >>= 1;
+  return T < unit ? unit : T;
 }
 
 int superpose_max_cell_rows() { return kMaxCellRows; }
 int superpose_min_threads() { return kRangeCap / kPerMax; }
 
 cudaError_t launch_superpose(const SuperposeArgs& a, cudaStream_t s) {
-  if (a.threads > 512 || a.threads < kRangeCap / kPerMax || a.threads % 32) return cudaErrorInvalidValue;
+  if (a.threads > 512 || a.threads < kRangeCap / kPerMax || a.threads % 32 || !a.lut.code)
+    return cudaErrorInvalidValue;
   switch (a.lut.L) {
     case 1: return launch_l<1>(a, s);
     case 2: return launch_l<2>(a, s);
