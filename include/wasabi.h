@@ -258,6 +258,62 @@ wasabi_status wasabi_batch_run(wasabi_batch* batch, const wasabi_job* jobs_host,
 wasabi_status wasabi_autotune(wasabi_lut* lut, int holo_side, int64_t n_points, void* stream, int* cell_out,
                               int* threads_out);
 
+/* ---- Serving loop (A11) -------------------------------------------------
+ * Hologram requests of mixed size and point count, admitted by a device-memory
+ * budget and continuously batched.  The server reserves hbm_budget_bytes of
+ * device memory once (an arena for every request's points, outputs and
+ * binning scratch) and runs one scheduler thread with `streams` CUDA streams.
+ * Whenever a stream is free, the scheduler takes requests from the head of the
+ * FIFO queue while their buffers fit in the free arena (at most max_batch per
+ * launch), uploads their points, runs them as one batch (wasabi_batch_run:
+ * superposition with the fused inverse transform and binarisation, replayed
+ * from a CUDA graph) and copies the outputs back into the request's host
+ * buffers.  Requests arriving while others run join the next launch on a free
+ * stream, so their work overlaps on the device.  The LUT stays resident; no
+ * wavelet buffer is needed (the fused path keeps it in shared memory).
+ * A request's result depends only on its own points and the server's
+ * super-tile configuration (picked from holo_side_hint), so it is the same
+ * alone and in any mix of requests. */
+typedef struct wasabi_server wasabi_server;
+
+typedef struct {
+  const wasabi_point* points_host; /* n points in host memory (pinned: asynchronous upload) */
+  int64_t n;
+  int holo_w, holo_h;               /* multiples of 2^L; holo_w % 8 == 0 for bits */
+  int rule;                         /* wasabi_shift_rule */
+  uint8_t* bits_host;               /* packed binary hologram (host), or NULL */
+  void* u_host;                     /* complex64 row-major field (host), or NULL; not both NULL */
+} wasabi_request;
+
+typedef struct {
+  double submit_s, launch_s, done_s; /* seconds since the server was created: queued, launched,
+                                        outputs copied back */
+  int batch_jobs;                    /* requests in the launch that carried this one */
+  int status;                        /* wasabi_status of the request */
+} wasabi_request_info;
+
+/* streams in [1, 16]; max_batch in [1, 1024]; budget >= 1 MiB; levels >= 2.
+ * E_NOMEM if the budget cannot be reserved. */
+wasabi_status wasabi_server_create(const wasabi_lut* lut, size_t hbm_budget_bytes, int streams,
+                                   int max_batch, int holo_side_hint, wasabi_server** out);
+/* Queues a request (thread-safe, returns at once with its id).  The host
+ * buffers must stay valid until wasabi_server_wait returns for it.
+ * E_INVALID on bad sizes, E_RANGE if a point's depth index is >= D (checked
+ * on the host), E_NOMEM if the request alone exceeds the budget. */
+wasabi_status wasabi_server_submit(wasabi_server* server, const wasabi_request* request, int64_t* id_out);
+/* Blocks until the request has finished (its outputs are in host memory),
+ * fills *info and forgets the request.  timeout_s <= 0 waits without limit;
+ * E_TIMEOUT if it runs out (the request stays queryable).  Returns the
+ * request's status. */
+wasabi_status wasabi_server_wait(wasabi_server* server, int64_t id, double timeout_s,
+                                 wasabi_request_info* info);
+/* Peak arena use (bytes), requests completed and launches so far. */
+wasabi_status wasabi_server_stats(wasabi_server* server, size_t* peak_bytes, int64_t* completed,
+                                  int64_t* launches);
+/* Finishes the launches in flight, cancels queued requests (status
+ * E_INVALID) and frees the server.  Destroy the server before its LUT. */
+wasabi_status wasabi_server_destroy(wasabi_server* server);
+
 /* Eq. (1), the direct sum, on the GPU:
  *   u(x_h, y_h) = sum_j a_j exp(i 2 pi r_hj / lambda) [aperture],
  * r_hj = sqrt(((x_h - x_j)^2 + (y_h - y_j)^2) pitch^2 + z_{d_j}^2), with the

@@ -48,6 +48,11 @@ SIGNATURES = [
     ("wasabi_batch_scratch_bytes", _i, [_VP, _VP, _i, C.POINTER(_sz)]),
     ("wasabi_batch_run", _i, [_VP, _VP, _i, _VP, _sz, _VP]),
     ("wasabi_autotune", _i, [_VP, _i, _i64, _VP, C.POINTER(_i), C.POINTER(_i)]),
+    ("wasabi_server_create", _i, [_VP, _sz, _i, _i, _i, C.POINTER(_VP)]),
+    ("wasabi_server_submit", _i, [_VP, _VP, _I64P]),
+    ("wasabi_server_wait", _i, [_VP, _i64, _d, _VP]),
+    ("wasabi_server_stats", _i, [_VP, C.POINTER(_sz), _I64P, _I64P]),
+    ("wasabi_server_destroy", _i, [_VP]),
 ]
 
 
@@ -56,6 +61,20 @@ class Job(C.Structure):
     _fields_ = [("points_dev", C.c_void_p), ("n", C.c_int64), ("holo_w", C.c_int),
                 ("holo_h", C.c_int), ("rule", C.c_int), ("wbuf_dev", C.c_void_p),
                 ("u_dev", C.c_void_p), ("bits_dev", C.c_void_p)]
+
+
+
+class Request(C.Structure):
+    """wasabi_request of include/wasabi.h."""
+    _fields_ = [("points_host", C.c_void_p), ("n", C.c_int64), ("holo_w", C.c_int), ("holo_h", C.c_int),
+                ("rule", C.c_int), ("bits_host", C.c_void_p), ("u_host", C.c_void_p)]
+
+
+class RequestInfo(C.Structure):
+    """wasabi_request_info of include/wasabi.h."""
+    _fields_ = [("submit_s", C.c_double), ("launch_s", C.c_double), ("done_s", C.c_double),
+                ("batch_jobs", C.c_int), ("status", C.c_int)]
+
 
 _lib = None
 

@@ -285,6 +285,66 @@ class Batch:
             pass
 
 
+class Server:
+    """Serving loop (wasabi_server_*): requests admitted by a device-memory
+    budget and continuously batched over `streams` CUDA streams by a native
+    scheduler thread.  submit() takes host tensors (pinned for asynchronous
+    copies) and returns at once; wait() returns the request's timings with its
+    host outputs filled in."""
+
+    def __init__(self, lut: Lut, budget_bytes: int, streams: int = 2, max_batch: int = 64,
+                 side_hint: int = 4096):
+        self.lut = lut
+        h = C.c_void_p()
+        check(_lib().wasabi_server_create(lut.handle, int(budget_bytes), streams, max_batch, side_hint,
+                                          C.byref(h)))
+        self._h = h
+        self._live = {}
+
+    def submit(self, points: torch.Tensor, w: int, h: int, want: str = "bits", rule: int = 0) -> int:
+        if points.is_cuda or not points.is_contiguous() or points.dtype != torch.int32:
+            raise ValueError("points: contiguous (N, 4) int32 host tensor")
+        pin = points.is_pinned()
+        bits = (torch.empty((h * w + 7) // 8, dtype=torch.uint8, pin_memory=pin)
+                if want in ("bits", "both") else None)
+        u = torch.empty((h, w), dtype=torch.complex64, pin_memory=pin) if want in ("complex", "both") else None
+        req = _abi.Request(points.data_ptr() if points.shape[0] else None, points.shape[0], w, h, rule,
+                           bits.data_ptr() if bits is not None else None,
+                           u.data_ptr() if u is not None else None)
+        rid = C.c_int64()
+        check(_lib().wasabi_server_submit(self._h, C.byref(req), C.byref(rid)))
+        self._live[rid.value] = (points, bits, u)
+        return rid.value
+
+    def wait(self, rid: int, timeout: float = 0.0) -> dict:
+        info = _abi.RequestInfo()
+        code = _lib().wasabi_server_wait(self._h, rid, timeout, C.byref(info))
+        if code == _abi.E_TIMEOUT:
+            check(code)
+        _, bits, u = self._live.pop(rid)
+        check(code)
+        return {"submit_s": info.submit_s, "launch_s": info.launch_s, "done_s": info.done_s,
+                "latency_s": info.done_s - info.submit_s, "batch_jobs": info.batch_jobs,
+                "bits": bits, "u": u}
+
+    def stats(self) -> dict:
+        peak, done, nl = C.c_size_t(), C.c_int64(), C.c_int64()
+        check(_lib().wasabi_server_stats(self._h, C.byref(peak), C.byref(done), C.byref(nl)))
+        return {"peak_bytes": int(peak.value), "completed": int(done.value), "launches": int(nl.value)}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            _lib().wasabi_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def autotune(lut: Lut, side: int, n_points: int, stream=None) -> tuple[int, int]:
     """Pick and store the fastest super-tile / block size for this size class."""
     c, t = C.c_int(), C.c_int()

@@ -64,10 +64,10 @@ __global__ void zero_kernel(BinArgs b) {
     const JobDev& J = b.jobs[j];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= J.ncells; i += stride)
       J.cnt[i] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) b.jobs[j].amax = 0.f;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     b.batch->counter = 0;
-    b.batch->amax = 0.f;
     for (int t = 0; t < 6; ++t) b.batch->timers[t] = 0;
   }
 }
@@ -86,14 +86,14 @@ __global__ void __launch_bounds__(256) count_kernel(BinArgs b) {
   const long long npts = b.batch->npts;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < npts; g += stride) {
-    const JobDev& J = b.jobs[job_of(spt0, nj, g)];
+    JobDev& J = b.jobs[job_of(spt0, nj, g)];
     const wasabi_point p = J.pts[g - J.pt0];
     if (p.d >= (uint32_t)b.D) atomicCAS(b.status, 0, WASABI_E_RANGE);
     const int c = cell_of(J, p, b.cell, b.reach, b.D);
     if (c >= 0) {
       atomicAdd(&J.cnt[c], 1);
       // Non-negative floats order like their bit patterns.
-      if (b.track_amax) atomicMax(reinterpret_cast<int*>(&b.batch->amax), __float_as_int(fabsf(p.a)));
+      if (b.track_amax) atomicMax(reinterpret_cast<int*>(&J.amax), __float_as_int(fabsf(p.a)));
     }
   }
 }

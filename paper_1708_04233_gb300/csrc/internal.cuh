@@ -183,6 +183,7 @@ struct JobDev {
   int sp0;                  // first superposition item (super-tile) of this job
   int inv0;                 // first inverse item (strip) of this job
   int ncells;               // ncx * ncy
+  float amax;               // largest |a| over the job's binned points (zeroed by zero_kernel)
 };
 
 struct BatchDev {
@@ -192,7 +193,6 @@ struct BatchDev {
   int pad;
   long long npts;           // points over all jobs
   int counter;              // superposition work counter (zeroed by zero_kernel)
-  float amax;               // largest |a| over binned points (zeroed by zero_kernel)
   unsigned long long timers[6];  // phase cycle counters (profiling builds only)
 };
 
@@ -208,12 +208,12 @@ __device__ __forceinline__ int job_of(const T* starts, int njobs, T item) {
 }
 
 struct BinArgs {
-  const JobDev* jobs;       // device job table
+  JobDev* jobs;             // device job table
   BatchDev* batch;          // device totals
   int D;
   int cell;                 // cell side (pixels)
   int reach;                // pixels: a point farther than this outside the hologram is dropped
-  int track_amax;           // record the largest |a| (superposition uses it)
+  int track_amax;           // record each job's largest |a| (superposition uses it)
   int* status;
   int grid;                 // blocks of the grid-stride kernels
 };

@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
     }
   }
   int* counter = &a.batch->counter;
-  const float amax_cmax = a.batch->amax * __ldg(lut.cmax);
+  const float cmax = __ldg(lut.cmax);
   float4* acc4 = reinterpret_cast<float4*>(S.acc);
   int* acci = reinterpret_cast<int*>(S.acc);
   const bool fixed = !a.acc_float;
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
     PT_MARK(1);
     const int total = s_total;
     // Fixed-point scale 2^sh: every partial sum stays below 2^31 in magnitude.
-    const float bound = (float)total * amax_cmax;
+    const float bound = (float)total * (J.amax * cmax);
     const int sh = bound > 0.f ? max(-100, min(30, (int)floorf(log2f(2.0e9f / bound)))) : 30;
     const float qs = ldexpf(1.0f, sh);
 

@@ -62,7 +62,7 @@ def heightfield_cloud(seed: int, N: int, Nh: int, zmin: float, zmax: float) -> d
     h = np.zeros(N, np.float64)
     for k in range(_NG):
         h += amp[k] * np.exp(-((xf - mx[k]) ** 2 + (yf - my[k]) ** 2) / (2.0 * sig[k] ** 2))
-    lo, hi = h.min(), h.max()
+    lo, hi = (h.min(), h.max()) if N else (0.0, 0.0)
     t = (h - lo) / (hi - lo) if hi > lo else np.zeros_like(h)
     z = np.clip(zmin + t * (zmax - zmin), zmin, zmax)
     a = (1.0 - uniform01(seed ^ 0x5A5A5A5A, N, 0)).astype(np.float32)
