@@ -28,7 +28,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import CONFIGS  # noqa: E402
+from workloads import CONFIGS, heightfield_cloud, serving_stream  # noqa: E402
 
 METRIC = "WASABI hologram Mpoint*coeff/s at 65536^2 (hologram s, HBM fraction)"
 UNIT = "Mpoint*coeff/s"
@@ -44,12 +44,15 @@ def _peaks():
 
 
 def _workload_desc(c):
-    return {"workload": f"{c.name}: {c.Nh}x{c.Nh} binarised hologram, {c.N} height-field points, "
-                        f"{c.D} depths, W={c.W}, L={c.L}, keep={c.gamma}",
+    form = "binarised hologram" if c.output == "bits" else "complex field"
+    out_bytes = c.Nh * c.Nh // 8 if c.output == "bits" else c.Nh * c.Nh * 8
+    return {"workload": f"{c.name}: {c.Nh}x{c.Nh} {form}, {c.N} {c.cloud} points, "
+                        f"{c.D} depths, W={c.W}, L={c.L}, keep={c.gamma}, LUT {c.lut_dtype}",
             "Nh": c.Nh, "N": c.N, "lambda_m": c.lam, "pitch_m": c.pitch, "z_range_m": [c.zmin, c.zmax],
             "depths": c.D, "window": c.W, "levels": c.L, "keep_ratio": c.gamma, "output": c.output,
-            "lut_dtype": c.lut_dtype, "l2": (f"{'outputs larger than L2' if c.Nh * c.Nh // 8 > 129e6 else 'NOT larger than L2'} "
-                   f"({c.Nh}^2: {c.Nh * c.Nh / 8e9:.3g} GB of bits per step; "
+            "lut_dtype": c.lut_dtype,
+            "l2": (f"{'outputs larger than L2' if out_bytes > 129e6 else 'outputs NOT larger than L2'} "
+                   f"({out_bytes / 1e9:.3g} GB written per step; "
                    f"{c.Nh * c.Nh * 8e-9:.3g} GB wavelet buffer in the two-pass form)")}
 
 
@@ -158,6 +161,118 @@ def run_reference(args, c):
 
 # --------------------------------------------------------------------- GPU arm
 
+def _time(torch, stream, fn, reps=5):
+    fn()
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def direct_comparison(w, torch, dev, c, depths, pbuf, u_wasabi, stream, wasabi_step_ms):
+    """C2: Eq. (1) summed directly on the GPU (aperture form) on the same
+    points, its time against the WASABI step, and the WASABI approximation
+    error against it (rel-L2 over the whole field, norms in FP64)."""
+    u_direct = torch.empty_like(u_wasabi)
+    scratch = torch.empty(w.cgh_direct_scratch_bytes(pbuf.shape[0], c.Nh, c.Nh), dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        ms = _time(torch, stream, lambda: w.cgh_direct(c.lam, c.pitch, depths, pbuf, c.Nh, c.Nh, True, u=u_direct,
+                                                        scratch=scratch, stream=stream), reps=3)
+    w.sync_status(stream)
+    diff = (u_wasabi.to(torch.complex128) - u_direct.to(torch.complex128)).abs().pow(2).sum().sqrt()
+    ref = u_direct.to(torch.complex128).abs().pow(2).sum().sqrt()
+    return {"kernel": "direct_kernel (Eq. (1), aperture form; FP64 phase reduction)", "ms": ms,
+            "wasabi_step_ms": wasabi_step_ms, "speedup": ms / wasabi_step_ms,
+            "rel_l2_wasabi_vs_eq1": float(diff / ref)}
+
+
+def precision_forms(w, torch, dev, c, depths, pbuf, stream):
+    """C4: the fused hologram with the LUT stored as FP32, FP16 and BF16
+    (per-32 FP32 scales); time of the hologram call per form.  The error of
+    each form against the FP64 oracle is measured by the test suite."""
+    out = {}
+    u = torch.empty((c.Nh, c.Nh), dtype=torch.complex64, device=dev)
+    for dt in ("f32", "f16s", "bf16s"):
+        lut = w.build_lut(c.lam, c.pitch, depths, c.W, c.L, c.gamma, dtype=dt, stream=stream)
+        scratch = torch.empty(w.scratch_bytes(lut, pbuf.shape[0], c.Nh, c.Nh), dtype=torch.uint8, device=dev)
+        with torch.cuda.stream(stream):
+            ms = _time(torch, stream, lambda: w.hologram(lut, pbuf, c.Nh, c.Nh, want="complex", u=u,
+                                                          scratch=scratch, stream=stream))
+        out[dt] = {"hologram_ms": ms}
+        lut.close()
+    w.sync_status(stream)
+    return out
+
+
+def serving_summary(w, torch, dev, n_jobs: int = 512, budget_gib: float = 4.0, streams: int = 4,
+                    max_batch: int = 32):
+    """C5: the seeded request stream (Poisson arrivals at 200/s, sides
+    1024..8192, N log-uniform in [1e3, 2e5]) through the serving loop, as
+    scheduled (p50/p99 latency) and all at once (saturated throughput), next
+    to the same holograms computed one call at a time (plain form)."""
+    c = CONFIGS["C5"]
+    jobs = serving_stream(n_jobs)
+    depths = w.depth_grid(c.zmin, c.zmax, c.D)
+    lut = w.build_lut(c.lam, c.pitch, depths, c.W, c.L, c.gamma)
+    hosts = []
+    for j in jobs:
+        p = heightfield_cloud(j.seed, j.N, j.Nh, c.zmin, c.zmax)
+        t = {k: torch.from_numpy(p[k]).to(dev) for k in "xyza"}
+        q = w.quantize_points(t["x"], t["y"], t["z"], t["a"], c.zmin, c.zmax, c.D)
+        hosts.append(q.cpu().pin_memory())
+    w.sync_status()
+    srv = w.Server(lut, int(budget_gib * (1 << 30)), streams=streams, max_batch=max_batch, side_hint=4096)
+    for i in range(min(8, n_jobs)):  # warm-up: graph capture on the streams
+        srv.wait(srv.submit(hosts[i], jobs[i].Nh, jobs[i].Nh), timeout=120)
+
+    def run(paced: bool):
+        ids = []
+        t0 = time.perf_counter()
+        for j, h in zip(jobs, hosts):
+            if paced:
+                dt = t0 + j.arrival_s - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+            ids.append(srv.submit(h, j.Nh, j.Nh))
+        return [srv.wait(i, timeout=600) for i in ids]
+
+    paced = run(True)
+    sat = run(False)
+    stats = srv.stats()
+    srv.close()
+    lat = np.array([r["latency_s"] for r in paced]) * 1e3
+
+    def rate(rs):
+        return len(rs) / (max(r["done_s"] for r in rs) - min(r["submit_s"] for r in rs))
+
+    # Plain form: one wasabi_hologram call per request, back to back.
+    stream = torch.cuda.Stream(device=dev)
+    outs = [torch.empty((j.Nh * j.Nh) // 8, dtype=torch.uint8).pin_memory() for j in jobs]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for j, h, o in zip(jobs, hosts, outs):
+            d = h.to(dev, non_blocking=True)
+            b = w.hologram(lut, d, j.Nh, j.Nh, want="bits", stream=stream)
+            o.copy_(b, non_blocking=True)
+    stream.synchronize()
+    plain = len(jobs) / (time.perf_counter() - t0)
+    w.sync_status()
+    lut.close()
+    return {"workload": f"C5: {len(jobs)} requests, Poisson arrivals at 200/s, sides 1024-8192, "
+                        f"N log-uniform [1e3, 2e5], bits out, {c.D}-depth LUT (lambda 532 nm)",
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "holograms_per_s_paced": rate(paced), "holograms_per_s_saturated": rate(sat),
+            "holograms_per_s_plain_one_call_each": plain,
+            "mean_jobs_per_launch_saturated": float(np.mean([r["batch_jobs"] for r in sat])),
+            "launches": stats["launches"], "peak_arena_bytes": stats["peak_bytes"],
+            "budget_bytes": int(budget_gib * (1 << 30)), "streams": streams, "max_batch": max_batch}
+
+
 def run_gpu(args, c):
     import torch
     import torch.distributed as dist
@@ -182,7 +297,10 @@ def run_gpu(args, c):
     z = torch.from_numpy(pts["z"]).to(dev)
     a = torch.from_numpy(pts["a"]).to(dev)
     pbuf = torch.empty((N, 4), dtype=torch.int32, device=dev)
-    bits = torch.empty(c.Nh * c.Nh // 8, dtype=torch.uint8, device=dev)
+    want = "bits" if c.output == "bits" else "complex"
+    bits = torch.empty(c.Nh * c.Nh // 8, dtype=torch.uint8, device=dev) if want == "bits" else None
+    ufield = torch.empty((c.Nh, c.Nh), dtype=torch.complex64, device=dev) if want == "complex" else None
+    out_dev = bits if want == "bits" else ufield
     stream = torch.cuda.Stream(device=dev)
     fused = args.path == "fused"
     wbuf = None if fused else torch.empty(c.Nh * c.Nh, dtype=torch.complex64, device=dev)
@@ -208,10 +326,10 @@ def run_gpu(args, c):
                 w.superpose(lut, pbuf, c.Nh, c.Nh, rule=0, wbuf=wb if wb is not None else wbuf,
                             scratch=step.scratch, stream=stream)
                 mark()
-                w.inverse_haar(wb if wb is not None else wbuf, c.Nh, c.Nh, c.L, bits=bits, want="bits",
+                w.inverse_haar(wb if wb is not None else wbuf, c.Nh, c.Nh, c.L, u=ufield, bits=bits, want=want,
                                stream=stream)
             else:
-                w.hologram(lut, pbuf, c.Nh, c.Nh, want="bits", rule=0, bits=bits, scratch=step.scratch,
+                w.hologram(lut, pbuf, c.Nh, c.Nh, want=want, rule=0, u=ufield, bits=bits, scratch=step.scratch,
                            stream=stream)
             mark()
             if record:
@@ -264,7 +382,7 @@ def run_gpu(args, c):
     hy = torch.from_numpy(pts["y"]).pin_memory()
     hz = torch.from_numpy(pts["z"]).pin_memory()
     ha = torch.from_numpy(pts["a"]).pin_memory()
-    hbits = torch.empty(bits.numel(), dtype=torch.uint8).pin_memory()
+    hout = torch.empty(out_dev.shape, dtype=out_dev.dtype).pin_memory()
     dx, dy, dz, da = (torch.empty_like(t) for t in (x, y, z, a))
 
     def e2e_step():
@@ -272,7 +390,7 @@ def run_gpu(args, c):
             for d_, h_ in ((dx, hx), (dy, hy), (dz, hz), (da, ha)):
                 d_.copy_(h_, non_blocking=True)
             step(xs=dx, ys=dy, zs=dz, as_=da)
-            hbits.copy_(bits, non_blocking=True)
+            hout.copy_(out_dev, non_blocking=True)
     e2e_step()
     barrier()
     te = time.perf_counter()
@@ -285,7 +403,7 @@ def run_gpu(args, c):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
     h2d = sum(t.numel() * t.element_size() for t in (hx, hy, hz, ha))
-    d2h = hbits.numel()
+    d2h = hout.numel() * hout.element_size()
 
     # The two-pass form (superposition into the 34 GB wavelet buffer, then the
     # separate inverse kernel): the inverse kernel's HBM fraction.
@@ -309,10 +427,10 @@ def run_gpu(args, c):
     elif not fused:
         two = {"ms_per_step": ms, "stages_ms": stage_ms, "steps": args.steps}
 
-    inv_bytes = c.Nh * c.Nh * 8 + c.Nh * c.Nh // 8
+    inv_bytes = c.Nh * c.Nh * 8 + (c.Nh * c.Nh // 8 if want == "bits" else c.Nh * c.Nh * 8)
     if two is not None:
         inv_gbs = inv_bytes / (two["stages_ms"]["inverse"] * 1e-3) / 1e9
-        two["inverse_hbm"] = {"kernel": "inverse_kernel<4> (inverse Haar + binarisation)",
+        two["inverse_hbm"] = {"kernel": f"inverse_kernel<{c.L}> (inverse Haar" + (" + binarisation)" if want == "bits" else ")"),
                               "algorithmic_bytes": inv_bytes, "gbs": inv_gbs, "frac": inv_gbs / peak,
                               "peak": peak, "peak_source": peak_kind}
     hot_ms = stage_ms["hologram" if fused else "superpose"]
@@ -322,8 +440,9 @@ def run_gpu(args, c):
     # Peak: one 32-bit access per bank per clock, 32 banks x 152 SMs x max SM clock.
     smem_peak = 32 * 152 * 2070e6 / 1e9  # Gop/s
     ach = 2 * units / (hot_ms * 1e-3) / 1e9
-    roof = {"kernel": ("superpose_kernel<4,f32> with fused inverse + binarisation" if fused
-                       else "superpose_kernel<4,f32>") + " (+ binning kernels, one ABI call)",
+    roof = {"kernel": (f"superpose_kernel<{c.L},{c.lut_dtype}> with fused inverse"
+                       + (" + binarisation" if want == "bits" else "") if fused
+                       else f"superpose_kernel<{c.L},{c.lut_dtype}>") + " (+ binning kernels, one ABI call)",
             "bound": "alu", "achieved": ach, "peak": smem_peak, "unit": "Gop/s", "frac": ach / smem_peak,
             "peak_source": "derived: 32 banks x 152 SMs x 2070 MHz (shared-memory 32-bit ops)",
             "algorithmic_ops": 2 * units, "traffic": None}
@@ -346,6 +465,12 @@ def run_gpu(args, c):
                        "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": per_step * args.steps,
                "clocks": clk.summary()}
+        if c.name == "C2":
+            out["direct_eq1"] = direct_comparison(w, torch, dev, c, depths, pbuf, out_dev, stream, ms)
+        if c.name == "C4":
+            out["precision_forms"] = precision_forms(w, torch, dev, c, depths, pbuf, stream)
+        if not args.no_serving and c.name == "C3":
+            out["serving"] = serving_summary(w, torch, dev)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = oracle_sample(c, pts, os.cpu_count() or 1)
         print(json.dumps(out), flush=True)
@@ -360,10 +485,13 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wasabi", choices=["wasabi", "reference"])
-    ap.add_argument("--config", default="C3", choices=["C2", "C3", "C4"])
+    ap.add_argument("--config", default="C3", choices=["C2", "C3", "C4"],
+                    help="C3 (default): the 65536^2 binarised hologram; C2: 8192^2 complex field "
+                         "with direct Eq. (1) beside it; C4: C2 with the precision forms")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="fused", choices=["fused", "two-pass"],
                     help="fused: wasabi_hologram; two-pass: wasabi_superpose + wasabi_inverse_haar")
+    ap.add_argument("--no-serving", action="store_true", help="skip the C5 serving-loop summary")
     ap.add_argument("--nh", type=int, default=0,
                     help="profiling cases: hologram side (points scaled by area, same density)")
     ap.add_argument("--no-two-pass", action="store_true",
