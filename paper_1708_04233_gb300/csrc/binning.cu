@@ -86,22 +86,30 @@ __global__ void __launch_bounds__(256) count_kernel(BinArgs b) {
   const long long npts = b.batch->npts;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < npts; g += stride) {
-    JobDev& J = b.jobs[job_of(spt0, nj, g)];
+    const int jid = job_of(spt0, nj, g);
+    const JobDev& J = b.jobs[jid];
     const wasabi_point p = J.pts[g - J.pt0];
     if (p.d >= (uint32_t)b.D) atomicCAS(b.status, 0, WASABI_E_RANGE);
     const int c = cell_of(J, p, b.cell, b.reach, b.D);
-    if (c >= 0) {
-      atomicAdd(&J.cnt[c], 1);
-      // Non-negative floats order like their bit patterns.
-      if (b.track_amax) atomicMax(reinterpret_cast<int*>(&J.amax), __float_as_int(fabsf(p.a)));
+    if (c >= 0) atomicAdd(&J.cnt[c], 1);
+    if (b.track_amax) {
+      // Largest |a| of the job: one atomic per warp and job (non-negative
+      // floats order like their bit patterns).
+      const unsigned v = c >= 0 ? __float_as_uint(fabsf(p.a)) : 0u;
+      const unsigned act = __activemask();
+      const unsigned grp = __match_any_sync(act, jid);
+      const unsigned mx = __reduce_max_sync(grp, v);
+      if ((threadIdx.x & 31) == __ffs(grp) - 1 && mx > 0u)
+        atomicMax(reinterpret_cast<unsigned*>(&b.jobs[jid].amax), mx);
     }
   }
 }
 
 // Exclusive scan of each job's cell counts into off[0..ncells] and
-// cursor[0..ncells): one block per job at a time, chunks of 4096 counts, each
-// thread a coalesced group of four, a running carry between chunks.
+// cursor[0..ncells): one block per job at a time, chunks of 16,384 counts,
+// each thread 16 consecutive counts, a running carry between chunks.
 __global__ void __launch_bounds__(1024) scan_kernel(BinArgs b) {
+  constexpr int CPT = 16;  // counts per thread
   __shared__ unsigned warp_sum[32];
   __shared__ unsigned s_carry;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -111,12 +119,15 @@ __global__ void __launch_bounds__(1024) scan_kernel(BinArgs b) {
     const int ncells = J.ncells;
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
-    for (int base = 0; base < ncells; base += 4096) {
-      const int i0 = base + 4 * threadIdx.x;
-      int c[4];
+    for (int base = 0; base < ncells; base += CPT * 1024) {
+      const int i0 = base + CPT * threadIdx.x;
+      int c[CPT];
+      unsigned local = 0;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) c[q] = i0 + q < ncells ? J.cnt[i0 + q] : 0;
-      const unsigned local = (unsigned)(c[0] + c[1] + c[2] + c[3]);
+      for (int q = 0; q < CPT; ++q) {
+        c[q] = i0 + q < ncells ? J.cnt[i0 + q] : 0;
+        local += (unsigned)c[q];
+      }
       unsigned x = local;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -138,7 +149,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(BinArgs b) {
       const unsigned carry = s_carry;
       unsigned run = carry + (wid ? warp_sum[wid - 1] : 0u) + x - local;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < CPT; ++q) {
         if (i0 + q < ncells) {
           J.off[i0 + q] = (int)run;
           J.cursor[i0 + q] = (int)run;

@@ -29,26 +29,33 @@ __host__ __device__ inline uint32_t pack_pos(int p, int q, int lev, int band) {
 // per kept level l, square planes of side G_l = (k + 2) 2^(L-l) cells -- the
 // super-tile plus a guard band one tile wide on every side -- four at level L
 // (approximation and three details), three at finer levels, coarse levels
-// first.  A coefficient's plane code is (l << 29) | (band plane * G_l^2 +
-// q G_l + p) with (p, q) its window-relative position: adding a survivor's
-// per-level base (its shift of Eq. (2), the guard and the level's offset)
-// gives the accumulator index, with no bounds test (every visited coefficient
-// lands inside the guard band by construction of the LUT ranges).
+// first.  Rows are G_l + 1 cells apart and planes are padded to 4 modulo 16
+// cells, so that lanes adding into neighbouring rows or other bands of the
+// same cells fall into different shared-memory banks.  A coefficient's plane
+// code is (l << 29) | (band plane * plane size + q * row + p) with (p, q) its
+// window-relative position: adding a survivor's per-level base (its shift of
+// Eq. (2), the guard and the level's offset) gives the accumulator index,
+// with no bounds test (every visited coefficient lands inside the guard band
+// by construction of the LUT ranges).
 __host__ __device__ inline int plane_side(int k, int L, int l) { return (k + 2) << (L - l); }
+__host__ __device__ inline int plane_row(int k, int L, int l) { return plane_side(k, L, l) + 1; }
+__host__ __device__ inline int plane_size(int k, int L, int l) {
+  const int n = plane_row(k, L, l) * plane_side(k, L, l);
+  return n + ((4 - n % 16) + 16) % 16;
+}
 __host__ __device__ inline int plane_count(int L, int l) { return l == L ? 4 : 3; }
 __host__ __device__ inline uint32_t plane_code(uint32_t pos, int L, int k) {
   const int p = (int)(pos & 4095u), q = (int)((pos >> 12) & 4095u);
   const int lev = (int)((pos >> 24) & 7u), band = (int)((pos >> 27) & 3u);
   if (lev < 1 || lev > L) return 0;  // unused capacity: never visited
-  const int G = plane_side(k, L, lev);
   const int bi = lev == L ? band : band - 1;
-  return ((uint32_t)lev << 29) | (uint32_t)(bi * G * G + q * G + p);
+  return ((uint32_t)lev << 29) | (uint32_t)(bi * plane_size(k, L, lev) + q * plane_row(k, L, lev) + p);
 }
-// Accumulator size (complex elements) for levels lmin..L.
+// Accumulator size (complex elements, even) for levels lmin..L.
 __host__ __device__ inline int plane_total(int k, int L, int lmin) {
   int n = 0;
-  for (int l = lmin; l <= L; ++l) n += plane_count(L, l) * plane_side(k, L, l) * plane_side(k, L, l);
-  return n;
+  for (int l = lmin; l <= L; ++l) n += plane_count(L, l) * plane_size(k, L, l);
+  return (n + 1) & ~1;
 }
 // Most plane codes a LUT keeps: one per super-tile width k the superposition
 // can use (super-tiles are multiples of 32 pixels, at most 256).

@@ -170,7 +170,7 @@ __host__ __device__ inline size_t smem_layout(int T, int L, int lmin, int D, Sme
 // 32-bit word of the packed binary hologram (the super-tile side is a
 // multiple of 32), and read neighbouring accumulator cells (no bank
 // conflicts).  lvC[l], lvG[l], lvPS[l]: index of the level's first
-// super-tile cell (past the guard), plane side and plane size.
+// super-tile cell (past the guard), row stride and plane size.
 // RE_ONLY (bits output alone): only real parts are read and transformed; the
 // inverse transform acts on real and imaginary parts separately, so Re u is
 // unchanged.
@@ -194,7 +194,11 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
     auto coef = [&](int l, int bi, int cx, int cy) -> float2 {
       if (l < lmin) return make_float2(0.f, 0.f);
       const int i = lvC[l] + bi * lvPS[l] + cy * lvG[l] + cx;
-      if (RE_ONLY) return make_float2(fixed ? (float)acci[2 * i] * dq : acc[i].x, 0.f);
+      // Bits alone: the fixed-point values are transformed unscaled.  Every
+      // step is then exactly 2^sh times the scaled one (power-of-two scaling
+      // commutes with the adds and halvings while values stay normal), so
+      // the signs -- the bits -- are those of the scaled field.
+      if (RE_ONLY) return make_float2(fixed ? (float)acci[2 * i] : acc[i].x, 0.f);
       if (fixed) {
         const int2 q = reinterpret_cast<const int2*>(acci)[i];
         return make_float2((float)q.x * dq, (float)q.y * dq);
@@ -325,8 +329,8 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
   __shared__ int s_st, s_n, s_total;
   __shared__ int s_rowstart[kMaxCellRows], s_rowpre[kMaxCellRows + 1];
   __shared__ unsigned long long warp_buf[32];
-  // Per level l: index of the first super-tile cell past the guard, plane
-  // side, plane size (see plane_code).
+  // Per level l: index of the first super-tile cell past the guard, row
+  // stride, plane size (see plane_code).
   __shared__ int lvC[8], lvG[8], lvPS[8];
 
   const LutView& lut = a.lut;
@@ -344,11 +348,11 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
   if (tid == 0) {
     int base = 0;
     for (int l = L; l >= 1; --l) {
-      const int G = plane_side(k, L, l), g = 1 << (L - l);
-      lvG[l] = G;
-      lvPS[l] = G * G;
-      lvC[l] = base + g * G + g;
-      if (l >= lmin) base += plane_count(L, l) * G * G;
+      const int R = plane_row(k, L, l), g = 1 << (L - l);
+      lvG[l] = R;
+      lvPS[l] = plane_size(k, L, l);
+      lvC[l] = base + g * R + g;
+      if (l >= lmin) base += plane_count(L, l) * lvPS[l];
     }
   }
   int* counter = &a.batch->counter;
@@ -572,7 +576,7 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
     // Write the super-tile's tiles to the tile-major buffer: each tile's TSL
     // slots are contiguous there; slots of levels finer than lmin are zero.
     // Slot -> accumulator offset table (in the free range records): offset of
-    // the slot's cell for tile (0, 0), plane side and m = L - level.
+    // the slot's cell for tile (0, 0), row stride and m = L - level.
     if (wbuf != nullptr) {
       int2* tab = S.rrec;
       for (int q = tid; q < TSL; q += NT) {
