@@ -132,7 +132,8 @@ void superpose_config(const wasabi_lut* lut, int w, int h, int* cell, int* threa
   // A multiple of 32 pixels (one word of the packed binary output) and of 2^L.
   const int unit = std::max(1 << lut->L, 32);
   T = std::max(unit, T / unit * unit);
-  while (T > unit && superpose_smem_bytes(T, lut->L, lut->lmin, lut->D) > 220 * 1024) T = std::max(unit, T / 2 / unit * unit);
+  while (T > unit && superpose_smem_bytes(T, lut->L, lut->lmin, lut->D, false, 2048) > 220 * 1024)
+    T = std::max(unit, T / 2 / unit * unit);
   nt = std::max(superpose_min_threads(), std::min(512, nt / 32 * 32));
   *cell = T;
   *threads = nt;
@@ -327,7 +328,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
     const int unit = std::max(1 << levels, 32);  // super-tile sides: multiples of 32 and of 2^L
     for (int T = unit; T <= 256 && lut->ncode < kMaxCodes; T += unit) lut->code_k[lut->ncode++] = T >> levels;
   }
-  c.take<uint32_t>((size_t)lut->ncode * (size_t)base);              // plane codes
+  c.take<uint2>((size_t)lut->ncode * (size_t)base);                 // plane-code records
   const size_t persist_bytes = align_up(c.off, 256);
   cudaError_t e = cudaMallocAsync(&lut->block, persist_bytes, s);
   if (e != cudaSuccess) { delete lut; set_error("build_lut: cudaMallocAsync: %s", cudaGetErrorString(e)); return WASABI_E_NOMEM; }
@@ -344,7 +345,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   lut->nr_dev = c.take<long long>((size_t)n_depths);
   lut->cmax = c.take<float>(1);
   lut->levels = c.take<unsigned>(1);
-  lut->code = c.take<uint32_t>((size_t)lut->ncode * (size_t)base);
+  lut->code = c.take<uint2>((size_t)lut->ncode * (size_t)base);
 
   // Build scratch.
   Carver sc;
@@ -608,7 +609,9 @@ wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* poi
   }
   const int rows = (cell + 2 * lut->reach) / cell + 2;
   if (rows > superpose_max_cell_rows()) { set_error("superpose: window too large for the super-tile"); return WASABI_E_INVALID; }
-  const size_t smem = superpose_smem_bytes(cell, lut->L, lut->lmin, lut->D);
+  const bool re_only = !wbuf_dev && !u_dev && bits_dev;
+  const int rcap = superpose_range_cap(cell, lut->L, lut->lmin, lut->D, re_only, threads);
+  const size_t smem = superpose_smem_bytes(cell, lut->L, lut->lmin, lut->D, re_only, rcap);
   if (smem > 220 * 1024) { set_error("superpose: super-tile %d needs %zu B of shared memory", cell, smem); return WASABI_E_INVALID; }
   const cudaStream_t s = (cudaStream_t)stream;
   JobDev J = make_job(lut, points_dev, n, holo_w, holo_h, rule, cell, static_cast<float2*>(wbuf_dev),
@@ -626,6 +629,8 @@ wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* poi
   sa.lut = lut->view(cell >> lut->L);
   sa.jobs = b.jobs; sa.batch = b.batch; sa.cell = cell; sa.reach = lut->reach;
   sa.acc_float = env_int("WASABI_ACC_FLOAT", 0) != 0;
+  sa.re_only = re_only ? 1 : 0;
+  sa.rcap = rcap;
   sa.status = status; sa.threads = threads; sa.grid = sms;
   e = launch_superpose(sa, s);
   return e == cudaSuccess ? WASABI_OK : cuda_fail("superpose: launch", e);

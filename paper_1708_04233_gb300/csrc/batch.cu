@@ -30,8 +30,10 @@ struct wasabi_batch {
   BatchDev* batch_dev = nullptr;
   cudaEvent_t staged = nullptr;     // the last upload of the staging buffers has completed
   bool staged_pending = false;
-  cudaGraphExec_t exec = nullptr;
-  cudaStream_t graph_stream = nullptr;
+  // One graph per accumulation mode (complex, or real parts only when every
+  // job wants bits alone), each bound to the stream it was captured on.
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaStream_t graph_stream[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -71,7 +73,7 @@ wasabi_status check_job(const wasabi_lut* lut, const wasabi_job& j, int idx) {
 // Enqueues the upload and the five launches of a batch on s.  Under stream
 // capture the record of `staged` becomes an external event node, so the host
 // can wait on it after each replay.
-cudaError_t enqueue_batch(wasabi_batch* b, cudaStream_t s, int* status, int sms, bool capturing) {
+cudaError_t enqueue_batch(wasabi_batch* b, cudaStream_t s, int* status, int sms, bool capturing, bool re_only) {
   cudaError_t e = cudaMemcpyAsync(b->jobs_dev, b->staging_jobs, sizeof(JobDev) * b->max_jobs,
                                   cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -88,6 +90,8 @@ cudaError_t enqueue_batch(wasabi_batch* b, cudaStream_t s, int* status, int sms,
   sa.lut = lut->view(b->cell >> lut->L);
   sa.jobs = b->jobs_dev; sa.batch = b->batch_dev; sa.cell = b->cell; sa.reach = lut->reach;
   sa.acc_float = 0; sa.status = status; sa.threads = b->threads; sa.grid = sms;
+  sa.re_only = re_only ? 1 : 0;
+  sa.rcap = superpose_range_cap(b->cell, lut->L, lut->lmin, lut->D, re_only, b->threads);
   if ((e = launch_superpose(sa, s)) != cudaSuccess) return e;
   return cudaSuccess;
 }
@@ -155,7 +159,8 @@ wasabi_status wasabi_batch_destroy(wasabi_batch* b) {
   cudaGetDevice(&prev);
   cudaSetDevice(b->device);
   if (b->staged) cudaEventSynchronize(b->staged);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (int m = 0; m < 2; ++m)
+    if (b->exec[m]) cudaGraphExecDestroy(b->exec[m]);
   if (b->staged) cudaEventDestroy(b->staged);
   if (b->jobs_dev) cudaFree(b->jobs_dev);
   if (b->batch_dev) cudaFree(b->batch_dev);
@@ -251,26 +256,29 @@ wasabi_status wasabi_batch_run(wasabi_batch* b, const wasabi_job* jobs, int njob
   B.njobs = njobs;
   B.nsp = sp0;
   B.npts = pt0;
+  bool re_only = njobs > 0;
+  for (int i = 0; i < njobs; ++i) re_only = re_only && !jobs[i].wbuf_dev && !jobs[i].u_dev && jobs[i].bits_dev;
+  const int m = re_only ? 1 : 0;
   const cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
   if (b->use_graph && s != nullptr) {
-    if (!b->exec || b->graph_stream != s) {
-      if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (!b->exec[m] || b->graph_stream[m] != s) {
+      if (b->exec[m]) { cudaGraphExecDestroy(b->exec[m]); b->exec[m] = nullptr; }
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        const cudaError_t e2 = enqueue_batch(b, s, status, sms, true);
+        const cudaError_t e2 = enqueue_batch(b, s, status, sms, true, re_only);
         e = cudaStreamEndCapture(s, &g);
         if (e2 != cudaSuccess) e = e2;
       }
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[m], g, 0);
       if (g) cudaGraphDestroy(g);
-      if (e != cudaSuccess) { b->exec = nullptr; return cuda_fail("batch_run: graph capture", e); }
-      b->graph_stream = s;
+      if (e != cudaSuccess) { b->exec[m] = nullptr; return cuda_fail("batch_run: graph capture", e); }
+      b->graph_stream[m] = s;
     }
-    e = cudaGraphLaunch(b->exec, s);
+    e = cudaGraphLaunch(b->exec[m], s);
   } else {
-    e = enqueue_batch(b, s, status, sms, false);
+    e = enqueue_batch(b, s, status, sms, false, re_only);
   }
   if (e != cudaSuccess) return cuda_fail("batch_run: launch", e);
   b->staged_pending = true;
@@ -308,7 +316,7 @@ wasabi_status wasabi_autotune(wasabi_lut* lut, int holo_side, int64_t n_points, 
   const int cells[] = {64, 128, 256};
   const int tcounts[] = {256, 384, 512};
   for (int cell : cells) {
-    if (cell < std::max(1 << lut->L, 32) || superpose_smem_bytes(cell, lut->L, lut->lmin, lut->D) > 220 * 1024)
+    if (cell < std::max(1 << lut->L, 32) || superpose_smem_bytes(cell, lut->L, lut->lmin, lut->D, false, 2048) > 220 * 1024)
       continue;
     for (int nt : tcounts) {
       if (nt < superpose_min_threads()) continue;

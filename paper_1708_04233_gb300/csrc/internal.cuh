@@ -51,11 +51,11 @@ __host__ __device__ inline uint32_t plane_code(uint32_t pos, int L, int k) {
   const int bi = lev == L ? band : band - 1;
   return ((uint32_t)lev << 29) | (uint32_t)(bi * plane_size(k, L, lev) + q * plane_row(k, L, lev) + p);
 }
-// Accumulator size (complex elements, even) for levels lmin..L.
+// Accumulator size (cells, a multiple of 4) for levels lmin..L.
 __host__ __device__ inline int plane_total(int k, int L, int lmin) {
   int n = 0;
   for (int l = lmin; l <= L; ++l) n += plane_count(L, l) * plane_size(k, L, l);
-  return (n + 1) & ~1;
+  return (n + 3) & ~3;
 }
 // Most plane codes a LUT keeps: one per super-tile width k the superposition
 // can use (super-tiles are multiples of 32 pixels, at most 256).
@@ -108,7 +108,8 @@ struct LutView {
   const DepthMeta* meta;
   const float* cmax;      // largest |re| or |im| of any kept coefficient
   int lmin;               // finest level with a kept coefficient
-  const uint32_t* code;   // plane codes for the launch's super-tile width (see plane_code)
+  const uint2* code;      // records for the launch's super-tile width: plane code (see
+                          // plane_code) and value word (FP32 real part or FP16 / BF16 pair)
 };
 
 // ------------------------------------------------------------------ launchers
@@ -139,7 +140,7 @@ struct LutBuildArgs {
   const DepthMeta* meta;
   float* cmax;              // out: largest |re| or |im| kept (zeroed by caller)
   unsigned* levels;         // out: bit l set if a level-l coefficient is kept (zeroed by caller)
-  uint32_t* code;           // out: ncode x total plane codes (see plane_code)
+  uint2* code;              // out: ncode x total records (plane code, value word)
   int ncode;
   int code_k[kMaxCodes];    // super-tile width (tiles) of each code array
   long long total;          // LUT entries (all depths' capacities)
@@ -233,12 +234,17 @@ struct SuperposeArgs {
   int cell;             // super-tile side T (pixels) == binning cell
   int reach;            // pixels
   int acc_float;        // 0: exact fixed-point accumulation, 1: FP32 atomics
+  int re_only;          // 1: accumulate real parts only (every job wants bits alone)
+  int rcap;             // LUT ranges per candidate batch (superpose_range_cap)
   int* status;
   int threads;          // block size
   int grid;             // SMs: the launch puts as many CTAs on each as fit
 };
 cudaError_t launch_superpose(const SuperposeArgs& a, cudaStream_t s);
-size_t superpose_smem_bytes(int cell, int L, int lmin, int D);
+size_t superpose_smem_bytes(int cell, int L, int lmin, int D, bool re_only, int rcap);
+// Range capacity for a launch: larger when only real parts are accumulated
+// and the freed shared memory still lets two CTAs share an SM.
+int superpose_range_cap(int cell, int L, int lmin, int D, bool re_only, int threads);
 int superpose_default_cell(int L, int lmin, int D);
 
 struct InverseArgs {

@@ -495,13 +495,16 @@ __global__ void __launch_bounds__(256) encode_kernel(LutBuildArgs a) {
   if (lane == 0) a.scale[e >> 5] = s;
 }
 
-// Plane codes of every LUT entry for each super-tile width (plane_code).
+// Superposition records of every LUT entry for each super-tile width: the
+// plane code (plane_code) and the value word the superposition reads with it
+// (FP32 real part, or the FP16 / BF16 pair).
 __global__ void plane_code_kernel(LutBuildArgs a) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.total) return;
   const uint32_t p = a.pos[e];
   const int c = blockIdx.y;
-  a.code[c * a.total + e] = plane_code(p, a.L, a.code_k[c]);
+  const uint32_t data = a.dtype == WASABI_F32 ? __float_as_uint(a.val[e].x) : a.val16[e];
+  a.code[c * a.total + e] = make_uint2(plane_code(p, a.L, a.code_k[c]), data);
 }
 
 template <int L>

@@ -28,7 +28,7 @@ struct wasabi_lut {
   long long* nr_dev = nullptr;
   float* cmax = nullptr;
   unsigned* levels = nullptr;  // bit l: a level-l coefficient is kept
-  uint32_t* code = nullptr;    // ncode x total_cap plane codes, one array per super-tile width
+  uint2* code = nullptr;       // ncode x total_cap (plane code, value word), one array per super-tile width
   int ncode = 0;
   int code_k[wsb::kMaxCodes] = {};
   int lmin = 1;                // finest kept level (host copy)

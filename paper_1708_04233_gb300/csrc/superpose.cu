@@ -38,7 +38,8 @@ namespace wsb {
 namespace {
 
 constexpr int kMaxCellRows = 128;
-constexpr int kRangeCap = 2048;  // LUT ranges per batch
+constexpr int kRangeCap = 2048;  // LUT ranges per batch (complex accumulation)
+constexpr int kRangeMax = 4096;  // LUT ranges per batch when only real parts are accumulated
 constexpr int kPerMax = 8;       // range slots per thread (block size >= 256)
 // Dynamic shared memory per CTA that still lets two CTAs share an SM (with
 // the kernel's static shared memory and the per-CTA reservation).
@@ -49,11 +50,10 @@ __device__ __forceinline__ int floor_div(int a, int b) {
   return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
 }
 
+// Value of a reduced-precision LUT entry: the FP16 / BF16 pair (low half =
+// real part) of its record word times its block's FP32 scale.
 template <int DT>
-__device__ __forceinline__ float2 lut_value(const LutView& lut, int e) {
-  if (DT == WASABI_F32) return __ldg(&lut.val[e]);
-  const uint32_t q = __ldg(&lut.val16[e]);
-  const float s = __ldg(&lut.scale[e >> 5]);
+__device__ __forceinline__ float2 decode16(uint32_t q, float s) {
   float re, im;
   if (DT == WASABI_F16S) {
     re = __half2float(__ushort_as_half((unsigned short)(q & 0xffffu)));
@@ -104,33 +104,34 @@ __device__ __forceinline__ int last_le(const int* pre, int lo, int hi, int v) {
 }
 
 struct Smem {
-  float2* acc;   // accumulator planes (plane_total complex), see plane_code
+  float2* acc;   // accumulator planes (plane_total cells: complex, or real parts only), see plane_code
   int4* sp;      // survivors: Ax, Ay, depth, unused
   int2* svb;     // survivors x kept levels: accumulator base of the level, amplitude bits
   int2* rrec;    // ranges: LUT offset minus visit prefix, survivor
-  int* rpre;     // ranges: visit prefix (kRangeCap + 1)
+  int* rpre;     // ranges: visit prefix (range capacity + 1)
   int2* dbox;    // depths: tlo, thi
 };
 
-__host__ __device__ inline int survivor_cap(int k) {
-  const int p = kRangeCap / (k + 1);
+__host__ __device__ inline int survivor_cap(int k, int rcap) {
+  const int p = rcap / (k + 1);
   return p < 1024 ? p : 1024;
 }
 
-__host__ __device__ inline size_t smem_layout(int T, int L, int lmin, int D, Smem* s, unsigned char* base) {
+__host__ __device__ inline size_t smem_layout(int T, int L, int lmin, int D, bool re_only, int rcap, Smem* s,
+                                              unsigned char* base) {
   const int k = T >> L;
-  const int P = survivor_cap(k);
+  const int P = survivor_cap(k, rcap);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
     off = (off + bytes + 15) & ~(size_t)15;
     return base ? base + o : nullptr;
   };
-  unsigned char* p0 = take((size_t)plane_total(k, L, lmin) * sizeof(float2));
+  unsigned char* p0 = take((size_t)plane_total(k, L, lmin) * (re_only ? sizeof(float) : sizeof(float2)));
   unsigned char* p1 = take((size_t)P * sizeof(int4));
   unsigned char* p2 = take((size_t)P * (L - lmin + 1) * sizeof(int2));
-  unsigned char* p3 = take((size_t)kRangeCap * sizeof(int2));
-  unsigned char* p4 = take((size_t)(kRangeCap + 1) * sizeof(int));
+  unsigned char* p3 = take((size_t)rcap * sizeof(int2));
+  unsigned char* p4 = take((size_t)(rcap + 1) * sizeof(int));
   unsigned char* p5 = take((size_t)D * sizeof(int2));
   if (s) {
     s->acc = reinterpret_cast<float2*>(p0);
@@ -173,9 +174,9 @@ __host__ __device__ inline size_t smem_layout(int T, int L, int lmin, int D, Sme
 // super-tile cell (past the guard), row stride and plane size.
 // RE_ONLY (bits output alone): only real parts are read and transformed; the
 // inverse transform acts on real and imaginary parts separately, so Re u is
-// unchanged.
+// unchanged.  re_acc: the accumulator holds real parts only.
 template <int L, bool RE_ONLY>
-__device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed, float dq, int lmin, int k,
+__device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed, bool re_acc, float dq, int lmin, int k,
                                                   int kx, int ky, int Sx, int Sy, const JobDev& J,
                                                   const int* lvC, const int* lvG, const int* lvPS, int tid,
                                                   int NT) {
@@ -198,7 +199,10 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
       // step is then exactly 2^sh times the scaled one (power-of-two scaling
       // commutes with the adds and halvings while values stay normal), so
       // the signs -- the bits -- are those of the scaled field.
-      if (RE_ONLY) return make_float2(fixed ? (float)acci[2 * i] : acc[i].x, 0.f);
+      if (RE_ONLY) {
+        const int wi = re_acc ? i : 2 * i;  // word of the real part
+        return make_float2(fixed ? (float)acci[wi] : reinterpret_cast<const float*>(acc)[wi], 0.f);
+      }
       if (fixed) {
         const int2 q = reinterpret_cast<const int2*>(acci)[i];
         return make_float2((float)q.x * dq, (float)q.y * dq);
@@ -313,19 +317,23 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
 }
 
 
-template <int L, int DT>
+// RE: accumulate real parts only (every job of the launch wants bits alone).
+template <int L, int DT, bool RE>
 __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
   constexpr int TSL = 1 << (2 * L);
   static_assert(TSL <= kRangeCap, "the write-out slot table lives in the range records");
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = a.cell;
   const int k = T >> L;
-  const int P = survivor_cap(k);
+  constexpr bool re_acc = RE;
+  const int rcap = a.rcap;
+  const int P = survivor_cap(k, rcap);
   const int lmin = a.lut.lmin;
   const int NLV = L - lmin + 1;  // kept levels
   const int NA = plane_total(k, L, lmin);  // accumulator size (complex)
   Smem S;
-  smem_layout(T, L, lmin, a.lut.D, &S, smem);
+  smem_layout(T, L, lmin, a.lut.D, re_acc, rcap, &S, smem);
+  const int NW = NA * (re_acc ? 1 : 2);  // accumulator words (a multiple of 4)
   __shared__ int s_st, s_n, s_total;
   __shared__ int s_rowstart[kMaxCellRows], s_rowpre[kMaxCellRows + 1];
   __shared__ unsigned long long warp_buf[32];
@@ -389,7 +397,7 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
     const int Sx = (st % nstx) * k, Sy = (st / nstx) * k;
     const int kx = min(k, ntx - Sx), ky = min(k, nty - Sy);
 
-    for (int i = tid; i < NA / 2; i += NT) acc4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < NW / 4; i += NT) acc4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     // Cell rows within reach of the super-tile, one thread per row.
     const int X0 = Sx << L, X1 = (Sx + kx) << L, Y0 = Sy << L, Y1 = (Sy + ky) << L;
@@ -522,8 +530,8 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
         int rb = v0 < v1 ? last_le(S.rpre, 0, nranges - 1, v0) : 0;
         for (int b0 = v0; b0 < v1; b0 += 32 * kUnroll) {
           int ee[kUnroll], sv[kUnroll];
-          uint32_t ppu[kUnroll];
-          float2 vvu[kUnroll];
+          uint2 ppu[kUnroll];   // records: plane code, value word
+          float vyu[kUnroll];   // FP32 imaginary part (complex accumulation), or the block scale
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
             const int b = b0 + 32 * u;
@@ -545,25 +553,30 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
           for (int u = 0; u < kUnroll; ++u) {
             if (ee[u] >= 0) {
               ppu[u] = __ldg(&lut.code[ee[u]]);
-              vvu[u] = lut_value<DT>(lut, ee[u]);
+              if (DT != WASABI_F32) vyu[u] = __ldg(&lut.scale[ee[u] >> 5]);
+              else if (!re_acc) vyu[u] = __ldg(&lut.val[ee[u]].y);
             }
           }
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
             if (ee[u] < 0) continue;
-            const uint32_t pe = ppu[u];
-            const float2 v = vvu[u];
-            const int2 sb = S.svb[sv[u] * NLV + (int)(pe >> 29) - lmin];
-            const int ai = (int)(pe & 0x1fffffffu) + sb.x;
+            const uint2 pe = ppu[u];
+            const float2 v = DT == WASABI_F32 ? make_float2(__uint_as_float(pe.y), vyu[u]) : decode16<DT>(pe.y, vyu[u]);
+            const int2 sb = S.svb[sv[u] * NLV + (int)(pe.x >> 29) - lmin];
+            const int ai = (int)(pe.x & 0x1fffffffu) + sb.x;
             const float amp = __int_as_float(sb.y);
-            if (fixed) {
-              // a_j c in FP32, exact scaling by 2^sh (folded into amp), rounded
-              // to the nearest integer; the integer sums are exact.
+            // a_j c in FP32; in fixed point exactly scaled by 2^sh (folded
+            // into amp) and rounded to the nearest integer: the integer sums
+            // are exact.
+            if (re_acc) {
+              if (fixed) atomicAdd(&acci[ai], __float2int_rn(amp * v.x));
+              else atomicAdd(reinterpret_cast<float*>(acci) + ai, amp * v.x);
+            } else if (fixed) {
               atomicAdd(&acci[2 * ai], __float2int_rn(amp * v.x));
               atomicAdd(&acci[2 * ai + 1], __float2int_rn(amp * v.y));
             } else {
-              atomicAdd(&S.acc[ai].x, amp * v.x);
-              atomicAdd(&S.acc[ai].y, amp * v.y);
+              atomicAdd(reinterpret_cast<float*>(acci) + 2 * ai, amp * v.x);
+              atomicAdd(reinterpret_cast<float*>(acci) + 2 * ai + 1, amp * v.y);
             }
           }
         }
@@ -613,9 +626,9 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
       }
     }
     if (L >= 2 && J.u != nullptr)
-      supertile_inverse<L, false>(S.acc, fixed, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid, NT);
+      supertile_inverse<L, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid, NT);
     else if (L >= 2 && J.bits != nullptr)
-      supertile_inverse<L, true>(S.acc, fixed, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid, NT);
+      supertile_inverse<L, true>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid, NT);
     PT_MARK(5);
   }
 #ifdef WASABI_PHASE_TIMERS
@@ -624,36 +637,49 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
 #endif
 }
 
-template <int L, int DT>
+template <int L, int DT, bool RE>
 cudaError_t launch_t(const SuperposeArgs& a, cudaStream_t s) {
-  const size_t smem = superpose_smem_bytes(a.cell, a.lut.L, a.lut.lmin, a.lut.D);
-  cudaError_t e = cudaFuncSetAttribute(superpose_kernel<L, DT>,
+  const size_t smem = superpose_smem_bytes(a.cell, a.lut.L, a.lut.lmin, a.lut.D, RE, a.rcap);
+  cudaError_t e = cudaFuncSetAttribute(superpose_kernel<L, DT, RE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, superpose_kernel<L, DT>, a.threads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, superpose_kernel<L, DT, RE>, a.threads, smem);
   if (e != cudaSuccess) return e;
   // A fixed grid (independent of the batch, so the launch can be replayed
   // from a graph): CTAs without work exit at their first claim.
   const long long grid = (long long)a.grid * std::max(per_sm, 1);
-  superpose_kernel<L, DT><<<(unsigned)grid, a.threads, smem, s>>>(a);
+  superpose_kernel<L, DT, RE><<<(unsigned)grid, a.threads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int L, int DT>
+cudaError_t launch_re(const SuperposeArgs& a, cudaStream_t s) {
+  // Real-only accumulation serves the bits-only fused path (levels >= 2).
+  if (a.re_only) return L >= 2 ? launch_t<L, DT, (L >= 2)>(a, s) : cudaErrorInvalidValue;
+  return launch_t<L, DT, false>(a, s);
 }
 
 template <int L>
 cudaError_t launch_l(const SuperposeArgs& a, cudaStream_t s) {
   switch (a.lut.dtype) {
-    case WASABI_F32: return launch_t<L, WASABI_F32>(a, s);
-    case WASABI_F16S: return launch_t<L, WASABI_F16S>(a, s);
-    case WASABI_BF16S: return launch_t<L, WASABI_BF16S>(a, s);
+    case WASABI_F32: return launch_re<L, WASABI_F32>(a, s);
+    case WASABI_F16S: return launch_re<L, WASABI_F16S>(a, s);
+    case WASABI_BF16S: return launch_re<L, WASABI_BF16S>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 }  // namespace
 
-size_t superpose_smem_bytes(int cell, int L, int lmin, int D) {
-  return smem_layout(cell, L, lmin, D, nullptr, nullptr);
+size_t superpose_smem_bytes(int cell, int L, int lmin, int D, bool re_only, int rcap) {
+  return smem_layout(cell, L, lmin, D, re_only, rcap, nullptr, nullptr);
+}
+
+int superpose_range_cap(int cell, int L, int lmin, int D, bool re_only, int threads) {
+  const int big = std::min(kRangeMax, threads * kPerMax);
+  if (re_only && big > kRangeCap && superpose_smem_bytes(cell, L, lmin, D, true, big) <= kTwoCtaSmem) return big;
+  return kRangeCap;
 }
 
 // Largest power-of-two super-tile side (at most 256 pixels) whose shared
@@ -661,7 +687,7 @@ size_t superpose_smem_bytes(int cell, int L, int lmin, int D) {
 int superpose_default_cell(int L, int lmin, int D) {
   const int unit = (1 << L) > 32 ? (1 << L) : 32;
   int T = 256;
-  while (T > unit && superpose_smem_bytes(T, L, lmin, D) > kTwoCtaSmem) T >>= 1;
+  while (T > unit && superpose_smem_bytes(T, L, lmin, D, false, kRangeCap) > kTwoCtaSmem) T >>= 1;
   return T < unit ? unit : T;
 }
 
@@ -669,7 +695,8 @@ int superpose_max_cell_rows() { return kMaxCellRows; }
 int superpose_min_threads() { return kRangeCap / kPerMax; }
 
 cudaError_t launch_superpose(const SuperposeArgs& a, cudaStream_t s) {
-  if (a.threads > 512 || a.threads < kRangeCap / kPerMax || a.threads % 32 || !a.lut.code)
+  if (a.threads > 512 || a.threads < kRangeCap / kPerMax || a.threads % 32 || !a.lut.code ||
+      a.rcap < kRangeCap || a.rcap > kRangeMax || a.rcap > a.threads * kPerMax)
     return cudaErrorInvalidValue;
   switch (a.lut.L) {
     case 1: return launch_l<1>(a, s);
