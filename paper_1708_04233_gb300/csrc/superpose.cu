@@ -41,6 +41,7 @@ constexpr int kMaxCellRows = 128;
 constexpr int kRangeCap = 2048;  // LUT ranges per batch (complex accumulation)
 constexpr int kRangeMax = 4096;  // LUT ranges per batch when only real parts are accumulated
 constexpr int kPerMax = 8;       // range slots per thread (block size >= 256)
+constexpr int kLookahead = 32;   // range starts one visit lookup reads (one per lane)
 // Dynamic shared memory per CTA that still lets two CTAs share an SM (with
 // the kernel's static shared memory and the per-CTA reservation).
 constexpr size_t kTwoCtaSmem = 104 * 1024;
@@ -130,8 +131,8 @@ __host__ __device__ inline size_t smem_layout(int T, int L, int lmin, int D, boo
   unsigned char* p0 = take((size_t)plane_total(k, L, lmin) * (re_only ? sizeof(float) : sizeof(float2)));
   unsigned char* p1 = take((size_t)P * sizeof(int4));
   unsigned char* p2 = take((size_t)P * (L - lmin + 1) * sizeof(int2));
-  unsigned char* p3 = take((size_t)rcap * sizeof(int2));
-  unsigned char* p4 = take((size_t)(rcap + 1) * sizeof(int));
+  unsigned char* p3 = take((size_t)(rcap + 1) * sizeof(int2));
+  unsigned char* p4 = take((size_t)(rcap + 1 + kLookahead) * sizeof(int));
   unsigned char* p5 = take((size_t)D * sizeof(int2));
   if (s) {
     s->acc = reinterpret_cast<float2*>(p0);
@@ -516,7 +517,12 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
             vrun += rln[u];
           }
         }
-        if (tid == 0) S.rpre[nranges] = nvis;
+        // Terminator, then sentinels for the lookahead of the visit lookup.
+        if (tid == 0) {
+          S.rpre[nranges] = nvis;
+          S.rrec[nranges] = make_int2(0, 0);
+        }
+        if (tid < kLookahead) S.rpre[nranges + 1 + tid] = 0x7fffffff;
       }
       __syncthreads();
       PT_MARK(3);
@@ -524,30 +530,45 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
       // chunks per round: every chunk's range lookup (shared memory only) and
       // LUT loads are issued before any of them is consumed.
       if (nvis > 0) {
-        constexpr int kUnroll = 4;
+        constexpr int kUnroll = 4;  // visits per lane per round: two windows of 64
         const int vper = (nvis + nwarps - 1) / nwarps;
         const int v0 = warp * vper, v1 = min(nvis, v0 + vper);
+        const unsigned le = (2u << lane) - 1u;  // lanes <= this one
         int rb = v0 < v1 ? last_le(S.rpre, 0, nranges - 1, v0) : 0;
         for (int b0 = v0; b0 < v1; b0 += 32 * kUnroll) {
           int ee[kUnroll], sv[kUnroll];
           uint2 ppu[kUnroll];   // records: plane code, value word
           float vyu[kUnroll];   // FP32 imaginary part (complex accumulation), or the block scale
 #pragma unroll
-          for (int u = 0; u < kUnroll; ++u) {
-            const int b = b0 + 32 * u;
-            const int i = b + lane;
-            // Range of visit i: rb plus the number of range starts in (b, i].
-            // Ranges are non-empty, so their starts are distinct.
-            const int f = rb + 1 + lane;
-            const int bnd = f <= nranges ? S.rpre[f] : 0x7fffffff;
-            const int mpos = bnd - b;
-            const unsigned bit = (mpos >= 0 && mpos < 32) ? (1u << mpos) : 0u;
-            const unsigned M = __reduce_or_sync(0xffffffffu, bit);
-            const int r = min(rb + __popc(M & ((2u << lane) - 1u)), nranges - 1);
-            rb = __shfl_sync(0xffffffffu, r, 31);
-            const int2 rec = S.rrec[r];
-            ee[u] = i < v1 ? i + rec.x : -1;
-            sv[u] = rec.y;
+          for (int h = 0; h < kUnroll / 2; ++h) {
+            // Window [b, b + 64): lane l takes visits b + l and b + 32 + l.  The
+            // range of visit i is rb plus the number of range starts in (b, i]
+            // (ranges are non-empty, so starts are distinct); one load per
+            // lane brings the next 32 starts, enough unless 32 of them fall
+            // inside the window -- then it is looked up 32 visits at a time.
+            const int b = b0 + 64 * h;
+            const int mpos = S.rpre[rb + 1 + lane] - b;
+            const unsigned lo = (unsigned)mpos < 32u ? 1u << mpos : 0u;
+            const unsigned hi = (unsigned)(mpos - 32) < 32u ? 1u << (mpos - 32) : 0u;
+            const unsigned Mlo = __reduce_or_sync(0xffffffffu, lo), Mhi = __reduce_or_sync(0xffffffffu, hi);
+            int r0, r1;
+            if (__popc(Mlo) + __popc(Mhi) < kLookahead) {
+              r0 = rb + __popc(Mlo & le);
+              r1 = rb + __popc(Mlo) + __popc(Mhi & le);
+            } else {  // many short ranges: two windows of 32
+              r0 = rb + __popc(Mlo & le);
+              const int rm = __shfl_sync(0xffffffffu, r0, 31);
+              const int mp2 = S.rpre[rm + 1 + lane] - (b + 32);
+              const unsigned M2 = __reduce_or_sync(0xffffffffu, (unsigned)mp2 < 32u ? 1u << mp2 : 0u);
+              r1 = rm + __popc(M2 & le);
+            }
+            rb = __shfl_sync(0xffffffffu, r1, 31);
+            const int2 rec0 = S.rrec[r0], rec1 = S.rrec[r1];
+            const int i0 = b + lane, i1 = b + 32 + lane;
+            ee[2 * h] = i0 < v1 ? i0 + rec0.x : -1;
+            sv[2 * h] = rec0.y;
+            ee[2 * h + 1] = i1 < v1 ? i1 + rec1.x : -1;
+            sv[2 * h + 1] = rec1.y;
           }
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
