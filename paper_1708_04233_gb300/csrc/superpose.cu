@@ -28,6 +28,7 @@
 // Every output element is written exactly once: no global atomics and no
 // zeroing pass.  Shared-memory atomics resolve collisions between survivors.
 #include <algorithm>
+#include <cstdlib>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -162,6 +163,14 @@ __host__ __device__ inline size_t smem_layout(int T, int L, int lmin, int D, boo
   } while (0)
 #endif
 
+// Bit i of an 8-bit value moved to bit 4 i.
+__device__ __forceinline__ unsigned spread_nibbles(unsigned x) {
+  x = (x | (x << 12)) & 0x000f000fu;
+  x = (x | (x << 6)) & 0x03030303u;
+  x = (x | (x << 3)) & 0x11111111u;
+  return x;
+}
+
 // Inverse transform (Sec. 1, step 3) and binarisation (Sec. 2) of a finished
 // super-tile, straight from the shared-memory accumulator: the wavelet
 // buffer never goes to global memory.  Levels finer than lmin were never
@@ -281,8 +290,15 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
           }
           put_u(y0 + 2 * ay, pa, pa, pb, pb);
           put_u(y0 + 2 * ay + 1, pa, pa, pb, pb);
-          if (bits != nullptr) {  // both rows of the pair are equal
-            const unsigned v = word(pa.x, pa.x, pb.x, pb.x);
+          if (bits != nullptr) {
+            // Both rows of the pair are equal, and each level-1 value covers
+            // two neighbouring pixels: two warp votes give the signs of the
+            // warp's 64 values; lane group q (8 lanes, 32 pixels) owns byte q
+            // of each vote, spread to one bit per nibble and doubled.
+            const unsigned va = __ballot_sync(0xffffffffu, valid && pa.x > 0.f);
+            const unsigned vb = __ballot_sync(0xffffffffu, valid && pb.x > 0.f);
+            const int q = (lane >> 3) * 8;
+            const unsigned v = spread_nibbles((va >> q) & 0xffu) * 3u | (spread_nibbles((vb >> q) & 0xffu) * 3u) << 2;
             put_bits(y0 + 2 * ay, v);
             put_bits(y0 + 2 * ay + 1, v);
           }
@@ -398,20 +414,25 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
     const int Sx = (st % nstx) * k, Sy = (st / nstx) * k;
     const int kx = min(k, ntx - Sx), ky = min(k, nty - Sy);
 
-    for (int i = tid; i < NW / 4; i += NT) acc4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-
-    // Cell rows within reach of the super-tile, one thread per row.
+    // Cell rows within reach of the super-tile, one thread per row; their
+    // offsets are loaded before the accumulator is zeroed, so the zeroing
+    // covers the load latency.
     const int X0 = Sx << L, X1 = (Sx + kx) << L, Y0 = Sy << L, Y1 = (Sy + ky) << L;
     const int cx0 = max(0, floor_div(X0 - a.reach, a.cell));
     const int cx1 = min(ncx - 1, floor_div(X1 - 1 + a.reach, a.cell));
     const int cy0 = max(0, floor_div(Y0 - a.reach, a.cell));
     const int cy1 = min(ncy - 1, floor_div(Y1 - 1 + a.reach, a.cell));
     const int ncrows = (cx0 <= cx1 && cy0 <= cy1) ? cy1 - cy0 + 1 : 0;
+    int row_s0 = 0, row_s1 = 0;
     if (tid < ncrows) {
       const int c0 = (cy0 + tid) * ncx;
-      const int s0 = __ldg(&cell_off[c0 + cx0]);
-      s_rowstart[tid] = s0;
-      s_rowpre[tid] = __ldg(&cell_off[c0 + cx1 + 1]) - s0;
+      row_s0 = __ldg(&cell_off[c0 + cx0]);
+      row_s1 = __ldg(&cell_off[c0 + cx1 + 1]);
+    }
+    for (int i = tid; i < NW / 4; i += NT) acc4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < ncrows) {
+      s_rowstart[tid] = row_s0;
+      s_rowpre[tid] = row_s1 - row_s0;
     }
     __syncthreads();
     if (warp == 0) {  // exclusive prefix over <= 128 rows, 4 per lane
@@ -699,6 +720,10 @@ size_t superpose_smem_bytes(int cell, int L, int lmin, int D, bool re_only, int 
 
 int superpose_range_cap(int cell, int L, int lmin, int D, bool re_only, int threads) {
   const int big = std::min(kRangeMax, threads * kPerMax);
+  if (const char* v = std::getenv("WASABI_RANGE_CAP")) {  // tuning override
+    const int r = std::max(kRangeCap, std::min(big, std::atoi(v)));
+    if (superpose_smem_bytes(cell, L, lmin, D, re_only, r) <= 220 * 1024) return r;
+  }
   if (re_only && big > kRangeCap && superpose_smem_bytes(cell, L, lmin, D, true, big) <= kTwoCtaSmem) return big;
   return kRangeCap;
 }
