@@ -100,3 +100,28 @@ def test_autotune_picks_a_valid_configuration(setup, orc):
     torch.cuda.synchronize()
     assert rel_l2(r[0]["wbuf"].cpu().numpy(), a) <= TOL
     b.close()
+
+
+def test_bits_only_batch_uses_real_accumulation_and_matches(setup, orc):
+    """A batch whose jobs all want bits alone accumulates real parts only (its
+    own graph); the bits equal the one-hologram call's, across a replay with a
+    new mix and after a complex batch on the same stream."""
+    w, _, _ = setup
+    # A LUT of its own: no autotuned entry, so every call here uses the
+    # default super-tile and the fixed-point results agree exactly.
+    lut = w.build_lut(LAM, PITCH, w.depth_grid(ZMIN, ZMAX, D), W, L, GAMMA)
+    batch = w.Batch(lut, 6, side_hint=512, use_graph=True)
+    stream = torch.cuda.Stream()
+    for specs in ([(21, 300, 512, "bits", 0), (22, 40, 256, "bits", 1), (23, 0, 128, "bits", 0)],
+                  [(24, 250, 384, "both", 0)],
+                  [(25, 500, 768, "bits", 1), (26, 90, 512, "bits", 0)]):
+        made = [_job(w, orc, *s) for s in specs]
+        with torch.cuda.stream(stream):
+            res = batch.run([j for _, j in made], stream=stream)
+        stream.synchronize()
+        w.sync_status(stream)
+        for (_, j), r in zip(made, res):
+            ref = w.hologram(lut, j["points"], j["w"], j["h"], want="bits", rule=j["rule"])
+            assert torch.equal(r["bits"], ref)
+    batch.close()
+    lut.close()

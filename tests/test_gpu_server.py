@@ -108,3 +108,15 @@ def test_requests_refused(setup, orc):
     r = srv.wait(srv.submit(h, 256, 256), timeout=30)
     assert r["bits"] is not None and r["latency_s"] >= 0
     srv.close()
+
+
+def test_bits_only_requests_match_the_one_hologram_call(setup, orc):
+    w, lut, _ = setup
+    srv = w.Server(lut, 1 << 28, streams=2, max_batch=8, side_hint=512)
+    jobs = [_job(w, orc, *s) for s in SPECS[:6]]
+    ids = [srv.submit(h, s[2], s[2], want="bits") for (_, h), s in zip(jobs, SPECS[:6])]
+    for (_, h), s, i in zip(jobs, SPECS[:6], ids):
+        r = srv.wait(i, timeout=60)
+        ref = w.hologram(lut, h.cuda(), s[2], s[2], want="bits").cpu()
+        assert torch.equal(r["bits"], ref)
+    srv.close()
