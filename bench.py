@@ -34,6 +34,24 @@ METRIC = "WASABI hologram Mpoint*coeff/s at 65536^2 (hologram s, HBM fraction)"
 UNIT = "Mpoint*coeff/s"
 
 
+# DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum, one ncu capture of the full workload), valid only
+# while the kernel source is the one that was profiled (sha256 prefix of
+# superpose.cu); see profiles/launches_C3_65536sq_fused.md.
+TRAFFIC = {("C3", "fused"): ("3efdf601d49c0444", 38.1e6 + 475.4e6)}
+
+
+def _traffic(c, path):
+    import hashlib
+    ent = TRAFFIC.get((c.name, path))
+    if ent is None:
+        return None
+    src = os.path.join(ROOT, "paper_1708_04233_gb300", "csrc", "superpose.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    return ent[1] if sha == ent[0] else None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -435,18 +453,21 @@ def run_gpu(args, c):
                               "peak": peak, "peak_source": peak_kind}
     hot_ms = stage_ms["hologram" if fused else "superpose"]
     # Dominant kernel: the superposition (with the fused inverse + binarisation
-    # epilogue in the fused form).  It is a shared-memory scatter-add: two
-    # 32-bit shared-memory atomic adds per point-coefficient (real, imaginary).
+    # epilogue in the fused form).  It is a shared-memory scatter-add: per
+    # point-coefficient one 32-bit shared-memory atomic add per accumulated
+    # part -- the real part alone when only bits are produced (Re u depends
+    # only on the real parts), real and imaginary parts otherwise.
     # Peak: one 32-bit access per bank per clock, 32 banks x 152 SMs x max SM clock.
+    parts = 1 if (fused and want == "bits") else 2
     smem_peak = 32 * 152 * 2070e6 / 1e9  # Gop/s
-    ach = 2 * units / (hot_ms * 1e-3) / 1e9
+    ach = parts * units / (hot_ms * 1e-3) / 1e9
     roof = {"kernel": (f"superpose_kernel<{c.L},{c.lut_dtype}> with fused inverse"
                        + (" + binarisation" if want == "bits" else "") if fused
                        else f"superpose_kernel<{c.L},{c.lut_dtype}>") + " (+ binning kernels, one ABI call)",
             "bound": "alu", "achieved": ach, "peak": smem_peak, "unit": "Gop/s", "frac": ach / smem_peak,
             "peak_source": "derived: 32 banks x 152 SMs x 2070 MHz (shared-memory 32-bit ops)",
-            "algorithmic_ops": 2 * units, "traffic": None}
-    lut_kernels = 5 + (0 if c.lut_dtype in ("f32", 0) else 1)
+            "algorithmic_ops": parts * units, "ops_per_point_coeff": parts, "traffic": _traffic(c, args.path)}
+    lut_kernels = 6 + (0 if c.lut_dtype in ("f32", 0) else 1)  # psf, select, tile count/scan, scatter, codes
     per_step = lut_kernels + 1 + 6 + (0 if fused else 1)
 
     if rank == 0:

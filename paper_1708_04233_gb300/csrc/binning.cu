@@ -106,10 +106,10 @@ __global__ void __launch_bounds__(256) count_kernel(BinArgs b) {
 }
 
 // Exclusive scan of each job's cell counts into off[0..ncells] and
-// cursor[0..ncells): one block per job at a time, chunks of 16,384 counts,
-// each thread 16 consecutive counts, a running carry between chunks.
+// cursor[0..ncells): one block per job at a time, chunks of 4,096 counts,
+// each thread four consecutive counts, a running carry between chunks.
 __global__ void __launch_bounds__(1024) scan_kernel(BinArgs b) {
-  constexpr int CPT = 16;  // counts per thread
+  constexpr int CPT = 4;  // counts per thread
   __shared__ unsigned warp_sum[32];
   __shared__ unsigned s_carry;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
