@@ -31,11 +31,15 @@
 //      are dropped.
 //   R7 binary hologram (Sec. 2): bit = 1 iff Re(u) > 0 (unit plane reference).
 //   R8 phase arithmetic of the FP32 PSF used for selection (so that the CPU
-//      and the GPU select the same coefficients): r = sqrt(fma(n, p^2, z^2)),
-//      t = r / lambda, f = t - floor(t) in FP64; g = (float) f; cos and sin of
-//      2 pi g from quadrant reduction and Taylor series in Horner form with
-//      fused multiply-adds in FP32 (J.-M. Muller, "Elementary Functions",
-//      range reduction + polynomial evaluation).
+//      and the GPU select the same coefficients): t = r / lambda =
+//      sqrt(s), s = fma(n, (p/lambda)^2, (z/lambda)^2) in FP64, evaluated as
+//      the FP32 square root t0 of s plus one FP64 Newton step
+//      t = t0 + fma(-t0, t0, s) * (float)(1 / (2 t0)); f = t - floor(t);
+//      g = (float) f; cos and sin of 2 pi g from quadrant reduction and
+//      Taylor series in Horner form with fused multiply-adds in FP32
+//      (J.-M. Muller, "Elementary Functions", range reduction + polynomial
+//      evaluation).  The FP64 PSF and Eq. (1) use the plain definition
+//      r = sqrt(n p^2 + z^2), t = r / lambda.
 //   R9 Eq. (1) has no 1/r factor and a +i sign, as printed; a_j is used as an
 //      amplitude.
 //
@@ -127,6 +131,22 @@ double phase_frac(int64_t n, double p2, double z2, double lambda) {
   return t - std::floor(t);
 }
 
+// The same fractional part, evaluated the way the FP32 PSF (R8) and the GPU
+// LUT builder evaluate it: t = r / lambda = sqrt(s) with s = n (p/lambda)^2 +
+// (z/lambda)^2, taken as the FP32 square root of s plus one Newton step in
+// FP64 (residual s - t0^2 by a fused multiply-add, divided by 2 t0 through
+// the FP32 reciprocal).  The error against phase_frac is ~1e-11 (the Newton
+// step squares the FP32 error); q = (p/lambda)^2, c = (z/lambda)^2.
+double phase_frac_newton(int64_t n, double q, double c) {
+  const double s = std::fma((double)n, q, c);
+  const float t0f = std::sqrt((float)s);
+  const double t0 = (double)t0f;
+  const double res = std::fma(-t0, t0, s);
+  const float inv = 1.0f / (2.0f * t0f);
+  const double t = t0 + res * (double)inv;
+  return t - std::floor(t);
+}
+
 // ---------------------------------------------------------------- the PSF --
 
 // Sec. 1, step 1: u_z = exp(i k r) circ(...), sampled on a W x W window whose
@@ -135,14 +155,15 @@ double phase_frac(int64_t n, double p2, double z2, double lambda) {
 void psf_f32(double lambda, double pitch, double z, int W, float* out) {
   const double R = support_radius_px(lambda, pitch, z);
   const double R2 = R * R;
-  const double p2 = pitch * pitch, z2 = z * z;
+  const double pl = pitch / lambda, zl = z / lambda;
+  const double q = pl * pl, cz = zl * zl;
   for (int v = 0; v < W; ++v) {
     for (int u = 0; u < W; ++u) {
       const int64_t du = u - W / 2, dv = v - W / 2;
       const int64_t n = du * du + dv * dv;
       float c = 0.0f, s = 0.0f;
       if ((double)n < R2) {
-        const float g = (float)phase_frac(n, p2, z2, lambda);
+        const float g = (float)phase_frac_newton(n, q, cz);
         sincos2pi_f32(g, &c, &s);
       }
       out[2 * ((int64_t)v * W + u) + 0] = c;

@@ -356,6 +356,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   sc.take<int>((size_t)n_depths * 2 * lut->nwt * lut->nwt);
   sc.take<double>((size_t)n_depths);
   sc.take<double>((size_t)n_depths);
+  sc.take<double>((size_t)n_depths);
   sc.take<long long>((size_t)n_depths);
   void* scratch = nullptr;
   e = cudaMallocAsync(&scratch, align_up(sc.off, 256), s);
@@ -378,8 +379,17 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   a.tile_cnt = sc.take<int>((size_t)n_depths * 2 * lut->nwt * lut->nwt);
   double* z_dev = sc.take<double>((size_t)n_depths);
   double* R2_dev = sc.take<double>((size_t)n_depths);
+  double* c_dev = sc.take<double>((size_t)n_depths);
   long long* target_dev = sc.take<long long>((size_t)n_depths);
-  a.z_dev = z_dev; a.R2_dev = R2_dev; a.target_dev = target_dev;
+  a.z_dev = z_dev; a.R2_dev = R2_dev; a.target_dev = target_dev; a.c_dev = c_dev;
+  // Phase constants of reading R8 (plain IEEE double operations).
+  const double pl = pitch / lambda;
+  a.q = pl * pl;
+  std::vector<double> cz(n_depths);
+  for (int d = 0; d < n_depths; ++d) {
+    const double zl = depths_host[d] / lambda;
+    cz[d] = zl * zl;
+  }
   a.nr_dev = lut->nr_dev; a.pos = lut->pos; a.val = lut->val; a.val16 = lut->val16; a.scale = lut->scale;
   a.tile_off = lut->tile_off; a.meta = lut->meta_dev; a.cmax = lut->cmax; a.levels = lut->levels;
   a.code = lut->code; a.ncode = lut->ncode; a.total = base;
@@ -389,6 +399,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   bool okc = true;
   okc = okc && cudaMemcpyAsync(z_dev, depths_host, sizeof(double) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
   okc = okc && cudaMemcpyAsync(R2_dev, R2.data(), sizeof(double) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  okc = okc && cudaMemcpyAsync(c_dev, cz.data(), sizeof(double) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
   okc = okc && cudaMemcpyAsync(target_dev, target.data(), sizeof(long long) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
   okc = okc && cudaMemcpyAsync(lut->meta_dev, lut->meta.data(), sizeof(DepthMeta) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
   okc = okc && cudaMemsetAsync(a.nnz, 0, sizeof(unsigned long long) * n_depths, s) == cudaSuccess;

@@ -124,6 +124,8 @@ struct LutBuildArgs {
   long long max_cap;        // largest per-depth capacity (entries)
   double lambda, pitch;
   const double* z_dev;      // D depths
+  const double* c_dev;      // D values (z / lambda)^2
+  double q;                 // (pitch / lambda)^2
   const double* R2_dev;     // D squared radii (pixels^2)
   const long long* target_dev;  // D budgets (LLONG_MAX = keep all nonzero)
   float2* coef;             // scratch D * W * W

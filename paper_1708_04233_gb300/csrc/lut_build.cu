@@ -116,9 +116,14 @@ psf_haar_kernel(LutBuildArgs a) {
     const long long dv = (long long)(ty * TS + pv) - a.W / 2;
     const long long n = du * du + dv * dv;
     if ((double)n < a.R2_dev[d]) {
-      const double z = a.z_dev[d];
-      const double r = __dsqrt_rn(__fma_rn((double)n, __dmul_rn(a.pitch, a.pitch), __dmul_rn(z, z)));
-      const double t = __ddiv_rn(r, a.lambda);
+      // r / lambda = sqrt(s), s = n (p/lambda)^2 + (z/lambda)^2: FP32 square
+      // root plus one FP64 Newton step (residual by a fused multiply-add).
+      const double s = __fma_rn((double)n, a.q, a.c_dev[d]);
+      const float t0f = __fsqrt_rn(__double2float_rn(s));
+      const double t0 = (double)t0f;
+      const double res = __fma_rn(-t0, t0, s);
+      const float inv = __frcp_rn(2.0f * t0f);
+      const double t = __dadd_rn(t0, __dmul_rn(res, (double)inv));
       const double f = __dsub_rn(t, floor(t));
       sincos2pi(__double2float_rn(f), &val.x, &val.y);
     }
