@@ -628,7 +628,7 @@ wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* poi
   JobDev J = make_job(lut, points_dev, n, holo_w, holo_h, rule, cell, static_cast<float2*>(wbuf_dev),
                       static_cast<float2*>(u_dev), bits_dev);
   J.sorted = b.sorted; J.cnt = b.cnt; J.off = b.off; J.cursor = b.cursor;
-  cudaError_t e = launch_init_single(J, b.jobs, b.batch, super_tiles(J.ntx, J.nty, cell >> lut->L), 0, s);
+  cudaError_t e = launch_init_single(J, b.jobs, b.batch, super_tiles(J.ntx, J.nty, cell >> lut->L), s);
   if (e != cudaSuccess) return cuda_fail("superpose: init", e);
   BinArgs ba;
   ba.jobs = b.jobs; ba.batch = b.batch; ba.D = lut->D; ba.cell = cell; ba.reach = lut->reach;
@@ -668,16 +668,13 @@ wasabi_status wasabi_inverse_haar(const void* wbuf_dev, int holo_w, int holo_h, 
   if (!device_info(&status, &sms)) return WASABI_E_CUDA;
   InverseArgs ia;
   std::memset(&ia, 0, sizeof ia);
-  ia.jobs = nullptr;
-  ia.batch = nullptr;
-  ia.job0.wbuf = const_cast<float2*>(static_cast<const float2*>(wbuf_dev));
-  ia.job0.u = static_cast<float2*>(u_dev);
-  ia.job0.bits = bits_dev;
-  ia.job0.w = holo_w;
-  ia.job0.h = holo_h;
-  ia.job0.ntx = holo_w >> levels;
-  ia.job0.nty = holo_h >> levels;
-  ia.ninv0 = inverse_strips(holo_w, holo_h, levels);
+  ia.wbuf = static_cast<const float2*>(wbuf_dev);
+  ia.u = static_cast<float2*>(u_dev);
+  ia.bits = bits_dev;
+  ia.w = holo_w;
+  ia.h = holo_h;
+  ia.ntx = holo_w >> levels;
+  ia.nstrips = inverse_strips(holo_w, holo_h, levels);
   ia.L = levels;
   ia.status = status;
   ia.num_sms = sms;
@@ -749,7 +746,7 @@ wasabi_status cgh_direct(double lambda, double pitch, const double* depths_host,
   std::memset(&J, 0, sizeof J);
   J.pts = points_dev; J.sorted = b.sorted; J.cnt = b.cnt; J.off = b.off; J.cursor = b.cursor;
   J.n = n; J.w = holo_w; J.h = holo_h; J.ncx = b.ncx; J.ncy = b.ncy; J.ncells = b.ncx * b.ncy;
-  e = launch_init_single(J, b.jobs, b.batch, 0, 0, s);
+  e = launch_init_single(J, b.jobs, b.batch, 0, s);
   if (e != cudaSuccess) return cuda_fail("cgh_direct: init", e);
   BinArgs ba;
   ba.jobs = b.jobs; ba.batch = b.batch; ba.D = n_depths; ba.cell = cell; ba.reach = reach;

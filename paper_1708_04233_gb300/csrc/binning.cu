@@ -38,11 +38,10 @@ __global__ void quantize_kernel(const int32_t* __restrict__ x, const int32_t* __
   out[i] = p;
 }
 
-__global__ void init_single_kernel(JobDev job, JobDev* jobs, BatchDev* b, int nsp, int ninv) {
+__global__ void init_single_kernel(JobDev job, JobDev* jobs, BatchDev* b, int nsp) {
   jobs[0] = job;
   b->njobs = 1;
   b->nsp = nsp;
-  b->ninv = ninv;
   b->npts = job.n;
 }
 
@@ -192,8 +191,8 @@ cudaError_t launch_quantize(const int32_t* x, const int32_t* y, const double* z,
 }
 
 cudaError_t launch_init_single(const JobDev& job, JobDev* jobs_dev, BatchDev* batch_dev, int nsp,
-                               int ninv, cudaStream_t s) {
-  init_single_kernel<<<1, 1, 0, s>>>(job, jobs_dev, batch_dev, nsp, ninv);
+                               cudaStream_t s) {
+  init_single_kernel<<<1, 1, 0, s>>>(job, jobs_dev, batch_dev, nsp);
   return cudaGetLastError();
 }
 

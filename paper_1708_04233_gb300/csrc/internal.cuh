@@ -183,15 +183,14 @@ struct JobDev {
   int* off;                 // ncells + 1 cell offsets, scratch
   int* cursor;              // ncells scatter cursors, scratch
   float2* wbuf;             // tile-major wavelet buffer (w * h)
-  float2* u;                // inverse output, complex row-major (or null)
-  uint8_t* bits;            // inverse output, packed bits (or null)
+  float2* u;                // field output of the fused inverse, complex row-major (or null)
+  uint8_t* bits;            // binarised output of the fused inverse, packed bits (or null)
   long long n;              // points
   long long pt0;            // first point of this job in the batch's point numbering
   int w, h, ntx, nty;       // pixels and 2^L x 2^L tiles
   int ncx, ncy;             // binning cells of cell x cell pixels
   int rule;                 // shift rule
   int sp0;                  // first superposition item (super-tile) of this job
-  int inv0;                 // first inverse item (strip) of this job
   int ncells;               // ncx * ncy
   float amax;               // largest |a| over the job's binned points (zeroed by zero_kernel)
 };
@@ -199,8 +198,7 @@ struct JobDev {
 struct BatchDev {
   int njobs;
   int nsp;                  // superposition items (super-tiles) over all jobs
-  int ninv;                 // inverse items (strips) over all jobs
-  int pad;
+  int pad[2];
   long long npts;           // points over all jobs
   int counter;              // superposition work counter (zeroed by zero_kernel)
   unsigned long long timers[6];  // phase cycle counters (profiling builds only)
@@ -250,10 +248,11 @@ int superpose_range_cap(int cell, int L, int lmin, int D, bool re_only, int thre
 int superpose_default_cell(int L, int lmin, int D);
 
 struct InverseArgs {
-  const JobDev* jobs;       // device job table, or null: job0 is the only job
-  const BatchDev* batch;    // totals (with a job table)
-  JobDev job0;              // the job of a one-job call (kernel parameter)
-  int ninv0;                // its strips
+  const float2* wbuf;       // tile-major wavelet buffer
+  float2* u;                // complex output (or null)
+  uint8_t* bits;            // packed bits output (or null)
+  int w, h, ntx;            // pixels; 2^L x 2^L tiles per row
+  int nstrips;              // work items: strips of 256 pixels x 2^L rows
   int L;
   int* status;
   int num_sms;
@@ -263,8 +262,7 @@ cudaError_t launch_inverse(const InverseArgs& a, cudaStream_t s);
 int inverse_strips(int w, int h, int L);
 
 // Writes one job and the batch totals of a one-job batch into device memory.
-cudaError_t launch_init_single(const JobDev& job, JobDev* jobs_dev, BatchDev* batch_dev, int nsp,
-                               int ninv, cudaStream_t s);
+cudaError_t launch_init_single(const JobDev& job, JobDev* jobs_dev, BatchDev* batch_dev, int nsp, cudaStream_t s);
 cudaError_t launch_haar_forward(const float2* u, int w, int h, int L, float2* wbuf, cudaStream_t s);
 cudaError_t launch_wbuf_to_mallat(const float2* wbuf, int w, int h, int L, float2* out,
                                   cudaStream_t s);

@@ -74,17 +74,15 @@ template <int L>
 __global__ void __launch_bounds__(InvCfg<L>::NT) inverse_kernel(const __grid_constant__ InverseArgs a) {
   using C = InvCfg<L>;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ int s_inv0[kMaxJobs];
   float2* ring = reinterpret_cast<float2*>(smem);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * C::STAGE_BYTES);
 
-  // Items are the strips of all jobs: item -> (job, strip) by the jobs' first items.
-  const int nj = a.jobs ? min(a.batch->njobs, kMaxJobs) : 1;
-  const long long nitems = a.jobs ? a.batch->ninv : a.ninv0;
+  // Items are the strips of the hologram, dealt to the CTAs round-robin.
+  const long long nitems = a.nstrips;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const long long count = nitems > blockIdx.x ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   int* status = a.status;
-  for (int j = tid; j < nj; j += blockDim.x) s_inv0[j] = a.jobs ? a.jobs[j].inv0 : 0;
+  const int spr = (a.ntx + C::G - 1) / C::G;  // strips per tile row
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
@@ -92,25 +90,20 @@ __global__ void __launch_bounds__(InvCfg<L>::NT) inverse_kernel(const __grid_con
   }
   __syncthreads();
 
-  // Job, tile row and strip column of the CTA's i-th item.
-  auto locate = [&](long long i, int* ty, int* sx) -> const JobDev& {
+  // Tile row and strip column of the CTA's i-th item.
+  auto locate = [&](long long i, int* ty, int* sx) {
     const int item = (int)(blockIdx.x + i * gridDim.x);
-    const int j = job_of(s_inv0, nj, item);
-    const JobDev& J = a.jobs ? a.jobs[j] : a.job0;
-    const int spr = (J.ntx + C::G - 1) / C::G;  // strips per tile row
-    const int ls = item - s_inv0[j];
-    *ty = ls / spr;
-    *sx = ls - *ty * spr;
-    return J;
+    *ty = item / spr;
+    *sx = item - *ty * spr;
   };
 
   auto issue = [&](long long i, int stage) {  // warp 0 only
     int ty, sx;
-    const JobDev& J = locate(i, &ty, &sx);
-    const int ntx = J.ntx;
+    locate(i, &ty, &sx);
+    const int ntx = a.ntx;
     const int tx0 = sx * C::G;
     const int gv = min(C::G, ntx - tx0);
-    const float2* src = J.wbuf + ((size_t)ty * ntx + tx0) * C::TSL;
+    const float2* src = a.wbuf + ((size_t)ty * ntx + tx0) * C::TSL;
     float2* dst = ring + (size_t)stage * C::G * C::STRIDE;
     if (lane == 0) mbar_expect_tx(&full[stage], (unsigned)(gv * C::TSL * sizeof(float2)));
     __syncwarp();
@@ -138,11 +131,11 @@ __global__ void __launch_bounds__(InvCfg<L>::NT) inverse_kernel(const __grid_con
       break;
     }
     int ty, sx;
-    const JobDev& J = locate(i, &ty, &sx);
-    const int w = J.w;
-    float2* u = J.u;
-    uint8_t* bits = J.bits;
-    const int gv = min(C::G, J.ntx - sx * C::G);
+    locate(i, &ty, &sx);
+    const int w = a.w;
+    float2* u = a.u;
+    uint8_t* bits = a.bits;
+    const int gv = min(C::G, a.ntx - sx * C::G);
     const bool valid = g < gv;
     const float2* c = ring + (size_t)stage * C::G * C::STRIDE + (size_t)(valid ? g : 0) * C::STRIDE;
 
@@ -306,10 +299,8 @@ cudaError_t launch_inv_l(const InverseArgs& a, cudaStream_t s) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, inverse_kernel<L>, C::NT, C::SMEM);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  // One job: no more CTAs than strips.  A job table: a fixed grid (the item
-  // count lives on the device), so the launch can be replayed from a graph.
-  long long grid = (long long)a.num_sms * per_sm;
-  if (!a.jobs) grid = std::min<long long>(grid, a.ninv0);
+  // No more CTAs than strips.
+  const long long grid = std::min<long long>((long long)a.num_sms * per_sm, a.nstrips);
   if (grid <= 0) return cudaSuccess;
   inverse_kernel<L><<<(unsigned)grid, C::NT, C::SMEM, s>>>(a);
   return cudaGetLastError();
