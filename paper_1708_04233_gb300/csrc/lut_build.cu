@@ -253,13 +253,21 @@ __global__ void __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
         if ((kb & hi_mask) == prefix) atomicAdd(&hist[(kb >> shift) & (nbins - 1)], 1u);
       }
     } else {
+      // Eight loads in flight per lane before any is used.
       for (int ti = warp; ti < ntb; ti += nwarps) {
         int tx, ty;
         it.tile(ti, &tx, &ty);
         const unsigned long long* kt = kd + it.coef_index(tx, ty, 0);
-        for (int slot = lane; slot < tsl; slot += 32) {
-          const unsigned long long kb = kt[slot];
-          if (kb != 0 && (kb & hi_mask) == prefix) atomicAdd(&hist[(kb >> shift) & (nbins - 1)], 1u);
+        for (int slot0 = 0; slot0 < tsl; slot0 += 256) {
+          unsigned long long kb[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int slot = slot0 + lane + 32 * j;
+            kb[j] = slot < tsl ? __ldg(&kt[slot]) : 0ull;
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (kb[j] != 0 && (kb[j] & hi_mask) == prefix) atomicAdd(&hist[(kb[j] >> shift) & (nbins - 1)], 1u);
         }
       }
     }
@@ -298,7 +306,7 @@ __global__ void __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
         it.tile(ti, &tx, &ty);
         const unsigned long long* kt = kd + it.coef_index(tx, ty, 0);
         for (int slot = lane; slot < tsl; slot += 32) {
-          const unsigned long long kb = kt[slot];
+          const unsigned long long kb = __ldg(&kt[slot]);
           if (kb != 0 && (kb & hi_mask) == prefix) {
             const int i = atomicAdd(&s_nc, 1);
             if (i < kCandCap) {
