@@ -357,6 +357,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   sc.take<double>((size_t)n_depths);
   sc.take<double>((size_t)n_depths);
   sc.take<double>((size_t)n_depths);
+  sc.take<int>((size_t)n_depths + 1);
   sc.take<long long>((size_t)n_depths);
   void* scratch = nullptr;
   e = cudaMallocAsync(&scratch, align_up(sc.off, 256), s);
@@ -380,6 +381,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   double* z_dev = sc.take<double>((size_t)n_depths);
   double* R2_dev = sc.take<double>((size_t)n_depths);
   double* c_dev = sc.take<double>((size_t)n_depths);
+  int* blk0_dev = sc.take<int>((size_t)n_depths + 1);
   long long* target_dev = sc.take<long long>((size_t)n_depths);
   a.z_dev = z_dev; a.R2_dev = R2_dev; a.target_dev = target_dev; a.c_dev = c_dev;
   // Phase constants of reading R8 (plain IEEE double operations).
@@ -390,6 +392,20 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
     const double zl = depths_host[d] / lambda;
     cz[d] = zl * zl;
   }
+  // PSF blocks: each depth's box tiles, psf_tiles_per_block(L) to a block.
+  std::vector<int> blk0(n_depths + 1, 0);
+  {
+    const int tpb = psf_tiles_per_block(levels);
+    long long acc = 0;
+    for (int d = 0; d < n_depths; ++d) {
+      blk0[d] = (int)acc;
+      const long long nbd = lut->meta[d].thi - lut->meta[d].tlo + 1;
+      acc += (nbd * nbd + tpb - 1) / tpb;
+    }
+    blk0[n_depths] = (int)acc;
+  }
+  a.psf_blk0 = blk0_dev;
+  a.psf_blocks = blk0[n_depths];
   a.nr_dev = lut->nr_dev; a.pos = lut->pos; a.val = lut->val; a.val16 = lut->val16; a.scale = lut->scale;
   a.tile_off = lut->tile_off; a.meta = lut->meta_dev; a.cmax = lut->cmax; a.levels = lut->levels;
   a.code = lut->code; a.ncode = lut->ncode; a.total = base;
@@ -400,6 +416,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   okc = okc && cudaMemcpyAsync(z_dev, depths_host, sizeof(double) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
   okc = okc && cudaMemcpyAsync(R2_dev, R2.data(), sizeof(double) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
   okc = okc && cudaMemcpyAsync(c_dev, cz.data(), sizeof(double) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  okc = okc && cudaMemcpyAsync(blk0_dev, blk0.data(), sizeof(int) * (n_depths + 1), cudaMemcpyHostToDevice, s) == cudaSuccess;
   okc = okc && cudaMemcpyAsync(target_dev, target.data(), sizeof(long long) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
   okc = okc && cudaMemcpyAsync(lut->meta_dev, lut->meta.data(), sizeof(DepthMeta) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
   okc = okc && cudaMemsetAsync(a.nnz, 0, sizeof(unsigned long long) * n_depths, s) == cudaSuccess;

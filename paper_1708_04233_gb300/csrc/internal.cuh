@@ -125,6 +125,8 @@ struct LutBuildArgs {
   double lambda, pitch;
   const double* z_dev;      // D depths
   const double* c_dev;      // D values (z / lambda)^2
+  const int* psf_blk0;      // D + 1: first PSF block of each depth (prefix over depths)
+  int psf_blocks;           // PSF blocks over all depths
   double q;                 // (pitch / lambda)^2
   const double* R2_dev;     // D squared radii (pixels^2)
   const long long* target_dev;  // D budgets (LLONG_MAX = keep all nonzero)
@@ -149,6 +151,11 @@ struct LutBuildArgs {
   int* status;
 };
 cudaError_t launch_lut_build(const LutBuildArgs& a, cudaStream_t s);
+// Window tiles one PSF block transforms (1,024 threads, one per pixel).
+inline int psf_tiles_per_block(int L) {
+  const int tsl = 1 << (2 * L);
+  return tsl >= 1024 ? 1 : 1024 / tsl;
+}
 
 // Points.
 cudaError_t launch_quantize(const int32_t* x, const int32_t* y, const double* z, const float* a,

@@ -89,21 +89,27 @@ struct BoxIter {
 };
 
 template <int L>
-__global__ void __launch_bounds__((1 << (2 * L)) >= 256 ? (1 << (2 * L)) : 256)
-psf_haar_kernel(LutBuildArgs a) {
+__global__ void __launch_bounds__(1024) psf_haar_kernel(LutBuildArgs a) {
   constexpr int TS = 1 << L;
   constexpr int TSL = TS * TS;
-  constexpr int NT = TSL >= 256 ? TSL : 256;
+  constexpr int NT = TSL >= 1024 ? TSL : 1024;
   constexpr int TPB = NT / TSL;
   __shared__ float2 sa[TPB][TSL];
   __shared__ float2 sb[TPB][TSL];
   __shared__ float2 co[TPB][TSL];
   __shared__ unsigned int nz;
-  const int d = blockIdx.y;
+  // Blocks cover the depths' box tiles back to back (no idle blocks): the
+  // block's depth by binary search over the per-depth first blocks.
+  int dlo = 0, dhi = a.D - 1;
+  while (dlo < dhi) {
+    const int mid = (dlo + dhi + 1) >> 1;
+    if (__ldg(&a.psf_blk0[mid]) <= (int)blockIdx.x) dlo = mid; else dhi = mid - 1;
+  }
+  const int d = dlo;
   const DepthMeta md = a.meta[d];
   const int nb = md.thi - md.tlo + 1;
   const int tl = threadIdx.x / TSL, pix = threadIdx.x % TSL;
-  const int bt = blockIdx.x * TPB + tl;  // tile index inside the box
+  const int bt = ((int)blockIdx.x - __ldg(&a.psf_blk0[d])) * TPB + tl;  // tile index inside the box
   const bool valid = bt < nb * nb;
   const int tx = md.tlo + (valid ? bt % nb : 0), ty = md.tlo + (valid ? bt / nb : 0);
   if (threadIdx.x == 0) nz = 0;
@@ -522,11 +528,11 @@ __global__ void plane_code_kernel(LutBuildArgs a) {
 
 template <int L>
 cudaError_t launch_psf_haar(const LutBuildArgs& a, int max_nb, cudaStream_t s) {
+  (void)max_nb;
   constexpr int TSL = 1 << (2 * L);
-  constexpr int NT = TSL >= 256 ? TSL : 256;
-  constexpr int TPB = NT / TSL;
-  const dim3 grid((unsigned)((max_nb * max_nb + TPB - 1) / TPB), (unsigned)a.D);
-  psf_haar_kernel<L><<<grid, NT, 0, s>>>(a);
+  constexpr int NT = TSL >= 1024 ? TSL : 1024;
+  if (a.psf_blocks <= 0) return cudaSuccess;
+  psf_haar_kernel<L><<<(unsigned)a.psf_blocks, NT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
