@@ -343,7 +343,7 @@ def run_gpu(args, c):
 
     ev = {k: [] for k in (("lut", "hologram") if fused else ("lut", "superpose", "inverse"))}
 
-    def step(record=False, xs=x, ys=y, zs=z, as_=a, two_pass=not fused, wb=None):
+    def step(record=False, xs=x, ys=y, zs=z, as_=a, two_pass=not fused, wb=None, out=None):
         with torch.cuda.stream(stream):
             marks = []
 
@@ -358,14 +358,16 @@ def run_gpu(args, c):
             mark()
             if step.scratch is None:
                 step.scratch = torch.empty(w.scratch_bytes(lut, N, c.Nh, c.Nh), dtype=torch.uint8, device=dev)
+            o_u = ufield if out is None or want != "complex" else out
+            o_b = bits if out is None or want != "bits" else out
             if two_pass:
                 w.superpose(lut, pbuf, c.Nh, c.Nh, rule=0, wbuf=wb if wb is not None else wbuf,
                             scratch=step.scratch, stream=stream)
                 mark()
-                w.inverse_haar(wb if wb is not None else wbuf, c.Nh, c.Nh, c.L, u=ufield, bits=bits, want=want,
+                w.inverse_haar(wb if wb is not None else wbuf, c.Nh, c.Nh, c.L, u=o_u, bits=o_b, want=want,
                                stream=stream)
             else:
-                w.hologram(lut, pbuf, c.Nh, c.Nh, want=want, rule=0, u=ufield, bits=bits, scratch=step.scratch,
+                w.hologram(lut, pbuf, c.Nh, c.Nh, want=want, rule=0, u=o_u, bits=o_b, scratch=step.scratch,
                            stream=stream)
             mark()
             if record:
@@ -410,30 +412,54 @@ def run_gpu(args, c):
     ms = max_over_ranks(ms, dev)
     stage_ms = {k: float(np.mean([s.elapsed_time(e) for s, e in v])) for k, v in ev.items()}
 
-    # End to end through the public API with pinned host buffers.
+    # End to end through the public API with pinned host buffers: every step
+    # uploads its points and downloads its result.  The copies run on their
+    # own streams with two buffer sets, so step k's download overlaps step
+    # k+1's computation (as a user pipelining the calls would).
     hx = torch.from_numpy(pts["x"]).pin_memory()
     hy = torch.from_numpy(pts["y"]).pin_memory()
     hz = torch.from_numpy(pts["z"]).pin_memory()
     ha = torch.from_numpy(pts["a"]).pin_memory()
-    hout = torch.empty(out_dev.shape, dtype=out_dev.dtype).pin_memory()
-    dx, dy, dz, da = (torch.empty_like(t) for t in (x, y, z, a))
+    hout = [torch.empty(out_dev.shape, dtype=out_dev.dtype).pin_memory() for _ in range(2)]
+    din = [[torch.empty_like(t) for t in (x, y, z, a)] for _ in range(2)]
+    dout = [out_dev, torch.empty_like(out_dev)]
+    up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    done_down = [None, None]
+    computed_ev = [None, None]
 
-    def e2e_step():
-        with torch.cuda.stream(stream):
-            for d_, h_ in ((dx, hx), (dy, hy), (dz, hz), (da, ha)):
+    def e2e_step(k):
+        j = k % 2
+        uploaded = torch.cuda.Event()
+        if computed_ev[j] is not None:
+            up.wait_event(computed_ev[j])  # step k-2 has finished reading din[j]
+        with torch.cuda.stream(up):
+            for d_, h_ in zip(din[j], (hx, hy, hz, ha)):
                 d_.copy_(h_, non_blocking=True)
-            step(xs=dx, ys=dy, zs=dz, as_=da)
-            hout.copy_(out_dev, non_blocking=True)
-    e2e_step()
+            uploaded.record(up)
+        stream.wait_event(uploaded)
+        if done_down[j] is not None:
+            stream.wait_event(done_down[j])  # the download of step k-2 has read dout[j]
+        step(xs=din[j][0], ys=din[j][1], zs=din[j][2], as_=din[j][3], out=dout[j])
+        computed = torch.cuda.Event()
+        computed.record(stream)
+        down.wait_event(computed)
+        with torch.cuda.stream(down):
+            hout[j].copy_(dout[j], non_blocking=True)
+            done_down[j] = torch.cuda.Event()
+            done_down[j].record(down)
+        computed_ev[j] = computed
+    for k in range(2):
+        e2e_step(k)
     barrier()
     te = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
+    for k in range(args.steps):
+        e2e_step(k)
     barrier()
     e2e_ms = (time.perf_counter() - te) * 1e3 / args.steps
     e2e_ms = max_over_ranks(e2e_ms, dev)
     h2d = sum(t.numel() * t.element_size() for t in (hx, hy, hz, ha))
-    d2h = hout.numel() * hout.element_size()
+    d2h = hout[0].numel() * hout[0].element_size()
+    assert torch.equal(hout[(args.steps - 1) % 2].to(dev), out_dev), "end-to-end result differs"
 
     # The two-pass form (superposition into the 34 GB wavelet buffer, then the
     # separate inverse kernel): the inverse kernel's HBM fraction.

@@ -89,6 +89,50 @@ double support_radius(double lambda, double pitch, double z) {
   return (z * t) / pitch;
 }
 
+// Pinned staging for the small per-depth tables a LUT build uploads: one
+// buffer per device, reused by later builds once the previous upload has
+// completed.  Uploads from pinned memory do not wait for other work on the
+// device, as copies from pageable memory can.
+struct Staging {
+  std::mutex mu;
+  char* host = nullptr;
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;
+};
+Staging g_staging[kMaxDev];
+
+struct Upload {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
+
+cudaError_t staged_upload(int dev, cudaStream_t s, const Upload* ups, int n) {
+  Staging& st = g_staging[dev];
+  std::lock_guard<std::mutex> lk(st.mu);
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) total += align_up(ups[i].bytes, 16);
+  cudaError_t e = cudaSuccess;
+  if (st.done) e = cudaEventSynchronize(st.done);  // the previous build's upload has left the buffer
+  if (e == cudaSuccess && st.cap < total) {
+    if (st.host) cudaFreeHost(st.host);
+    st.host = nullptr;
+    st.cap = 0;
+    const size_t want = std::max<size_t>(total, 64 * 1024);
+    e = cudaMallocHost(&st.host, want);
+    if (e == cudaSuccess) st.cap = want;
+  }
+  if (e == cudaSuccess && !st.done) e = cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming);
+  size_t off = 0;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    std::memcpy(st.host + off, ups[i].src, ups[i].bytes);
+    e = cudaMemcpyAsync(ups[i].dst, st.host + off, ups[i].bytes, cudaMemcpyHostToDevice, s);
+    off += align_up(ups[i].bytes, 16);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(st.done, s);
+  return e;
+}
+
 int env_int(const char* name, int dflt) {
   const char* v = std::getenv(name);
   return v && *v ? std::atoi(v) : dflt;
@@ -412,19 +456,18 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   for (int i = 0; i < kMaxCodes; ++i) a.code_k[i] = lut->code_k[i];
   a.status = status;
 
-  bool okc = true;
-  okc = okc && cudaMemcpyAsync(z_dev, depths_host, sizeof(double) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
-  okc = okc && cudaMemcpyAsync(R2_dev, R2.data(), sizeof(double) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
-  okc = okc && cudaMemcpyAsync(c_dev, cz.data(), sizeof(double) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
-  okc = okc && cudaMemcpyAsync(blk0_dev, blk0.data(), sizeof(int) * (n_depths + 1), cudaMemcpyHostToDevice, s) == cudaSuccess;
-  okc = okc && cudaMemcpyAsync(target_dev, target.data(), sizeof(long long) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
-  okc = okc && cudaMemcpyAsync(lut->meta_dev, lut->meta.data(), sizeof(DepthMeta) * n_depths, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  const Upload ups[] = {
+      {z_dev, depths_host, sizeof(double) * n_depths},
+      {R2_dev, R2.data(), sizeof(double) * n_depths},
+      {c_dev, cz.data(), sizeof(double) * n_depths},
+      {blk0_dev, blk0.data(), sizeof(int) * (n_depths + 1)},
+      {target_dev, target.data(), sizeof(long long) * n_depths},
+      {lut->meta_dev, lut->meta.data(), sizeof(DepthMeta) * n_depths},
+  };
+  bool okc = staged_upload(lut->device, s, ups, (int)(sizeof ups / sizeof ups[0])) == cudaSuccess;
   okc = okc && cudaMemsetAsync(a.nnz, 0, sizeof(unsigned long long) * n_depths, s) == cudaSuccess;
   okc = okc && cudaMemsetAsync(lut->cmax, 0, sizeof(float), s) == cudaSuccess;
   okc = okc && cudaMemsetAsync(lut->levels, 0, sizeof(unsigned), s) == cudaSuccess;
-  // The per-depth tables come from pageable host memory; make their upload
-  // complete before the host vectors are released.
-  okc = okc && cudaStreamSynchronize(s) == cudaSuccess;
   if (!okc) {
     cudaFreeAsync(scratch, s);
     cudaFreeAsync(lut->block, s);
