@@ -505,7 +505,8 @@ def run_gpu(args, c):
             "bound": "alu", "achieved": ach, "peak": smem_peak, "unit": "Gop/s", "frac": ach / smem_peak,
             "peak_source": "derived: 32 banks x 152 SMs x 2070 MHz (shared-memory 32-bit ops)",
             "algorithmic_ops": parts * units, "ops_per_point_coeff": parts, "traffic": _traffic(c, args.path)}
-    lut_kernels = 6 + (0 if c.lut_dtype in ("f32", 0) else 1)  # psf, select, tile count/scan, scatter, codes
+    # psf, select, tile count/scan, scatter, codes, level-mask readback (+ encode for FP16/BF16)
+    lut_kernels = 7 + (0 if c.lut_dtype in ("f32", 0) else 1)
     per_step = lut_kernels + 1 + 6 + (0 if fused else 1)
 
     if rank == 0:

@@ -133,6 +133,31 @@ cudaError_t staged_upload(int dev, cudaStream_t s, const Upload* ups, int n) {
   return e;
 }
 
+// A pinned host word per device that a one-thread kernel writes: small
+// results come back without a device-to-host copy, so they never queue
+// behind a large copy in flight on another stream.
+struct HostWord {
+  std::mutex mu;
+  unsigned* word = nullptr;
+};
+HostWord g_hostword[kMaxDev];
+
+__global__ void word_to_host_kernel(const unsigned* src, unsigned* dst) { *(volatile unsigned*)dst = *src; }
+
+// Reads *src_dev after the work already on s; synchronises s.
+cudaError_t read_word(int dev, const unsigned* src_dev, cudaStream_t s, unsigned* out) {
+  HostWord& hw = g_hostword[dev];
+  std::lock_guard<std::mutex> lk(hw.mu);
+  cudaError_t e = cudaSuccess;
+  if (!hw.word) e = cudaMallocHost(&hw.word, sizeof(unsigned));
+  if (e != cudaSuccess) return e;
+  word_to_host_kernel<<<1, 1, 0, s>>>(src_dev, hw.word);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) *out = *(volatile unsigned*)hw.word;
+  return e;
+}
+
 int env_int(const char* name, int dflt) {
   const char* v = std::getenv(name);
   return v && *v ? std::atoi(v) : dflt;
@@ -484,8 +509,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   // The finest kept level sizes the superposition's accumulator: wait for the
   // build and read it back.
   unsigned lvmask = 0;
-  e = cudaMemcpyAsync(&lvmask, lut->levels, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  e = read_word(lut->device, lut->levels, s, &lvmask);
   if (e != cudaSuccess) {
     cudaFreeAsync(lut->block, s);
     delete lut;
