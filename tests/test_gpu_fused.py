@@ -88,3 +88,24 @@ def test_fused_empty_and_invalid(w, orc):
         _abi.check(_abi.load().wasabi_hologram(lut.handle, p.data_ptr(), 10, 64, 64, 0, None, None, None,
                                                scratch.data_ptr(), scratch.numel(), None))
     lut.close()
+
+
+def test_points_outside_the_hologram(w, orc):
+    """Points up to 100 pixels outside the hologram still contribute the part
+    of their footprint that lands inside it (Eq. (2) drops only the
+    coefficients that land outside)."""
+    D = 6
+    zd = w.depth_grid(ZMIN, ZMAX, D)
+    lut = w.build_lut(LAM, PITCH, zd, 128, 4, 0.2)
+    olut = orc.build_lut(LAM, PITCH, zd, 128, 4, 0.2)
+    g = np.random.default_rng(5)
+    n = 400
+    pts = {"x": g.integers(-100, 356, n).astype(np.int32), "y": g.integers(-100, 356, n).astype(np.int32),
+           "a": (1.0 - g.random(n)).astype(np.float32), "z": g.uniform(ZMIN, ZMAX, n)}
+    pts["d"], _ = orc.quantize(pts["z"], ZMIN, ZMAX, D)
+    p = w.pack_points(pts["x"], pts["y"], pts["a"], pts["d"])
+    for rule in (0, 1):
+        u = w.hologram(lut, p, 256, 256, rule=rule).cpu().numpy()
+        assert rel_l2(u, orc.hologram(olut, pts, 256, rule=rule)) <= 1e-5
+    w.sync_status()
+    lut.close()
