@@ -99,14 +99,19 @@ wasabi_status wasabi_quantize_points(const int32_t* x_dev, const int32_t* y_dev,
 /* A1-A3, the look-up table (Sec. 1, step 1): for each depth z_d
  * (depths_host[0..n_depths)), the PSF u_z = exp(i 2 pi r / lambda) on the
  * W x W window centred at pixel (W/2, W/2) with r = sqrt(n pitch^2 + z^2),
- * n = du^2 + dv^2, restricted to the disk n < R(z)^2; its L-level Haar
- * transform; and the N_r strongest coefficients by re^2 + im^2 (FP64), equal
- * strengths going to the lower Mallat index row * W + col.
- * N_r = min(nnz, ceil(keep_ratio * pi * R^2 - 1e-9)) for keep_ratio < 1, and
- * every nonzero coefficient for keep_ratio >= 1 (Sec. 1, step 1:
- * N_r = pi (W_j/2)^2 gamma with W_j the PSF diameter 2R).
- * Phase arithmetic (so CPU and GPU select identical sets): f = t - floor(t),
- * t = r / lambda, in FP64; cos/sin of 2 pi (float) f by quadrant reduction and
+ * n = du^2 + dv^2, restricted to the disk n < R(|z|)^2 and the centre pixel;
+ * its L-level Haar transform; and the N_r strongest coefficients by
+ * re^2 + im^2 (FP64), equal strengths going to the lower Mallat index
+ * row * W + col.  Depths may lie on both sides of the hologram plane (an
+ * image-type hologram): a depth z < 0 has the conjugate PSF (the wave
+ * converging on a point behind the plane), and z = 0 is a single-pixel delta.
+ * N_r = min(nnz, ceil(keep_ratio * pi * R^2 - 1e-9)) for keep_ratio < 1 and
+ * R > 1, and every nonzero coefficient for keep_ratio >= 1 or R <= 1 (Sec. 1,
+ * step 1: N_r = pi (W_j/2)^2 gamma with W_j the PSF diameter 2R).
+ * Phase arithmetic (so CPU and GPU select identical sets): t = r / lambda =
+ * sqrt(s), s = n (pitch/lambda)^2 + (z/lambda)^2 in FP64, as the FP32 square
+ * root t0 of s plus one FP64 Newton step t0 + (s - t0^2) / (2 t0);
+ * f = t - floor(t); cos/sin of 2 pi (float) f by quadrant reduction and
  * Taylor polynomials in FP32 with fused multiply-adds.
  * Requires 1 <= levels <= 5 (2 <= levels for the inverse), window a multiple
  * of 2^(levels+1) with window / 2^levels <= 512, 2 R(z_d) + 1 <= window for
@@ -317,9 +322,10 @@ wasabi_status wasabi_server_destroy(wasabi_server* server);
 /* Eq. (1), the direct sum, on the GPU:
  *   u(x_h, y_h) = sum_j a_j exp(i 2 pi r_hj / lambda) [aperture],
  * r_hj = sqrt(((x_h - x_j)^2 + (y_h - y_j)^2) pitch^2 + z_{d_j}^2), with the
- * point's quantised depth z_{d_j} = depths_host[d_j]; aperture = 1 restricts
- * each term to the PSF disk n < R(z)^2 (the second form of Eq. (1)), 0 sums
- * every pixel.  u_dev: holo_w x holo_h complex64, row-major, overwritten.
+ * point's quantised depth z_{d_j} = depths_host[d_j] (a point behind the plane,
+ * z < 0, contributes the conjugate term); aperture = 1 restricts each term to
+ * the PSF disk n < R(|z|)^2 and the point's own pixel (the second form of
+ * Eq. (1)), 0 sums every pixel.  u_dev: holo_w x holo_h complex64, row-major, overwritten.
  * FP64 is used for the phase reduction r / lambda mod 1, FP32 elsewhere.
  * scratch_dev: at least cgh_direct_scratch_bytes() bytes. */
 wasabi_status cgh_direct_scratch_bytes(int64_t n, int holo_w, int holo_h, size_t* bytes_out);

@@ -110,7 +110,8 @@ def support_radius(lam: float, pitch: float, z) -> np.ndarray | float:
 
 
 def keep_target(gamma: float, R: float) -> int:
-    """Reading R3: coefficient budget ceil(gamma * pi * R^2 - 1e-9)."""
+    """Reading R3: coefficient budget ceil(gamma * pi * R^2 - 1e-9); R11: no
+    limit (every nonzero kept) when R <= 1, the single-pixel support."""
     return int(lib().orc_keep_target(gamma, R))
 
 
@@ -235,7 +236,7 @@ def build_lut(lam, pitch, depths, W, L, gamma, dtype="f32", threads=1,
     if gamma >= 1.0:
         cap = D * W * W
     else:
-        cap = sum(keep_target(gamma, support_radius(lam, pitch, z)) for z in depths)
+        cap = sum(min(keep_target(gamma, support_radius(lam, pitch, z)), W * W) for z in depths)
     nr = np.zeros(D, np.int64)
     idx = np.empty(max(cap, 1), np.int32)
     if dtype == "f32":

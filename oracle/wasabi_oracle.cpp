@@ -66,11 +66,20 @@ constexpr double kPi = 3.14159265358979323846264338327950288;
 double support_radius_px(double lambda, double pitch, double z) {
   const double s = lambda / (2.0 * pitch);
   const double t = s / std::sqrt(1.0 - s * s);  // tan(asin(s))
-  return (z * t) / pitch;
+  return (std::fabs(z) * t) / pitch;
 }
+
+// R11 (image-type holograms, points on both sides of the hologram plane): the
+// support is the open disk n < R(|z|)^2 plus the centre pixel (a point on
+// the plane is a single pixel), and a point behind the plane (z < 0) has the
+// conjugate PSF -- the wave converging on it.
+bool in_support(int64_t n, double R2) { return n == 0 || (double)n < R2; }
 
 // R3: coefficient budget for gamma < 1 (Sec. 1, step 1).
 int64_t keep_target(double gamma, double R) {
+  // R11: a support of the centre pixel alone (R <= 1) is a delta; all of its
+  // (at most 3L + 1) nonzero coefficients are kept.
+  if (R <= 1.0) return INT64_MAX;
   const double area = kPi * (R * R);
   return (int64_t)std::ceil(gamma * area - 1e-9);
 }
@@ -142,6 +151,7 @@ double phase_frac_newton(int64_t n, double q, double c) {
   const float t0f = std::sqrt((float)s);
   const double t0 = (double)t0f;
   const double res = std::fma(-t0, t0, s);
+  if (t0f == 0.0f) return 0.0;  // s = 0: a point on the plane, at its own pixel
   const float inv = 1.0f / (2.0f * t0f);
   const double t = t0 + res * (double)inv;
   return t - std::floor(t);
@@ -155,16 +165,17 @@ double phase_frac_newton(int64_t n, double q, double c) {
 void psf_f32(double lambda, double pitch, double z, int W, float* out) {
   const double R = support_radius_px(lambda, pitch, z);
   const double R2 = R * R;
-  const double pl = pitch / lambda, zl = z / lambda;
+  const double pl = pitch / lambda, zl = std::fabs(z) / lambda;
   const double q = pl * pl, cz = zl * zl;
   for (int v = 0; v < W; ++v) {
     for (int u = 0; u < W; ++u) {
       const int64_t du = u - W / 2, dv = v - W / 2;
       const int64_t n = du * du + dv * dv;
       float c = 0.0f, s = 0.0f;
-      if ((double)n < R2) {
+      if (in_support(n, R2)) {
         const float g = (float)phase_frac_newton(n, q, cz);
         sincos2pi_f32(g, &c, &s);
+        if (z < 0) s = -s;  // R11
       }
       out[2 * ((int64_t)v * W + u) + 0] = c;
       out[2 * ((int64_t)v * W + u) + 1] = s;
@@ -183,10 +194,10 @@ void psf_f64(double lambda, double pitch, double z, int W, double* out) {
       const int64_t du = u - W / 2, dv = v - W / 2;
       const int64_t n = du * du + dv * dv;
       double c = 0.0, s = 0.0;
-      if ((double)n < R2) {
+      if (in_support(n, R2)) {
         const double f = phase_frac(n, p2, z2, lambda);
         c = std::cos(2.0 * kPi * f);
-        s = std::sin(2.0 * kPi * f);
+        s = (z < 0 ? -1.0 : 1.0) * std::sin(2.0 * kPi * f);  // R11
       }
       out[2 * ((int64_t)v * W + u) + 0] = c;
       out[2 * ((int64_t)v * W + u) + 1] = s;
@@ -459,10 +470,10 @@ void cgh_direct(double lambda, double pitch, const int32_t* x, const int32_t* y,
       for (int64_t j = 0; j < N; ++j) {
         const int64_t dx = ox + xx - x[j], dy = oy + yy - y[j];
         const int64_t n = dx * dx + dy * dy;
-        if (aperture && !((double)n < R2[(size_t)j])) continue;
+        if (aperture && !in_support(n, R2[(size_t)j])) continue;
         const double f = phase_frac(n, p2, z[j] * z[j], lambda);
         re += (double)a[j] * std::cos(2.0 * kPi * f);
-        im += (double)a[j] * std::sin(2.0 * kPi * f);
+        im += (double)a[j] * (z[j] < 0 ? -1.0 : 1.0) * std::sin(2.0 * kPi * f);  // R11
       }
       u[2 * (yy * w + xx) + 0] = re;
       u[2 * (yy * w + xx) + 1] = im;

@@ -86,7 +86,7 @@ namespace {
 double support_radius(double lambda, double pitch, double z) {
   const double s = lambda / (2.0 * pitch);
   const double t = s / std::sqrt(1.0 - s * s);
-  return (z * t) / pitch;
+  return (std::fabs(z) * t) / pitch;
 }
 
 // Pinned staging for the small per-depth tables a LUT build uploads: one
@@ -341,7 +341,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   long long max_cap = 0, base = 0;
   for (int d = 0; d < n_depths; ++d) {
     const double z = depths_host[d];
-    if (!(z > 0)) { delete lut; set_error("build_lut: depth %d must be > 0", d); return WASABI_E_INVALID; }
+    if (!std::isfinite(z)) { delete lut; set_error("build_lut: depth %d is not finite", d); return WASABI_E_INVALID; }
     const double R = support_radius(lambda, pitch, z);
     if (2.0 * R + 1.0 > (double)window) {
       delete lut;
@@ -360,7 +360,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
     max_nb = std::max(max_nb, nb);
     const long long box = (long long)nb * nb * TSL;
     long long cap = box;
-    if (keep_ratio < 1.0) {
+    if (keep_ratio < 1.0 && R > 1.0) {  // R <= 1: a delta, all its coefficients kept
       target[d] = (long long)std::ceil(keep_ratio * (kPi * (R * R)) - 1e-9);
       cap = std::min(cap, std::max(0ll, target[d]));
     } else {
@@ -458,7 +458,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   a.q = pl * pl;
   std::vector<double> cz(n_depths);
   for (int d = 0; d < n_depths; ++d) {
-    const double zl = depths_host[d] / lambda;
+    const double zl = std::fabs(depths_host[d]) / lambda;
     cz[d] = zl * zl;
   }
   // PSF blocks: each depth's box tiles, psf_tiles_per_block(L) to a block.
@@ -812,12 +812,14 @@ wasabi_status cgh_direct(double lambda, double pitch, const double* depths_host,
   double Rmax = 0;
   for (int d = 0; d < n_depths; ++d) {
     const double z = depths_host[d];
-    if (!(z > 0)) { set_error("cgh_direct: depth %d must be > 0", d); return WASABI_E_INVALID; }
-    const double zl = z / lambda;
-    beta[d] = zl * zl;
+    if (!std::isfinite(z)) { set_error("cgh_direct: depth %d is not finite", d); return WASABI_E_INVALID; }
+    const double zl = std::fabs(z) / lambda;
+    // (z / lambda)^2, negated for a point behind the plane (conjugate term).
+    beta[d] = z < 0 ? -(zl * zl) : zl * zl;
     const double R = support_radius(lambda, pitch, z);
     Rmax = std::max(Rmax, R);
-    nlim[d] = aperture ? (long long)std::ceil(R * R) : LLONG_MAX;
+    // n < R^2 for integer n, or the centre pixel alone.
+    nlim[d] = aperture ? std::max(1ll, (long long)std::ceil(R * R)) : LLONG_MAX;
   }
   const double pl = pitch / lambda;
   const cudaStream_t s = (cudaStream_t)stream;

@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(kNT) direct_kernel(DirectArgs a) {
       const int px = X0 + col;
       for (int s = 0; s < n; ++s) {
         const int4 p = list[s];
-        const double beta = lbeta[s];
+        const double beta = fabs(lbeta[s]);
+        const float sgn = lbeta[s] < 0.0 ? -1.0f : 1.0f;  // conjugate term for a point behind the plane
         const long long nlim = lnlim[s];
         const float amp = __int_as_float(p.z);
         const long long dx = px - p.x;
@@ -110,11 +111,11 @@ __global__ void __launch_bounds__(kNT) direct_kernel(DirectArgs a) {
             const float s0 = qf * r0;
             const double e = __fma_rn(-(double)s0, (double)s0, qd);
             const float corr = __double2float_rn(e) * (0.5f * r0);
-            const float f = (s0 - floorf(s0)) + corr;
+            const float f = qf > 0.f ? (s0 - floorf(s0)) + corr : 0.f;  // q = 0: a point on the plane
             float sn, cs;
             sincospif(2.0f * f, &sn, &cs);
             re[q] = fmaf(amp, cs, re[q]);
-            im[q] = fmaf(amp, sn, im[q]);
+            im[q] = fmaf(amp, sgn * sn, im[q]);
           }
         }
       }

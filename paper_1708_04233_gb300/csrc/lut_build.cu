@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(1024) psf_haar_kernel(LutBuildArgs a) {
     const long long du = (long long)(tx * TS + pu) - a.W / 2;
     const long long dv = (long long)(ty * TS + pv) - a.W / 2;
     const long long n = du * du + dv * dv;
-    if ((double)n < a.R2_dev[d]) {
+    if (n == 0 || (double)n < a.R2_dev[d]) {  // the open disk and the centre pixel
       // r / lambda = sqrt(s), s = n (p/lambda)^2 + (z/lambda)^2: FP32 square
       // root plus one FP64 Newton step (residual by a fused multiply-add).
       const double s = __fma_rn((double)n, a.q, a.c_dev[d]);
@@ -129,9 +129,11 @@ __global__ void __launch_bounds__(1024) psf_haar_kernel(LutBuildArgs a) {
       const double t0 = (double)t0f;
       const double res = __fma_rn(-t0, t0, s);
       const float inv = __frcp_rn(2.0f * t0f);
-      const double t = __dadd_rn(t0, __dmul_rn(res, (double)inv));
+      // s = 0 (a point on the plane, at its own pixel): t = 0.
+      const double t = t0f > 0.0f ? __dadd_rn(t0, __dmul_rn(res, (double)inv)) : 0.0;
       const double f = __dsub_rn(t, floor(t));
       sincos2pi(__double2float_rn(f), &val.x, &val.y);
+      if (a.z_dev[d] < 0.0) val.y = -val.y;  // behind the plane: the conjugate PSF
     }
   }
   sa[tl][pix] = val;

@@ -38,8 +38,8 @@ def test_tie_goes_to_lower_index(orc):
     c[5, 2] = 3 + 0j
     c[1, 6] = 3j          # same magnitude as c[5,2], lower index
     c[0, 1] = 1
-    R = 1.0 / np.sqrt(np.pi)        # gamma * pi * R^2 = gamma
-    got = orc.select(c, 1.0 - 1e-12, R)  # budget 1
+    R = 2.0                         # gamma * pi * R^2 = 1: budget 1
+    got = orc.select(c, 1.0 / (4.0 * np.pi), R)
     assert list(got) == [1 * W + 6]
 
 

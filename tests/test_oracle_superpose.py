@@ -197,3 +197,62 @@ def test_binarize_bit_order(orc):
     bits = orc.binarize(u)
     # x = 0, 3, 5, 6 set in byte 0; x = 8 and 15 in byte 1.
     assert list(bits) == [0b01101001, 0b10000001]
+
+
+# ---- R11: image-type holograms (points on both sides of the plane) --------
+
+def test_lut_behind_the_plane_is_the_conjugate(orc):
+    """A depth -z keeps the same coefficients as +z with conjugate values
+    (the PSF of a point behind the plane converges on it), FP32 and FP64."""
+    zd = np.array([-70e-6, -33e-6, 33e-6, 70e-6])
+    for dtype in ("f32", "f64"):
+        lut = orc.build_lut(LAM, PITCH, zd, W, L, 0.3, dtype=dtype)
+        for dn, dp in ((0, 3), (1, 2)):
+            i_n, v_n = lut.depth(dn)
+            i_p, v_p = lut.depth(dp)
+            assert np.array_equal(i_n, i_p)
+            assert np.array_equal(v_n, np.conj(v_p))
+
+
+def test_hologram_behind_the_plane_is_the_conjugate(orc):
+    pts = uniform_cloud(3, 30, NH, ZMIN, ZMAX)
+    zp = orc.depth_grid(ZMIN, ZMAX, D)
+    zd = np.concatenate([-zp[::-1], zp])  # depth D - 1 - d is exactly -(depth D + d)
+    d, _ = orc.quantize(pts["z"], ZMIN, ZMAX, D)
+    d_pos, d_neg = (D + d).astype(np.uint32), (D - 1 - d).astype(np.uint32)
+    assert np.array_equal(zd[d_neg], -zd[d_pos])
+    for dtype in ("f32", "f64"):
+        lut = orc.build_lut(LAM, PITCH, zd, W, L, 0.4, dtype=dtype)
+        up = orc.hologram(lut, dict(pts, d=d_pos), NH)
+        un = orc.hologram(lut, dict(pts, d=d_neg), NH)
+        assert np.array_equal(un, np.conj(up))
+    ep = orc.cgh_direct(LAM, PITCH, pts["x"], pts["y"], pts["a"], zd[d_pos], 0, 0, NH, NH, True)
+    en = orc.cgh_direct(LAM, PITCH, pts["x"], pts["y"], pts["a"], zd[d_neg], 0, 0, NH, NH, True)
+    assert np.array_equal(en, np.conj(ep))
+
+
+def test_point_on_the_plane_is_a_delta(orc):
+    """z = 0: the support is the centre pixel, every coefficient of the delta
+    is kept, and on the 2^L grid the hologram is a_j at (x_j, y_j) exactly
+    (Eq. (1) gives the same)."""
+    g = np.random.default_rng(4)
+    n = 20
+    pts = {"x": (g.integers(0, NH // 8, n) * 8).astype(np.int32), "y": (g.integers(0, NH // 8, n) * 8).astype(np.int32),
+           "a": (1.0 - g.random(n)).astype(np.float32), "d": np.zeros(n, np.uint32)}
+    lut = orc.build_lut(LAM, PITCH, np.array([0.0]), W, L, 0.01, dtype="f64")
+    assert lut.nr[0] == 3 * L + 1
+    u = orc.hologram(lut, pts, NH)
+    want = np.zeros((NH, NH), np.complex128)
+    np.add.at(want, (pts["y"], pts["x"]), pts["a"].astype(np.float64))
+    assert np.max(np.abs(u - want)) < 1e-12
+    e = orc.cgh_direct(LAM, PITCH, pts["x"], pts["y"], pts["a"], np.zeros(n), 0, 0, NH, NH, True)
+    assert np.max(np.abs(e - want)) < 1e-12
+
+
+def test_keep_all_exact_on_both_sides_of_the_plane(orc):
+    pts = aligned(uniform_cloud(9, 30, NH, -ZMAX, ZMAX), 8)
+    zd = orc.depth_grid(-ZMAX, ZMAX, 2 * D)
+    pts["d"], bad = orc.quantize(pts["z"], -ZMAX, ZMAX, 2 * D)
+    assert bad == 0 and np.any(zd[pts["d"]] < 0) and np.any(zd[pts["d"]] > 0)
+    lut = orc.build_lut(LAM, PITCH, zd, W, L, 1.0, dtype="f64")
+    assert _rel(orc.hologram(lut, pts, NH), _eq1(orc, pts, zd, NH)) < 1e-12
