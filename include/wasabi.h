@@ -184,6 +184,43 @@ wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points
 wasabi_status wasabi_superpose_static(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n,
                                       int holo_w, int holo_h, int rule, void* wbuf_dev, void* stream);
 
+/* ---- Frame of a hologram: sub-hologram origin and reference wave --------
+ * Sub-hologram (Sec. 1, large-scale calculation, steps 2-4): the output's
+ * pixel (i, j) is pixel (origin_x + i, origin_y + j) of the hologram plane,
+ * the frame in which the points' (x_j, y_j) are given; the points are
+ * shifted by (-origin_x, -origin_y) before the superposition, the paper's
+ * coordinate transform x'_j = x_j - s N_h, y'_j = y_j - t N_h.  Points whose
+ * footprint misses the output contribute nothing; points partly outside it
+ * contribute the part inside.
+ * Reference wave (Sec. 2): the binary hologram is bit = Re(u conj(R)) > 0.
+ * WASABI_REF_PLANE: R = 1 (a unit plane wave at normal incidence).
+ * WASABI_REF_SPHERICAL: the wave of a unit point source at plane pixel
+ * coordinates (x, y) (real numbers; the plane's pixel (i, j) sits at (i, j))
+ * and signed distance z (metres, nonzero) from the plane, in the convention of
+ * the object points: R = exp(i sgn(z) 2 pi r / lambda),
+ * r = sqrt(pitch^2 ((i - x)^2 + (j - y)^2) + z^2) -- z < 0 (a source behind
+ * the plane) is the converging, conjugate wave.  lambda and pitch in metres
+ * (normally the LUT's).  The phase is reduced in FP64 once per 128- to
+ * 256-pixel-wide anchor and carried to each pixel in FP32 by an exact
+ * difference of squares and a quadratic expansion (phase error below
+ * about 3e-5 cycles); bits can differ from an exact evaluation only where
+ * |Re(u conj R)| is within that of zero.
+ * An all-zero frame is the whole plane from pixel (0, 0) with R = 1. */
+typedef enum { WASABI_REF_PLANE = 0, WASABI_REF_SPHERICAL = 1 } wasabi_reference_kind;
+
+typedef struct {
+  int32_t kind;          /* wasabi_reference_kind */
+  int32_t reserved;      /* 0 */
+  double lambda, pitch;  /* metres (spherical) */
+  double x, y;           /* source position, plane pixels (spherical) */
+  double z;              /* signed source distance from the plane, metres, nonzero (spherical) */
+} wasabi_reference;
+
+typedef struct {
+  int32_t origin_x, origin_y; /* plane pixel of the output's pixel (0, 0) */
+  wasabi_reference ref;       /* reference wave of the binarisation */
+} wasabi_frame;
+
 /* A6 + A7, inverse transformation (Sec. 1, step 3; Sec. 2 binary hologram):
  * the L-level inverse Haar of the tile-major wbuf_dev gives the field u.
  * u_dev (may be NULL): holo_w x holo_h complex64, row-major.
@@ -193,6 +230,14 @@ wasabi_status wasabi_superpose_static(const wasabi_lut* lut, const wasabi_point*
  * 2 <= levels <= 5. */
 wasabi_status wasabi_inverse_haar(const void* wbuf_dev, int holo_w, int holo_h, int levels,
                                   void* u_dev, uint8_t* bits_dev, void* stream);
+/* wasabi_inverse_haar with a frame (may be NULL = all zero): the bits use the
+ * frame's reference wave, evaluated at the output's plane pixels.
+ * E_INVALID for an unknown kind, a nonzero reserved word, or a spherical
+ * reference with non-finite or non-positive lambda / pitch, non-finite x / y,
+ * or z zero or non-finite. */
+wasabi_status wasabi_inverse_haar_frame(const void* wbuf_dev, int holo_w, int holo_h, int levels,
+                                        const wasabi_frame* frame, void* u_dev, uint8_t* bits_dev,
+                                        void* stream);
 
 /* A4 + A5 + A6 + A7 in one pass: superposition (Eq. (2)) fused with the
  * inverse transformation (Sec. 1, step 3) and binarisation (Sec. 2).  Each
@@ -208,6 +253,15 @@ wasabi_status wasabi_inverse_haar(const void* wbuf_dev, int holo_w, int holo_h, 
 wasabi_status wasabi_hologram(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n,
                               int holo_w, int holo_h, int rule, void* wbuf_dev, void* u_dev,
                               uint8_t* bits_dev, void* scratch_dev, size_t scratch_bytes, void* stream);
+/* wasabi_hologram of a frame (may be NULL = all zero): the sub-hologram at
+ * the frame's origin, binarised against its reference wave.  Here wbuf_dev
+ * alone is also allowed (the superposition of a sub-hologram).  A spherical
+ * reference needs complex accumulation (the bits-only fast path accumulates
+ * real parts only).  Frame errors as for wasabi_inverse_haar_frame. */
+wasabi_status wasabi_hologram_frame(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n,
+                                    int holo_w, int holo_h, int rule, const wasabi_frame* frame,
+                                    void* wbuf_dev, void* u_dev, uint8_t* bits_dev, void* scratch_dev,
+                                    size_t scratch_bytes, void* stream);
 
 /* ---- Batches: many holograms through one launch sequence (A10) ----------
  * One job = one hologram with its own points, wavelet buffer and outputs, all
@@ -232,6 +286,7 @@ typedef struct {
                                      or NULL when only u / bits are wanted */
   void* u_dev;                    /* complex64 row-major output (16-B aligned), or NULL */
   uint8_t* bits_dev;              /* packed bits output (4-B aligned), or NULL; not all three NULL */
+  wasabi_frame frame;             /* sub-hologram origin and reference wave; all zero = whole plane, R = 1 */
 } wasabi_job;
 
 typedef struct wasabi_batch wasabi_batch;
@@ -288,6 +343,7 @@ typedef struct {
   int rule;                         /* wasabi_shift_rule */
   uint8_t* bits_host;               /* packed binary hologram (host), or NULL */
   void* u_host;                     /* complex64 row-major field (host), or NULL; not both NULL */
+  wasabi_frame frame;               /* sub-hologram origin and reference wave; all zero = whole plane, R = 1 */
 } wasabi_request;
 
 typedef struct {

@@ -17,6 +17,8 @@ Functions and the passages they follow:
 * ``superpose``       — Eq. (2) with the shift rule R6
 * ``subhologram`` / ``hologram`` — Sec. 1, large-scale steps 2-4
 * ``binarize``        — Sec. 2 (binary amplitude hologram; R7)
+* ``reference_wave`` / ``binarize_ref`` — Sec. 2 (spherical reference wave,
+  bit = Re(u conj R) > 0; R12)
 * ``cgh_direct``      — Eq. (1)
 
 Parity pins live in ``tests/test_oracle_*.py``.  Functions without an
@@ -91,6 +93,9 @@ def lib():
                       _f32p, _u32p, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
                       C.c_int, t]
     L.orc_binarize_f32.argtypes = [_f32p, C.c_int64, C.c_int64, _u8p]
+    L.orc_reference_wave.argtypes = [C.c_double] * 5 + [C.c_int64] * 4 + [_f64p]
+    L.orc_binarize_ref_f64.argtypes = ([_f64p, C.c_int64, C.c_int64] + [C.c_double] * 5 +
+                                       [C.c_int64, C.c_int64, _u8p, _f64p])
     L.orc_cgh_direct_f64.argtypes = [C.c_double, C.c_double, _i32p, _i32p, _f32p,
                                      _f64p, C.c_int64, C.c_int64, C.c_int64,
                                      C.c_int64, C.c_int64, C.c_int, _f64p, C.c_int]
@@ -310,6 +315,28 @@ def binarize(u: np.ndarray) -> np.ndarray:
     bits = np.empty((w * h + 7) // 8, np.uint8)
     lib().orc_binarize_f32(_p(uf, _f32p), w, h, _p(bits, _u8p))
     return bits
+
+
+def reference_wave(lam: float, pitch: float, xr: float, yr: float, zr: float, w: int, h: int,
+                   ox: int = 0, oy: int = 0) -> np.ndarray:
+    """Reading R12 (Sec. 2): the spherical reference wave over the region
+    [ox, ox+w) x [oy, oy+h) of the plane (h x w complex128)."""
+    R = np.empty((h, w), np.complex128)
+    lib().orc_reference_wave(lam, pitch, xr, yr, zr, ox, oy, w, h, _p(R, _f64p))
+    return R
+
+
+def binarize_ref(u: np.ndarray, lam: float, pitch: float, xr: float, yr: float, zr: float,
+                 ox: int = 0, oy: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Reading R12: packed bits of Re(u conj R) > 0 and the values
+    Re(u conj R) (h x w float64) for the field u of the region at (ox, oy)."""
+    h, w = u.shape
+    uf = np.ascontiguousarray(u, np.complex128)
+    bits = np.empty((w * h + 7) // 8, np.uint8)
+    val = np.empty((h, w), np.float64)
+    lib().orc_binarize_ref_f64(_p(uf, _f64p), w, h, lam, pitch, xr, yr, zr, ox, oy, _p(bits, _u8p),
+                               _p(val, _f64p))
+    return bits, val
 
 
 def cgh_direct(lam: float, pitch: float, x, y, a, z, ox: int, oy: int, w: int, h: int,

@@ -7,7 +7,8 @@
 // product path (the CUDA library) never does, and the two share no code.
 //
 // Every function cites the passage it follows.  Where the paper is silent or
-// ambiguous the reading taken is stated beside the code (readings R1-R9):
+// ambiguous the reading taken is stated beside the code (readings R1-R12;
+// R10 is the sub-hologram driver, R11 the image-type sign convention):
 //   R1 PSF support radius (Sec. 1, step 1: "W_j is the PSF radius"):
 //      one radius R(z) = z * tan(asin(lambda / (2 p))) / p  [pixels], the
 //      alias-free diffraction limit of pitch p; support is the open disk
@@ -42,6 +43,13 @@
 //      r = sqrt(n p^2 + z^2), t = r / lambda.
 //   R9 Eq. (1) has no 1/r factor and a +i sign, as printed; a_j is used as an
 //      amplitude.
+//   R12 reference wave (Sec. 2, a spherical wave from (x_r, y_r, z_r)): the
+//      wave of a unit point source in the object points' convention (R9,
+//      R11), R = exp(i sgn(z_r) 2 pi r / lambda),
+//      r = sqrt(((x_h - x_r) p)^2 + ((y_h - y_r) p)^2 + z_r^2), with x_r, y_r
+//      in plane pixels (real) and pixel (i, j) at (i, j); the binary
+//      hologram is bit = Re(u conj R) > 0, the sign of the interference term
+//      of |u + R|^2.  R7 is the case R = 1.
 //
 // Build: g++ -O2 -ffp-contract=off -fPIC -shared (contraction must stay off:
 // the FP32 selection path depends on every rounding being the written one).
@@ -481,6 +489,23 @@ void cgh_direct(double lambda, double pitch, const int32_t* x, const int32_t* y,
   }
 }
 
+// R12: reference wave over the region [ox, ox + w) x [oy, oy + h) of the
+// plane, FP64, interleaved complex, row-major.
+void reference_wave(double lambda, double pitch, double xr, double yr,
+                    double zr, int64_t ox, int64_t oy, int64_t w, int64_t h,
+                    double* R) {
+  const double sg = zr < 0 ? -1.0 : 1.0;
+  for (int64_t yy = 0; yy < h; ++yy)
+    for (int64_t xx = 0; xx < w; ++xx) {
+      const double dx = ((double)(ox + xx) - xr) * pitch;
+      const double dy = ((double)(oy + yy) - yr) * pitch;
+      const double t = std::sqrt(dx * dx + dy * dy + zr * zr) / lambda;
+      const double f = t - std::floor(t);
+      R[2 * (yy * w + xx) + 0] = std::cos(2.0 * kPi * f);
+      R[2 * (yy * w + xx) + 1] = sg * std::sin(2.0 * kPi * f);
+    }
+}
+
 }  // namespace
 
 // =================================================================== C ABI ==
@@ -609,6 +634,28 @@ void orc_binarize_f32(const float* u, int64_t w, int64_t h, uint8_t* bits) {
       const int64_t i = yy * w + xx;
       if (u[2 * i] > 0.0f) bits[i >> 3] |= (uint8_t)(1u << (i & 7));
     }
+}
+
+void orc_reference_wave(double lambda, double pitch, double xr, double yr,
+                        double zr, int64_t ox, int64_t oy, int64_t w, int64_t h,
+                        double* R) {
+  reference_wave(lambda, pitch, xr, yr, zr, ox, oy, w, h, R);
+}
+
+// R12: bits of Re(u conj R) > 0 for the field u (interleaved complex FP64)
+// of the region at (ox, oy); val receives Re(u conj R) per pixel.
+void orc_binarize_ref_f64(const double* u, int64_t w, int64_t h, double lambda,
+                          double pitch, double xr, double yr, double zr,
+                          int64_t ox, int64_t oy, uint8_t* bits, double* val) {
+  std::vector<double> R((size_t)(2 * w * h));
+  reference_wave(lambda, pitch, xr, yr, zr, ox, oy, w, h, R.data());
+  std::memset(bits, 0, (size_t)((w * h + 7) / 8));
+  for (int64_t i = 0; i < w * h; ++i) {
+    // Re(u conj R) = Re u Re R + Im u Im R
+    const double v = u[2 * i] * R[(size_t)(2 * i)] + u[2 * i + 1] * R[(size_t)(2 * i + 1)];
+    val[i] = v;
+    if (v > 0.0) bits[i >> 3] |= (uint8_t)(1u << (i & 7));
+  }
 }
 
 void orc_cgh_direct_f64(double lambda, double pitch, const int32_t* x,

@@ -37,6 +37,8 @@ SIGNATURES = [
     ("wasabi_superpose_static", _i, [_VP, _VP, _i64, _i, _i, _i, _VP, _VP]),
     ("wasabi_hologram", _i, [_VP, _VP, _i64, _i, _i, _i, _VP, _VP, _VP, _VP, _sz, _VP]),
     ("wasabi_inverse_haar", _i, [_VP, _i, _i, _i, _VP, _VP, _VP]),
+    ("wasabi_hologram_frame", _i, [_VP, _VP, _i64, _i, _i, _i, _VP, _VP, _VP, _VP, _VP, _sz, _VP]),
+    ("wasabi_inverse_haar_frame", _i, [_VP, _i, _i, _i, _VP, _VP, _VP, _VP]),
     ("cgh_direct_scratch_bytes", _i, [_i64, _i, _i, C.POINTER(_sz)]),
     ("cgh_direct", _i, [_d, _d, _F64P, _i, _VP, _i64, _i, _i, _i, _VP, _VP, _sz, _VP]),
     ("wasabi_sync_status", _i, [_VP]),
@@ -56,18 +58,31 @@ SIGNATURES = [
 ]
 
 
+REF_PLANE, REF_SPHERICAL = 0, 1
+
+
+class Reference(C.Structure):
+    """wasabi_reference of include/wasabi.h."""
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("lam", C.c_double), ("pitch", C.c_double),
+                ("x", C.c_double), ("y", C.c_double), ("z", C.c_double)]
+
+
+class Frame(C.Structure):
+    """wasabi_frame of include/wasabi.h."""
+    _fields_ = [("origin_x", C.c_int32), ("origin_y", C.c_int32), ("ref", Reference)]
+
+
 class Job(C.Structure):
     """wasabi_job of include/wasabi.h."""
     _fields_ = [("points_dev", C.c_void_p), ("n", C.c_int64), ("holo_w", C.c_int),
                 ("holo_h", C.c_int), ("rule", C.c_int), ("wbuf_dev", C.c_void_p),
-                ("u_dev", C.c_void_p), ("bits_dev", C.c_void_p)]
-
+                ("u_dev", C.c_void_p), ("bits_dev", C.c_void_p), ("frame", Frame)]
 
 
 class Request(C.Structure):
     """wasabi_request of include/wasabi.h."""
     _fields_ = [("points_host", C.c_void_p), ("n", C.c_int64), ("holo_w", C.c_int), ("holo_h", C.c_int),
-                ("rule", C.c_int), ("bits_host", C.c_void_p), ("u_host", C.c_void_p)]
+                ("rule", C.c_int), ("bits_host", C.c_void_p), ("u_host", C.c_void_p), ("frame", Frame)]
 
 
 class RequestInfo(C.Structure):

@@ -130,8 +130,10 @@ def scratch_bytes(lut: Lut, n: int, w: int, h: int) -> int:
 
 def superpose(lut: Lut, points: torch.Tensor, w: int, h: int, rule: int = 0,
               wbuf: torch.Tensor | None = None, scratch: torch.Tensor | None = None,
-              stream=None) -> torch.Tensor:
-    """Eq. (2): the tile-major wavelet buffer (h*w complex64)."""
+              stream=None, origin=(0, 0)) -> torch.Tensor:
+    """Eq. (2): the tile-major wavelet buffer (h*w complex64); origin: plane
+    pixel of the buffer's pixel (0, 0) (a sub-hologram, through
+    wasabi_hologram_frame with the wavelet buffer as the only output)."""
     n = points.shape[0]
     dev = points.device
     if wbuf is None:
@@ -139,9 +141,14 @@ def superpose(lut: Lut, points: torch.Tensor, w: int, h: int, rule: int = 0,
     need = scratch_bytes(lut, n, w, h)
     if scratch is None:
         scratch = torch.empty(need, dtype=torch.uint8, device=dev)
-    check(_lib().wasabi_superpose(lut.handle, _ptr(points) if n else C.c_void_p(None), n, w, h,
-                                  rule, _ptr(wbuf), _ptr(scratch), scratch.numel(),
-                                  _stream(stream)))
+    pts = _ptr(points) if n else C.c_void_p(None)
+    if tuple(origin) == (0, 0):
+        check(_lib().wasabi_superpose(lut.handle, pts, n, w, h, rule, _ptr(wbuf), _ptr(scratch),
+                                      scratch.numel(), _stream(stream)))
+    else:
+        frame = make_frame(origin, None)
+        check(_lib().wasabi_hologram_frame(lut.handle, pts, n, w, h, rule, C.byref(frame), _ptr(wbuf),
+                                           None, None, _ptr(scratch), scratch.numel(), _stream(stream)))
     return wbuf
 
 
@@ -158,14 +165,38 @@ def superpose_static(lut: Lut, points: torch.Tensor, w: int, h: int, rule: int =
     return wbuf
 
 
+def spherical_reference(lam: float, pitch: float, x: float, y: float, z: float) -> dict:
+    """Reference wave of a unit point source at plane pixel coordinates
+    (x, y) and signed distance z (metres) from the plane (Sec. 2)."""
+    return {"lam": float(lam), "pitch": float(pitch), "x": float(x), "y": float(y), "z": float(z)}
+
+
+def make_frame(origin=(0, 0), reference: dict | None = None) -> _abi.Frame:
+    """wasabi_frame: sub-hologram origin (plane pixel of output pixel
+    (0, 0)) and reference wave (None = unit plane wave)."""
+    f = _abi.Frame()
+    f.origin_x, f.origin_y = int(origin[0]), int(origin[1])
+    if reference is not None:
+        f.ref.kind = _abi.REF_SPHERICAL
+        f.ref.lam, f.ref.pitch = reference["lam"], reference["pitch"]
+        f.ref.x, f.ref.y, f.ref.z = reference["x"], reference["y"], reference["z"]
+    return f
+
+
 def inverse_haar(wbuf: torch.Tensor, w: int, h: int, levels: int, u: torch.Tensor | None = None,
-                 bits: torch.Tensor | None = None, want: str = "complex", stream=None):
+                 bits: torch.Tensor | None = None, want: str = "complex", stream=None,
+                 origin=(0, 0), reference: dict | None = None):
+    """Inverse transform and binarisation (wasabi_inverse_haar_frame); the
+    bits use `reference` (None = unit plane wave) at plane pixels offset by
+    `origin`."""
     dev = wbuf.device
     if want in ("complex", "both") and u is None:
         u = torch.empty((h, w), dtype=torch.complex64, device=dev)
     if want in ("bits", "both") and bits is None:
         bits = torch.empty((h * w + 7) // 8, dtype=torch.uint8, device=dev)
-    check(_lib().wasabi_inverse_haar(_ptr(wbuf), w, h, levels, _ptr(u), _ptr(bits), _stream(stream)))
+    frame = make_frame(origin, reference)
+    check(_lib().wasabi_inverse_haar_frame(_ptr(wbuf), w, h, levels, C.byref(frame), _ptr(u), _ptr(bits),
+                                           _stream(stream)))
     if want == "complex":
         return u
     if want == "bits":
@@ -175,10 +206,13 @@ def inverse_haar(wbuf: torch.Tensor, w: int, h: int, levels: int, u: torch.Tenso
 
 def hologram(lut: Lut, points: torch.Tensor, w: int, h: int, want: str = "complex", rule: int = 0,
              u: torch.Tensor | None = None, bits: torch.Tensor | None = None,
-             wbuf: torch.Tensor | None = None, scratch: torch.Tensor | None = None, stream=None):
+             wbuf: torch.Tensor | None = None, scratch: torch.Tensor | None = None, stream=None,
+             origin=(0, 0), reference: dict | None = None):
     """Eq. (2) fused with the inverse transform and binarisation
-    (wasabi_hologram): want = "complex" | "bits" | "both".  A given wbuf also
-    receives the tile-major wavelet buffer."""
+    (wasabi_hologram / wasabi_hologram_frame): want = "complex" | "bits" |
+    "both".  A given wbuf also receives the tile-major wavelet buffer.
+    origin: plane pixel of the output's pixel (0, 0) (a sub-hologram);
+    reference: spherical_reference(...) for the bits, None = unit plane wave."""
     n = points.shape[0]
     dev = points.device
     if want in ("complex", "both") and u is None:
@@ -187,9 +221,15 @@ def hologram(lut: Lut, points: torch.Tensor, w: int, h: int, want: str = "comple
         bits = torch.empty((h * w + 7) // 8, dtype=torch.uint8, device=dev)
     if scratch is None:
         scratch = torch.empty(scratch_bytes(lut, n, w, h), dtype=torch.uint8, device=dev)
-    check(_lib().wasabi_hologram(lut.handle, _ptr(points) if n else C.c_void_p(None), n, w, h, rule,
-                                 _ptr(wbuf), _ptr(u), _ptr(bits), _ptr(scratch), scratch.numel(),
-                                 _stream(stream)))
+    if tuple(origin) == (0, 0) and reference is None:
+        check(_lib().wasabi_hologram(lut.handle, _ptr(points) if n else C.c_void_p(None), n, w, h, rule,
+                                     _ptr(wbuf), _ptr(u), _ptr(bits), _ptr(scratch), scratch.numel(),
+                                     _stream(stream)))
+    else:
+        frame = make_frame(origin, reference)
+        check(_lib().wasabi_hologram_frame(lut.handle, _ptr(points) if n else C.c_void_p(None), n, w, h, rule,
+                                           C.byref(frame), _ptr(wbuf), _ptr(u), _ptr(bits), _ptr(scratch),
+                                           scratch.numel(), _stream(stream)))
     if want == "complex":
         return u
     if want == "bits":
@@ -224,9 +264,11 @@ class Batch:
     """Many holograms through one launch sequence (wasabi_batch_*).
 
     A job is a dict: points (N x 4 int32 CUDA tensor), w, h, and optionally
-    rule, wbuf, want ("none" | "complex" | "bits" | "both"); run() allocates
-    missing buffers, returns the jobs with their wbuf / u / bits tensors and
-    keeps the scratch alive until the next run."""
+    rule, want ("none" | "complex" | "bits" | "both"), wbuf (a tensor, or
+    keep_wbuf=True to have one allocated; always for want "none"), origin and
+    reference (as for hologram()); run() allocates missing buffers, returns
+    the jobs with their wbuf / u / bits tensors and keeps the scratch alive
+    until the next run."""
 
     def __init__(self, lut: Lut, max_jobs: int, side_hint: int = 4096, use_graph: bool = True):
         self.lut = lut
@@ -251,7 +293,7 @@ class Batch:
             w, h = j["w"], j["h"]
             want = j.get("want", "bits")
             wbuf = j.get("wbuf")
-            if wbuf is None:
+            if wbuf is None and (want == "none" or j.get("keep_wbuf", False)):
                 wbuf = torch.empty(h * w, dtype=torch.complex64, device=dev)
             u = j.get("u")
             if u is None and want in ("complex", "both"):
@@ -260,9 +302,10 @@ class Batch:
             if bits is None and want in ("bits", "both"):
                 bits = torch.empty((h * w + 7) // 8, dtype=torch.uint8, device=dev)
             arr[i] = _abi.Job(pts.data_ptr() if pts.shape[0] else None, pts.shape[0], w, h,
-                              j.get("rule", 0), wbuf.data_ptr(),
+                              j.get("rule", 0), wbuf.data_ptr() if wbuf is not None else None,
                               u.data_ptr() if u is not None else None,
-                              bits.data_ptr() if bits is not None else None)
+                              bits.data_ptr() if bits is not None else None,
+                              make_frame(j.get("origin", (0, 0)), j.get("reference")))
             out.append(dict(j, wbuf=wbuf, u=u, bits=bits))
         need = C.c_size_t()
         check(_lib().wasabi_batch_scratch_bytes(self._h, C.cast(arr, C.c_void_p), n, C.byref(need)))
@@ -301,7 +344,8 @@ class Server:
         self._h = h
         self._live = {}
 
-    def submit(self, points: torch.Tensor, w: int, h: int, want: str = "bits", rule: int = 0) -> int:
+    def submit(self, points: torch.Tensor, w: int, h: int, want: str = "bits", rule: int = 0,
+               origin=(0, 0), reference: dict | None = None) -> int:
         if points.is_cuda or not points.is_contiguous() or points.dtype != torch.int32:
             raise ValueError("points: contiguous (N, 4) int32 host tensor")
         pin = points.is_pinned()
@@ -310,7 +354,7 @@ class Server:
         u = torch.empty((h, w), dtype=torch.complex64, pin_memory=pin) if want in ("complex", "both") else None
         req = _abi.Request(points.data_ptr() if points.shape[0] else None, points.shape[0], w, h, rule,
                            bits.data_ptr() if bits is not None else None,
-                           u.data_ptr() if u is not None else None)
+                           u.data_ptr() if u is not None else None, make_frame(origin, reference))
         rid = C.c_int64()
         check(_lib().wasabi_server_submit(self._h, C.byref(req), C.byref(rid)))
         self._live[rid.value] = (points, bits, u)

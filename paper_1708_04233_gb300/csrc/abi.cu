@@ -663,16 +663,59 @@ wasabi_status wasabi_hologram(const wasabi_lut* lut, const wasabi_point* points_
                         scratch_bytes, (cudaStream_t)stream, cell, threads);
 }
 
+wasabi_status wasabi_hologram_frame(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n, int holo_w,
+                                    int holo_h, int rule, const wasabi_frame* frame, void* wbuf_dev, void* u_dev,
+                                    uint8_t* bits_dev, void* scratch_dev, size_t scratch_bytes, void* stream) {
+  if (!lut) { set_error("hologram_frame: NULL argument"); return WASABI_E_INVALID; }
+  int cell, threads;
+  superpose_config(lut, holo_w, holo_h, &cell, &threads);
+  return superpose_impl(lut, points_dev, n, holo_w, holo_h, rule, wbuf_dev, u_dev, bits_dev, scratch_dev,
+                        scratch_bytes, (cudaStream_t)stream, cell, threads, frame);
+}
+
 }  // extern "C"
+
+bool wsb::frame_to_dev(const wasabi_frame* f, int* ox, int* oy, RefDev* ref, const char** why) {
+  *ox = *oy = 0;
+  std::memset(ref, 0, sizeof *ref);
+  if (!f) return true;
+  const wasabi_reference& r = f->ref;
+  if (r.reserved != 0 || (r.kind != WASABI_REF_PLANE && r.kind != WASABI_REF_SPHERICAL)) {
+    *why = "unknown reference kind";
+    return false;
+  }
+  if (r.kind == WASABI_REF_SPHERICAL) {
+    if (!(std::isfinite(r.lambda) && r.lambda > 0 && std::isfinite(r.pitch) && r.pitch > 0 &&
+          std::isfinite(r.x) && std::isfinite(r.y) && std::isfinite(r.z) && r.z != 0)) {
+      *why = "spherical reference needs finite lambda, pitch > 0, finite x, y and a finite nonzero z";
+      return false;
+    }
+    const double a = r.pitch / r.lambda, c = r.z / r.lambda;
+    ref->kind = 1;
+    ref->sgn = r.z < 0 ? -1.f : 1.f;
+    ref->a2 = a * a;
+    ref->a2f = (float)(a * a);
+    ref->c = c * c;
+    ref->x = r.x;
+    ref->y = r.y;
+  }
+  *ox = f->origin_x;
+  *oy = f->origin_y;
+  return true;
+}
 
 wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n, int holo_w,
                                   int holo_h, int rule, void* wbuf_dev, void* u_dev, uint8_t* bits_dev,
                                   void* scratch_dev, size_t scratch_bytes, cudaStream_t stream, int cell,
-                                  int threads) {
+                                  int threads, const wasabi_frame* frame) {
   if (!lut || n < 0 || (n > 0 && !points_dev) || (!wbuf_dev && !u_dev && !bits_dev) || !scratch_dev) {
     set_error("superpose: NULL argument");
     return WASABI_E_INVALID;
   }
+  int fox, foy;
+  RefDev fref;
+  const char* why = "";
+  if (!frame_to_dev(frame, &fox, &foy, &fref, &why)) { set_error("hologram: %s", why); return WASABI_E_INVALID; }
   if ((u_dev || bits_dev) && lut->L < 2) {
     set_error("hologram: the fused inverse needs levels >= 2");
     return WASABI_E_INVALID;
@@ -704,7 +747,7 @@ wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* poi
   }
   const int rows = (cell + 2 * lut->reach) / cell + 2;
   if (rows > superpose_max_cell_rows()) { set_error("superpose: window too large for the super-tile"); return WASABI_E_INVALID; }
-  const bool re_only = !wbuf_dev && !u_dev && bits_dev;
+  const bool re_only = !wbuf_dev && !u_dev && bits_dev && !frame_needs_complex(frame);
   const int rcap = superpose_range_cap(cell, lut->L, lut->lmin, lut->D, re_only, threads);
   const size_t smem = superpose_smem_bytes(cell, lut->L, lut->lmin, lut->D, re_only, rcap);
   if (smem > 220 * 1024) { set_error("superpose: super-tile %d needs %zu B of shared memory", cell, smem); return WASABI_E_INVALID; }
@@ -712,6 +755,7 @@ wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* poi
   JobDev J = make_job(lut, points_dev, n, holo_w, holo_h, rule, cell, static_cast<float2*>(wbuf_dev),
                       static_cast<float2*>(u_dev), bits_dev);
   J.sorted = b.sorted; J.cnt = b.cnt; J.off = b.off; J.cursor = b.cursor;
+  J.ox = fox; J.oy = foy; J.ref = fref;
   cudaError_t e = launch_init_single(J, b.jobs, b.batch, super_tiles(J.ntx, J.nty, cell >> lut->L), s);
   if (e != cudaSuccess) return cuda_fail("superpose: init", e);
   BinArgs ba;
@@ -725,6 +769,7 @@ wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* poi
   sa.jobs = b.jobs; sa.batch = b.batch; sa.cell = cell; sa.reach = lut->reach;
   sa.acc_float = env_int("WASABI_ACC_FLOAT", 0) != 0;
   sa.re_only = re_only ? 1 : 0;
+  sa.has_ref = (fref.kind != 0 && bits_dev) ? 1 : 0;
   sa.rcap = rcap;
   sa.status = status; sa.threads = threads; sa.grid = sms;
   e = launch_superpose(sa, s);
@@ -735,6 +780,15 @@ extern "C" {
 
 wasabi_status wasabi_inverse_haar(const void* wbuf_dev, int holo_w, int holo_h, int levels, void* u_dev,
                                   uint8_t* bits_dev, void* stream) {
+  return wasabi_inverse_haar_frame(wbuf_dev, holo_w, holo_h, levels, nullptr, u_dev, bits_dev, stream);
+}
+
+wasabi_status wasabi_inverse_haar_frame(const void* wbuf_dev, int holo_w, int holo_h, int levels,
+                                        const wasabi_frame* frame, void* u_dev, uint8_t* bits_dev, void* stream) {
+  int fox, foy;
+  RefDev fref;
+  const char* why = "";
+  if (!frame_to_dev(frame, &fox, &foy, &fref, &why)) { set_error("inverse_haar: %s", why); return WASABI_E_INVALID; }
   if (!wbuf_dev || (!u_dev && !bits_dev)) { set_error("inverse_haar: need the buffer and an output"); return WASABI_E_INVALID; }
   if (levels < 2 || levels > kMaxLevels) { set_error("inverse_haar: levels must be in [2, %d]", kMaxLevels); return WASABI_E_INVALID; }
   const int ts = 1 << levels;
@@ -762,6 +816,9 @@ wasabi_status wasabi_inverse_haar(const void* wbuf_dev, int holo_w, int holo_h, 
   ia.L = levels;
   ia.status = status;
   ia.num_sms = sms;
+  ia.ox = fox;
+  ia.oy = foy;
+  ia.ref = fref;
   const cudaError_t e = launch_inverse(ia, (cudaStream_t)stream);
   return e == cudaSuccess ? WASABI_OK : cuda_fail("inverse_haar: launch", e);
 }

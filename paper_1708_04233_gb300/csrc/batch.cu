@@ -32,8 +32,10 @@ struct wasabi_batch {
   bool staged_pending = false;
   // One graph per accumulation mode (complex, or real parts only when every
   // job wants bits alone), each bound to the stream it was captured on.
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
-  cudaStream_t graph_stream[2] = {nullptr, nullptr};
+  // One graph per kernel mode: complex accumulation, real parts only,
+  // complex with the spherical-reference epilogue.
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t graph_stream[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -67,13 +69,21 @@ wasabi_status check_job(const wasabi_lut* lut, const wasabi_job& j, int idx) {
     set_error("batch: job %d: misaligned buffer", idx);
     return WASABI_E_INVALID;
   }
+  int ox, oy;
+  RefDev ref;
+  const char* why = "";
+  if (!frame_to_dev(&j.frame, &ox, &oy, &ref, &why)) {
+    set_error("batch: job %d: %s", idx, why);
+    return WASABI_E_INVALID;
+  }
   return WASABI_OK;
 }
 
 // Enqueues the upload and the five launches of a batch on s.  Under stream
 // capture the record of `staged` becomes an external event node, so the host
 // can wait on it after each replay.
-cudaError_t enqueue_batch(wasabi_batch* b, cudaStream_t s, int* status, int sms, bool capturing, bool re_only) {
+cudaError_t enqueue_batch(wasabi_batch* b, cudaStream_t s, int* status, int sms, bool capturing, int mode) {
+  const bool re_only = mode == 1;
   cudaError_t e = cudaMemcpyAsync(b->jobs_dev, b->staging_jobs, sizeof(JobDev) * b->max_jobs,
                                   cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -91,6 +101,7 @@ cudaError_t enqueue_batch(wasabi_batch* b, cudaStream_t s, int* status, int sms,
   sa.jobs = b->jobs_dev; sa.batch = b->batch_dev; sa.cell = b->cell; sa.reach = lut->reach;
   sa.acc_float = 0; sa.status = status; sa.threads = b->threads; sa.grid = sms;
   sa.re_only = re_only ? 1 : 0;
+  sa.has_ref = mode == 2 ? 1 : 0;
   sa.rcap = superpose_range_cap(b->cell, lut->L, lut->lmin, lut->D, re_only, b->threads);
   if ((e = launch_superpose(sa, s)) != cudaSuccess) return e;
   return cudaSuccess;
@@ -159,7 +170,7 @@ wasabi_status wasabi_batch_destroy(wasabi_batch* b) {
   cudaGetDevice(&prev);
   cudaSetDevice(b->device);
   if (b->staged) cudaEventSynchronize(b->staged);
-  for (int m = 0; m < 2; ++m)
+  for (int m = 0; m < 3; ++m)
     if (b->exec[m]) cudaGraphExecDestroy(b->exec[m]);
   if (b->staged) cudaEventDestroy(b->staged);
   if (b->jobs_dev) cudaFree(b->jobs_dev);
@@ -242,6 +253,8 @@ wasabi_status wasabi_batch_run(wasabi_batch* b, const wasabi_job* jobs, int njob
     J.ncy = (j.holo_h + b->cell - 1) / b->cell;
     J.ncells = J.ncx * J.ncy;
     J.rule = j.rule;
+    const char* why = "";
+    frame_to_dev(&j.frame, &J.ox, &J.oy, &J.ref, &why);  // checked above
     J.cnt = c.take<int>((size_t)J.ncells + 1);
     J.off = c.take<int>((size_t)J.ncells + 1);
     J.cursor = c.take<int>((size_t)J.ncells);
@@ -257,8 +270,11 @@ wasabi_status wasabi_batch_run(wasabi_batch* b, const wasabi_job* jobs, int njob
   B.nsp = sp0;
   B.npts = pt0;
   bool re_only = njobs > 0;
-  for (int i = 0; i < njobs; ++i) re_only = re_only && !jobs[i].wbuf_dev && !jobs[i].u_dev && jobs[i].bits_dev;
-  const int m = re_only ? 1 : 0;
+  for (int i = 0; i < njobs; ++i)
+    re_only = re_only && !jobs[i].wbuf_dev && !jobs[i].u_dev && jobs[i].bits_dev && !frame_needs_complex(&jobs[i].frame);
+  bool has_ref = false;
+  for (int i = 0; i < njobs; ++i) has_ref = has_ref || (jobs[i].bits_dev && frame_needs_complex(&jobs[i].frame));
+  const int m = re_only ? 1 : has_ref ? 2 : 0;
   const cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
   if (b->use_graph && s != nullptr) {
@@ -267,7 +283,7 @@ wasabi_status wasabi_batch_run(wasabi_batch* b, const wasabi_job* jobs, int njob
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        const cudaError_t e2 = enqueue_batch(b, s, status, sms, true, re_only);
+        const cudaError_t e2 = enqueue_batch(b, s, status, sms, true, m);
         e = cudaStreamEndCapture(s, &g);
         if (e2 != cudaSuccess) e = e2;
       }
@@ -278,7 +294,7 @@ wasabi_status wasabi_batch_run(wasabi_batch* b, const wasabi_job* jobs, int njob
     }
     e = cudaGraphLaunch(b->exec[m], s);
   } else {
-    e = enqueue_batch(b, s, status, sms, false, re_only);
+    e = enqueue_batch(b, s, status, sms, false, m);
   }
   if (e != cudaSuccess) return cuda_fail("batch_run: launch", e);
   b->staged_pending = true;

@@ -45,10 +45,15 @@ __global__ void init_single_kernel(JobDev job, JobDev* jobs, BatchDev* b, int ns
   b->npts = job.n;
 }
 
-// Cell of a point of job J, or -1 if the point is left out.
-__device__ __forceinline__ int cell_of(const JobDev& J, const wasabi_point& p, int cell, int reach, int D) {
+// Cell of a point of job J, or -1 if the point is left out.  The point is
+// moved into the job's frame first: x'_j = x_j - origin_x, y'_j = y_j - origin_y
+// (the sub-hologram coordinate transform of Sec. 1, large-scale step 3).
+__device__ __forceinline__ int cell_of(const JobDev& J, wasabi_point& p, int cell, int reach, int D) {
   if (p.d >= (uint32_t)D) return -1;
-  if (p.x < -reach || p.x >= J.w + reach || p.y < -reach || p.y >= J.h + reach) return -1;
+  const long long lx = (long long)p.x - J.ox, ly = (long long)p.y - J.oy;
+  if (lx < -reach || lx >= (long long)J.w + reach || ly < -reach || ly >= (long long)J.h + reach) return -1;
+  p.x = (int)lx;
+  p.y = (int)ly;
   const int cx = min(max(p.x, 0), J.w - 1) / cell;
   const int cy = min(max(p.y, 0), J.h - 1) / cell;
   return cy * J.ncx + cx;
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(256) count_kernel(BinArgs b) {
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < npts; g += stride) {
     const int jid = job_of(spt0, nj, g);
     const JobDev& J = b.jobs[jid];
-    const wasabi_point p = J.pts[g - J.pt0];
+    wasabi_point p = J.pts[g - J.pt0];
     if (p.d >= (uint32_t)b.D) atomicCAS(b.status, 0, WASABI_E_RANGE);
     const int c = cell_of(J, p, b.cell, b.reach, b.D);
     if (c >= 0) atomicAdd(&J.cnt[c], 1);
@@ -171,8 +176,8 @@ __global__ void __launch_bounds__(256) scatter_points_kernel(BinArgs b) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < npts; g += stride) {
     const JobDev& J = b.jobs[job_of(spt0, nj, g)];
-    const wasabi_point p = J.pts[g - J.pt0];
-    const int c = cell_of(J, p, b.cell, b.reach, b.D);
+    wasabi_point p = J.pts[g - J.pt0];
+    const int c = cell_of(J, p, b.cell, b.reach, b.D);  // p now in the job's frame
     if (c < 0) continue;
     const int slot = atomicAdd(&J.cursor[c], 1);
     J.sorted[slot] = p;

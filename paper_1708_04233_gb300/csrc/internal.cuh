@@ -183,6 +183,72 @@ __device__ __forceinline__ float2 ipick(float2 s, float2 lh, float2 hl, float2 h
   return make_float2(ipick1(s.x, lh.x, hl.x, hh.x, ax, ay), ipick1(s.y, lh.y, hl.y, hh.y, ax, ay));
 }
 
+// Reference wave of the binarisation (Sec. 2): a unit point source at plane
+// pixel coordinates (x, y) and signed distance z,
+// R = exp(i sgn(z) 2 pi t), t = r / lambda = sqrt(a2 ((i - x)^2 + (j - y)^2) + c)
+// with a2 = (pitch / lambda)^2 and c = (z / lambda)^2; bit = Re(u conj R) > 0.
+// kind 0 is the unit plane wave R = 1 (nothing below is evaluated).
+struct RefDev {
+  int kind;
+  float sgn;   // sign of z
+  float a2f;   // a2 in FP32
+  float pad;
+  double x, y, a2, c;
+};
+
+// Phase of R at an anchor pixel (X, Y) of the plane: frac(t) from an FP64
+// reduction, t and the offsets from the source in FP32.
+struct RefAnchor {
+  float f0, t0, ex, ey;
+};
+__device__ __forceinline__ RefAnchor ref_anchor(const RefDev& r, long long X, long long Y) {
+  const double ex = (double)X - r.x, ey = (double)Y - r.y;
+  const double t = sqrt(fma(r.a2, fma(ex, ex, ey * ey), r.c));
+  RefAnchor A;
+  A.f0 = (float)(t - floor(t));
+  A.t0 = (float)t;
+  A.ex = (float)ex;
+  A.ey = (float)ey;
+  return A;
+}
+
+// Phase at pixel (dx, dy) from the anchor, reduced to [0, 1), with the
+// first and half second derivatives there: t - t0 = a2 m / (t0 + t) with the
+// exact difference of squares m = dx (2 ex + dx) + dy (2 ey + dy) (no
+// cancellation), and dt/dx = a2 ex / t, d2t/dx2 = (a2 - (dt/dx)^2) / t,
+// d2t/dxdy = -(dt/dx)(dt/dy) / t.  Across a 4 x 4 pixel block the dropped
+// third-order term is at most about 100 a2 |grad t| / t^2 cycles: 2e-10 for a
+// source 0.4 m away (pitch 1 um, lambda 633 nm), growing as 1 / z^2.
+struct RefBlock {
+  float phi, gx, gy, hxx, hyy, hxy;
+};
+__device__ __forceinline__ RefBlock ref_block(const RefDev& r, const RefAnchor& A, int dx, int dy) {
+  const float fx = (float)dx, fy = (float)dy;
+  const float m = fmaf(fx, fmaf(2.f, A.ex, fx), fy * fmaf(2.f, A.ey, fy));
+  const float am = r.a2f * m;
+  const float dt = am / (A.t0 + sqrtf(fmaf(A.t0, A.t0, am)));
+  const float ph = A.f0 + dt;
+  const float it = 1.0f / (A.t0 + dt);
+  const float ex = A.ex + fx, ey = A.ey + fy;
+  RefBlock B;
+  B.phi = ph - floorf(ph);
+  B.gx = r.a2f * ex * it;
+  B.gy = r.a2f * ey * it;
+  B.hxx = 0.5f * (r.a2f - B.gx * B.gx) * it;
+  B.hyy = 0.5f * (r.a2f - B.gy * B.gy) * it;
+  B.hxy = -B.gx * B.gy * it;
+  return B;
+}
+// Re(u conj R) at offset (i, j) from the block's pixel.
+__device__ __forceinline__ float ref_value(const RefBlock& B, float sgn, float2 u, int i, int j) {
+  const float fi = (float)i, fj = (float)j;
+  float ph = B.phi + fi * fmaf(B.hxx, fi, B.gx) + fj * fmaf(B.hyy, fj, B.gy) + B.hxy * (fi * fj);
+  ph -= rintf(ph);
+  float sn, cs;
+  __sincosf(6.28318530717958648f * ph, &sn, &cs);
+  return fmaf(u.x, cs, sgn * u.y * sn);
+}
+
 struct JobDev {
   const wasabi_point* pts;  // input points (n)
   wasabi_point* sorted;     // binned points (n), scratch
@@ -200,6 +266,9 @@ struct JobDev {
   int sp0;                  // first superposition item (super-tile) of this job
   int ncells;               // ncx * ncy
   float amax;               // largest |a| over the job's binned points (zeroed by zero_kernel)
+  int ox, oy;               // plane pixel of the hologram's pixel (0, 0) (sub-hologram origin)
+  int pad;
+  RefDev ref;               // reference wave of the bits
 };
 
 struct BatchDev {
@@ -242,6 +311,7 @@ struct SuperposeArgs {
   int reach;            // pixels
   int acc_float;        // 0: exact fixed-point accumulation, 1: FP32 atomics
   int re_only;          // 1: accumulate real parts only (every job wants bits alone)
+  int has_ref;          // 1: some job binarises against a spherical reference wave
   int rcap;             // LUT ranges per candidate batch (superpose_range_cap)
   int* status;
   int threads;          // block size
@@ -263,6 +333,8 @@ struct InverseArgs {
   int L;
   int* status;
   int num_sms;
+  int ox, oy;               // plane pixel of the output's pixel (0, 0)
+  RefDev ref;               // reference wave of the bits
 };
 cudaError_t launch_inverse(const InverseArgs& a, cudaStream_t s);
 // Strips of one hologram as the inverse kernel cuts it (256 pixels x 2^L rows).

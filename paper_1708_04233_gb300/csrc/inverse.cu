@@ -8,8 +8,11 @@
 // a 4 x 4 pixel block: the scaling value is carried down the levels it shares
 // with its neighbours, then the level-2 and level-1 steps fan out to 16 pixels
 // held in registers.  Output is either complex64 row-major (two 16-byte
-// streaming stores per row of the block) or packed bits (Re u > 0), gathered
-// across the warp with shuffles into 32-bit words.
+// streaming stores per row of the block) or packed bits (Re(u conj R) > 0
+// for the reference wave R, R = 1 by default), gathered across the warp with
+// shuffles into 32-bit words.  A spherical R is anchored once per strip (FP64
+// phase reduction by one thread, double-buffered in shared memory) and carried
+// to the pixels in FP32.
 //
 // The wavelet buffer is read exactly once and each output byte is written
 // once: the kernel is bound by HBM bandwidth.
@@ -83,12 +86,8 @@ __global__ void __launch_bounds__(InvCfg<L>::NT) inverse_kernel(const __grid_con
   const long long count = nitems > blockIdx.x ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   int* status = a.status;
   const int spr = (a.ntx + C::G - 1) / C::G;  // strips per tile row
-
-  if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
+  __shared__ RefAnchor s_anc[2];  // reference phase anchors of items i and i + 1
+  const bool ref = a.ref.kind != 0 && a.bits != nullptr;
 
   // Tile row and strip column of the CTA's i-th item.
   auto locate = [&](long long i, int* ty, int* sx) {
@@ -96,6 +95,19 @@ __global__ void __launch_bounds__(InvCfg<L>::NT) inverse_kernel(const __grid_con
     *ty = item / spr;
     *sx = item - *ty * spr;
   };
+  // Reference phase at the first pixel of the CTA's i-th strip.
+  auto anchor = [&](long long i) {
+    int ty, sx;
+    locate(i, &ty, &sx);
+    return ref_anchor(a.ref, (long long)a.ox + sx * 256, (long long)a.oy + (long long)ty * C::TS);
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (ref && count > 0) s_anc[0] = anchor(0);
+  }
+  __syncthreads();
 
   auto issue = [&](long long i, int stage) {  // warp 0 only
     int ty, sx;
@@ -195,12 +207,17 @@ __global__ void __launch_bounds__(InvCfg<L>::NT) inverse_kernel(const __grid_con
     if (bits != nullptr) {
       const int xend = min(w, sx * 256 + gv * C::TS);
       const int xw = sx * 256 + (wid & 1) * 128 + 32 * (lane >> 3);  // word's first pixel
+      RefBlock RB;
+      if (ref) RB = ref_block(a.ref, s_anc[i & 1], g * C::TS + 4 * bx, 4 * by);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         unsigned nib = 0;
         if (valid) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) nib |= (px[j][q].x > 0.f ? 1u : 0u) << q;
+          for (int q = 0; q < 4; ++q) {
+            const float v = ref ? ref_value(RB, a.ref.sgn, px[j][q], q, j) : px[j][q].x;
+            nib |= (v > 0.f ? 1u : 0u) << q;
+          }
         }
         unsigned v = nib << (4 * (lane & 7));
         v |= __shfl_xor_sync(0xffffffffu, v, 1);
@@ -217,6 +234,9 @@ __global__ void __launch_bounds__(InvCfg<L>::NT) inverse_kernel(const __grid_con
         }
       }
     }
+    // Item i + 1's anchor goes to the buffer item i - 1 used (every read of
+    // it ended before the previous barrier).
+    if (ref && tid == 0 && i + 1 < count) s_anc[(i + 1) & 1] = anchor(i + 1);
     __syncthreads();
     if (wid == 0 && i + kStages < count) issue(i + kStages, stage);
   }

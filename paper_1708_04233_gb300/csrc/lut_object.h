@@ -84,9 +84,17 @@ void superpose_config(const wasabi_lut* lut, int w, int h, int* cell, int* threa
 
 // wasabi_superpose / wasabi_hologram with an explicit configuration: any of
 // the wavelet buffer, the complex field and the packed bits may be written.
+// frame may be NULL (whole plane from pixel (0, 0), unit plane reference).
 wasabi_status superpose_impl(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n, int holo_w,
                              int holo_h, int rule, void* wbuf_dev, void* u_dev, uint8_t* bits_dev,
-                             void* scratch_dev, size_t scratch_bytes, cudaStream_t s, int cell, int threads);
+                             void* scratch_dev, size_t scratch_bytes, cudaStream_t s, int cell, int threads,
+                             const wasabi_frame* frame = nullptr);
+
+// Checks a frame (NULL = all zero) and converts it for the kernels: origin
+// and reference wave.  false (message in *why) for an invalid frame.
+bool frame_to_dev(const wasabi_frame* f, int* ox, int* oy, RefDev* ref, const char** why);
+// True when the frame's bits need the field's imaginary part (spherical R).
+inline bool frame_needs_complex(const wasabi_frame* f) { return f && f->ref.kind != WASABI_REF_PLANE; }
 
 bool device_info(int** status, int* sms);
 wasabi_status cuda_fail(const char* what, cudaError_t e);

@@ -258,6 +258,7 @@ void wasabi_server::run() {
         j.wbuf_dev = nullptr;
         j.u_dev = q->sz_u ? arena_base + q->off_u : nullptr;
         j.bits_dev = q->sz_bits ? reinterpret_cast<uint8_t*>(arena_base + q->off_bits) : nullptr;
+        j.frame = q->r.frame;
         if (q->r.n > 0)
           e = cudaMemcpyAsync(arena_base + q->off_pts, q->r.points_host, q->sz_pts, cudaMemcpyHostToDevice, s);
       }
@@ -367,6 +368,15 @@ wasabi_status wasabi_server_submit(wasabi_server* s, const wasabi_request* r, in
       (r->rule != WASABI_SHIFT_FLOOR && r->rule != WASABI_SHIFT_NEAREST)) {
     set_error("server_submit: holo_w, holo_h must be multiples of 2^L = %d (holo_w %% 8 == 0 for bits)", ts);
     return WASABI_E_INVALID;
+  }
+  {
+    int ox, oy;
+    RefDev ref;
+    const char* why = "";
+    if (!frame_to_dev(&r->frame, &ox, &oy, &ref, &why)) {
+      set_error("server_submit: %s", why);
+      return WASABI_E_INVALID;
+    }
   }
   // Depth indices are checked here, on the host, so that a bad request is
   // refused on its own instead of flagging the shared device status word.

@@ -185,11 +185,14 @@ __device__ __forceinline__ unsigned spread_nibbles(unsigned x) {
 // RE_ONLY (bits output alone): only real parts are read and transformed; the
 // inverse transform acts on real and imaginary parts separately, so Re u is
 // unchanged.  re_acc: the accumulator holds real parts only.
-template <int L, bool RE_ONLY>
+// REF: the bits are those of Re(u conj R) for the job's spherical reference
+// wave R; ref_a: R's phase anchor at the super-tile's first pixel.
+template <int L, bool RE_ONLY, bool REF>
 __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed, bool re_acc, float dq, int lmin, int k,
                                                   int kx, int ky, int Sx, int Sy, const JobDev& J,
                                                   const int* lvC, const int* lvG, const int* lvPS, int tid,
-                                                  int NT) {
+                                                  int NT, const RefAnchor* ref_a) {
+  static_assert(!(RE_ONLY && REF), "a reference wave needs the imaginary parts");
   if constexpr (L >= 2) {
     const int bpr = (k << L) >> 2;           // 4 x 4 blocks per super-tile row
     const int total = bpr * ((ky << L) >> 2);
@@ -201,6 +204,8 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
     const int X0 = Sx << L, Y0 = Sy << L;
     const int xend = (Sx + kx) << L;
     const int* acci = reinterpret_cast<const int*>(acc);
+    float rsg = 1.f;
+    if constexpr (REF) rsg = J.ref.sgn;
     // Coefficient of level l, band plane bi, at super-tile cell (cx, cy).
     auto coef = [&](int l, int bi, int cx, int cy) -> float2 {
       if (l < lmin) return make_float2(0.f, 0.f);
@@ -247,6 +252,8 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
       }
       const int x0 = X0 + px0;
       const int xw = X0 + 32 * (bcol >> 3);  // first pixel of this lane group's bit word
+      RefBlock RB;
+      if constexpr (REF) RB = ref_block(J.ref, *ref_a, px0, py0);  // anchor re-read from shared memory
       // One pixel row of the block: complex values, and its bit word (eight
       // lanes OR their nibbles into the word at xw).
       auto put_u = [&](int y, float2 p0, float2 p1, float2 p2, float2 p3) {
@@ -290,7 +297,14 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
           }
           put_u(y0 + 2 * ay, pa, pa, pb, pb);
           put_u(y0 + 2 * ay + 1, pa, pa, pb, pb);
-          if (bits != nullptr) {
+          if (REF && bits != nullptr) {
+#pragma unroll
+            for (int qy = 0; qy < 2; ++qy) {
+              const int j = 2 * ay + qy;
+              put_bits(y0 + j, word(ref_value(RB, rsg, pa, 0, j), ref_value(RB, rsg, pa, 1, j),
+                                    ref_value(RB, rsg, pb, 2, j), ref_value(RB, rsg, pb, 3, j)));
+            }
+          } else if (bits != nullptr) {
             // Both rows of the pair are equal, and each level-1 value covers
             // two neighbouring pixels: two warp votes give the signs of the
             // warp's 64 values; lane group q (8 lanes, 32 pixels) owns byte q
@@ -325,7 +339,13 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
 #pragma unroll
           for (int qy = 0; qy < 2; ++qy) {
             put_u(y0 + 2 * ay + qy, px[qy][0], px[qy][1], px[qy][2], px[qy][3]);
-            if (bits != nullptr) put_bits(y0 + 2 * ay + qy, word(px[qy][0].x, px[qy][1].x, px[qy][2].x, px[qy][3].x));
+            if (REF && bits != nullptr) {
+              const int j = 2 * ay + qy;
+              put_bits(y0 + j, word(ref_value(RB, rsg, px[qy][0], 0, j), ref_value(RB, rsg, px[qy][1], 1, j),
+                                    ref_value(RB, rsg, px[qy][2], 2, j), ref_value(RB, rsg, px[qy][3], 3, j)));
+            } else if (bits != nullptr) {
+              put_bits(y0 + 2 * ay + qy, word(px[qy][0].x, px[qy][1].x, px[qy][2].x, px[qy][3].x));
+            }
           }
         }
       }
@@ -334,14 +354,21 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
 }
 
 
-// RE: accumulate real parts only (every job of the launch wants bits alone).
-template <int L, int DT, bool RE>
+// Kernel modes: complex accumulation; real parts only (every job of the
+// launch wants bits alone with R = 1); complex accumulation with the
+// reference-wave epilogue compiled in (a launch where some job binarises
+// against a spherical R -- a kernel of its own, so that the other two keep
+// their register allocation).
+constexpr int kModeComplex = 0, kModeRe = 1, kModeRef = 2;
+
+template <int L, int DT, int MODE>
 __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
   constexpr int TSL = 1 << (2 * L);
   static_assert(TSL <= kRangeCap, "the write-out slot table lives in the range records");
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = a.cell;
   const int k = T >> L;
+  constexpr bool RE = MODE == kModeRe;
   constexpr bool re_acc = RE;
   const int rcap = a.rcap;
   const int P = survivor_cap(k, rcap);
@@ -357,6 +384,7 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
   // Per level l: index of the first super-tile cell past the guard, row
   // stride, plane size (see plane_code).
   __shared__ int lvC[8], lvG[8], lvPS[8];
+  __shared__ RefAnchor s_ref;  // reference-wave phase anchor of the current super-tile
 
   const LutView& lut = a.lut;
   const int NT = blockDim.x;
@@ -418,6 +446,8 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
     // offsets are loaded before the accumulator is zeroed, so the zeroing
     // covers the load latency.
     const int X0 = Sx << L, X1 = (Sx + kx) << L, Y0 = Sy << L, Y1 = (Sy + ky) << L;
+    if (MODE == kModeRef && tid == 0 && J.ref.kind != 0 && J.bits != nullptr)  // read after the syncs below
+      s_ref = ref_anchor(J.ref, (long long)J.ox + X0, (long long)J.oy + Y0);
     const int cx0 = max(0, floor_div(X0 - a.reach, a.cell));
     const int cx1 = min(ncx - 1, floor_div(X1 - 1 + a.reach, a.cell));
     const int cy0 = max(0, floor_div(Y0 - a.reach, a.cell));
@@ -667,10 +697,20 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
         __stcs(dst, make_float4(v[0], v[1], v[2], v[3]));
       }
     }
-    if (L >= 2 && J.u != nullptr)
-      supertile_inverse<L, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid, NT);
-    else if (L >= 2 && J.bits != nullptr)
-      supertile_inverse<L, true>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid, NT);
+    if constexpr (RE) {  // bits alone, plane reference (the host sends nothing else here)
+      if (L >= 2 && J.bits != nullptr)
+        supertile_inverse<L, true, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS,
+                                          tid, NT, nullptr);
+    } else if (MODE == kModeRef && L >= 2 && J.bits != nullptr && J.ref.kind != 0) {
+      supertile_inverse<L, false, MODE == kModeRef>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG,
+                                                    lvPS, tid, NT, &s_ref);
+    } else if (L >= 2 && J.u != nullptr) {
+      supertile_inverse<L, false, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS,
+                                         tid, NT, nullptr);
+    } else if (L >= 2 && J.bits != nullptr) {
+      supertile_inverse<L, true, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS,
+                                        tid, NT, nullptr);
+    }
     PT_MARK(5);
   }
 #ifdef WASABI_PHASE_TIMERS
@@ -679,27 +719,29 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
 #endif
 }
 
-template <int L, int DT, bool RE>
+template <int L, int DT, int MODE>
 cudaError_t launch_t(const SuperposeArgs& a, cudaStream_t s) {
-  const size_t smem = superpose_smem_bytes(a.cell, a.lut.L, a.lut.lmin, a.lut.D, RE, a.rcap);
-  cudaError_t e = cudaFuncSetAttribute(superpose_kernel<L, DT, RE>,
+  const size_t smem = superpose_smem_bytes(a.cell, a.lut.L, a.lut.lmin, a.lut.D, MODE == kModeRe, a.rcap);
+  cudaError_t e = cudaFuncSetAttribute(superpose_kernel<L, DT, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, superpose_kernel<L, DT, RE>, a.threads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, superpose_kernel<L, DT, MODE>, a.threads, smem);
   if (e != cudaSuccess) return e;
   // A fixed grid (independent of the batch, so the launch can be replayed
   // from a graph): CTAs without work exit at their first claim.
   const long long grid = (long long)a.grid * std::max(per_sm, 1);
-  superpose_kernel<L, DT, RE><<<(unsigned)grid, a.threads, smem, s>>>(a);
+  superpose_kernel<L, DT, MODE><<<(unsigned)grid, a.threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int L, int DT>
 cudaError_t launch_re(const SuperposeArgs& a, cudaStream_t s) {
   // Real-only accumulation serves the bits-only fused path (levels >= 2).
-  if (a.re_only) return L >= 2 ? launch_t<L, DT, (L >= 2)>(a, s) : cudaErrorInvalidValue;
-  return launch_t<L, DT, false>(a, s);
+  // The spherical-reference epilogue likewise (levels >= 2).
+  if (a.re_only) return L >= 2 ? launch_t<L, DT, (L >= 2 ? kModeRe : kModeComplex)>(a, s) : cudaErrorInvalidValue;
+  if (a.has_ref) return L >= 2 ? launch_t<L, DT, (L >= 2 ? kModeRef : kModeComplex)>(a, s) : cudaErrorInvalidValue;
+  return launch_t<L, DT, kModeComplex>(a, s);
 }
 
 template <int L>

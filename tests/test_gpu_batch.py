@@ -40,7 +40,7 @@ def test_batch_equals_single_calls(setup, orc, use_graph):
     batch = w.Batch(lut, 8, side_hint=512, use_graph=use_graph)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        res = batch.run([j for _, j in made], stream=stream)
+        res = batch.run([dict(j, keep_wbuf=True) for _, j in made], stream=stream)
     stream.synchronize()
     w.sync_status(stream)
     for (pts, j), r in zip(made, res):
@@ -68,7 +68,7 @@ def test_graph_replay_with_a_new_job_mix(setup, orc):
                                      (11, 90, 512, "bits", 0)]]):
         made = [_job(w, orc, *s) for s in specs]
         with torch.cuda.stream(stream):
-            res = batch.run([j for _, j in made], stream=stream)
+            res = batch.run([dict(j, keep_wbuf=True) for _, j in made], stream=stream)
         stream.synchronize()
         w.sync_status(stream)
         for (_, j), r in zip(made, res):
