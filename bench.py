@@ -209,6 +209,61 @@ def _time(torch, stream, fn, reps=5):
     return e0.elapsed_time(e1) / reps
 
 
+def reference_summary(w, torch, c, depths, pbuf, stream, units):
+    """The paper's reference wave (Sec. 2): a spherical wave from
+    (0, 30 mm, -400 mm) relative to the hologram centre, against the unit
+    plane reference of the headline, on the same points and LUT."""
+    lut = w.build_lut(c.lam, c.pitch, depths, c.W, c.L, c.gamma, dtype=c.lut_dtype, stream=stream)
+    n = pbuf.shape[0]
+    bits = torch.empty(c.Nh * c.Nh // 8, dtype=torch.uint8, device=pbuf.device)
+    scratch = torch.empty(w.scratch_bytes(lut, n, c.Nh, c.Nh), dtype=torch.uint8, device=pbuf.device)
+    ref = w.spherical_reference(c.lam, c.pitch, c.Nh / 2, c.Nh / 2 + 30e-3 / c.pitch, -0.4)
+
+    def run(r):
+        return lambda: w.hologram(lut, pbuf, c.Nh, c.Nh, want="bits", bits=bits, scratch=scratch, stream=stream,
+                                  reference=r)
+    ms_plane = _time(torch, stream, run(None), reps=3)
+    ms_ref = _time(torch, stream, run(ref), reps=3)
+    w.sync_status(stream)
+    lut.close()
+    return {"reference": "spherical, source at (0, 30 mm, -400 mm) from the hologram centre",
+            "hologram_ms": ms_ref, "plane_reference_hologram_ms": ms_plane,
+            "value": units / (ms_ref * 1e-3) / 1e6, "unit": UNIT,
+            "note": "complex accumulation (the imaginary parts enter Re(u conj R)) + per-pixel reference phase"}
+
+
+def streaming_summary(w, torch, dev, c, side: int, band_h: int, reps: int = 2):
+    """Sub-hologram streaming (Sec. 1, large-scale steps 2-4): a side^2
+    binarised hologram at the headline's point density, computed in bands of
+    band_h rows with each band's bits copied to pinned host memory while the
+    next band is computed (wasabi_hologram_stream; the call's wall time,
+    including its band-buffer allocations)."""
+    n = int(round(c.N * (side / c.Nh) ** 2))
+    pts = c.points(N=n, Nh=side)
+    cols = [torch.from_numpy(pts[k]).to(dev) for k in ("x", "y", "z", "a")]
+    pbuf = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    depths = w.depth_grid(c.zmin, c.zmax, c.D)
+    w.quantize_points(*cols, c.zmin, c.zmax, c.D, out=pbuf)
+    lut = w.build_lut(c.lam, c.pitch, depths, c.W, c.L, c.gamma, dtype=c.lut_dtype)
+    nr = lut.counts()
+    units = float(np.sum(nr[pbuf[:, 3].cpu().numpy().view(np.uint32)]))
+    del cols
+    bits = torch.empty(side * side // 8, dtype=torch.uint8).pin_memory()
+    w.hologram_stream(lut, pbuf, side, side, band_h, want="bits", bits=bits)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        w.hologram_stream(lut, pbuf, side, side, band_h, want="bits", bits=bits)
+    s = (time.perf_counter() - t0) / reps
+    w.sync_status()
+    lut.close()
+    return {"hologram": f"{side}x{side} binarised, {n} {c.cloud} points, bands of {band_h} rows "
+                        f"streamed to pinned host memory",
+            "s_per_hologram": s, "value": units / s / 1e6, "unit": UNIT,
+            "point_coeff": units, "host_bytes": side * side // 8,
+            "device_bytes_held": "two bands of bits + two binning scratches"}
+
+
 def direct_comparison(w, torch, dev, c, depths, pbuf, u_wasabi, stream, wasabi_step_ms):
     """C2: Eq. (1) summed directly on the GPU (aperture form) on the same
     points, its time against the WASABI step, and the WASABI approximation
@@ -531,6 +586,9 @@ def run_gpu(args, c):
             out["precision_forms"] = precision_forms(w, torch, dev, c, depths, pbuf, stream)
         if not args.no_serving and c.name == "C3":
             out["serving"] = serving_summary(w, torch, dev)
+        if c.name == "C3" and args.nh == 0 and not args.no_extras:
+            out["paper_reference_wave"] = reference_summary(w, torch, c, depths, pbuf, stream, units)
+            out["streaming"] = streaming_summary(w, torch, dev, c, args.stream_side, args.stream_band)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = oracle_sample(c, pts, os.cpu_count() or 1)
         print(json.dumps(out), flush=True)
@@ -554,6 +612,11 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the C5 serving-loop summary")
     ap.add_argument("--nh", type=int, default=0,
                     help="profiling cases: hologram side (points scaled by area, same density)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the spherical-reference and sub-hologram streaming summaries")
+    ap.add_argument("--stream-side", type=int, default=131072,
+                    help="side of the streamed hologram (points scaled by area)")
+    ap.add_argument("--stream-band", type=int, default=16384, help="rows per streamed band")
     ap.add_argument("--no-two-pass", action="store_true",
                     help="skip the secondary two-pass measurement (inverse kernel HBM fraction)")
     args = ap.parse_args()

@@ -263,6 +263,23 @@ wasabi_status wasabi_hologram_frame(const wasabi_lut* lut, const wasabi_point* p
                                     void* wbuf_dev, void* u_dev, uint8_t* bits_dev, void* scratch_dev,
                                     size_t scratch_bytes, void* stream);
 
+/* Sub-hologram streaming (Sec. 1, large-scale calculation, steps 2-4): the
+ * holo_w x holo_h hologram of the frame (may be NULL), computed as bands of
+ * band_h rows -- band k is the sub-hologram at (origin_x, origin_y + k band_h),
+ * fused as in wasabi_hologram_frame -- with each band's outputs copied into
+ * host memory while the next band is computed.  The device holds two bands
+ * (outputs and binning scratch), so the hologram is bounded by host memory.
+ * bits_host: packed bits of the whole hologram (holo_w % 8 == 0); u_host:
+ * complex64 row-major; at least one; pinned host memory makes the copies
+ * asynchronous.  band_h: a multiple of 2^L (the last band may be shorter).
+ * Work starts after what is queued on `stream`; the call returns when every
+ * band has been copied.  Allocates and frees its band buffers (device memory)
+ * and two streams per call.  Pixels equal the sub-holograms' (up to the
+ * rounding of a per-band fixed-point scale: each band is its own job). */
+wasabi_status wasabi_hologram_stream(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n,
+                                     int holo_w, int holo_h, int band_h, int rule, const wasabi_frame* frame,
+                                     uint8_t* bits_host, void* u_host, void* stream);
+
 /* ---- Batches: many holograms through one launch sequence (A10) ----------
  * One job = one hologram with its own points, wavelet buffer and outputs, all
  * sharing the LUT.  A batch runs every job through five launches (binning:

@@ -39,6 +39,7 @@ SIGNATURES = [
     ("wasabi_inverse_haar", _i, [_VP, _i, _i, _i, _VP, _VP, _VP]),
     ("wasabi_hologram_frame", _i, [_VP, _VP, _i64, _i, _i, _i, _VP, _VP, _VP, _VP, _VP, _sz, _VP]),
     ("wasabi_inverse_haar_frame", _i, [_VP, _i, _i, _i, _VP, _VP, _VP, _VP]),
+    ("wasabi_hologram_stream", _i, [_VP, _VP, _i64, _i, _i, _i, _i, _VP, _VP, _VP, _VP]),
     ("cgh_direct_scratch_bytes", _i, [_i64, _i, _i, C.POINTER(_sz)]),
     ("cgh_direct", _i, [_d, _d, _F64P, _i, _VP, _i64, _i, _i, _i, _VP, _VP, _sz, _VP]),
     ("wasabi_sync_status", _i, [_VP]),

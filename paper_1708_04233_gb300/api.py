@@ -237,6 +237,32 @@ def hologram(lut: Lut, points: torch.Tensor, w: int, h: int, want: str = "comple
     return u, bits
 
 
+def hologram_stream(lut: Lut, points: torch.Tensor, w: int, h: int, band_h: int, want: str = "bits",
+                    rule: int = 0, origin=(0, 0), reference: dict | None = None,
+                    bits: torch.Tensor | None = None, u: torch.Tensor | None = None, stream=None):
+    """Sub-hologram streaming (wasabi_hologram_stream): the w x h hologram
+    computed in bands of band_h rows, each copied to host memory while the
+    next is computed.  Outputs are host tensors (pinned when allocated here);
+    want = "bits" | "complex" | "both"."""
+    n = points.shape[0]
+    if want in ("bits", "both") and bits is None:
+        bits = torch.empty((h * w + 7) // 8, dtype=torch.uint8, pin_memory=True)
+    if want in ("complex", "both") and u is None:
+        u = torch.empty((h, w), dtype=torch.complex64, pin_memory=True)
+    for t in (bits, u):
+        if t is not None and (t.is_cuda or not t.is_contiguous()):
+            raise ValueError("hologram_stream: outputs are contiguous host tensors")
+    frame = make_frame(origin, reference)
+    host = [C.c_void_p(t.data_ptr()) if t is not None else None for t in (bits, u)]
+    check(_lib().wasabi_hologram_stream(lut.handle, _ptr(points) if n else C.c_void_p(None), n, w, h, band_h,
+                                        rule, C.byref(frame), host[0], host[1], _stream(stream)))
+    if want == "complex":
+        return u
+    if want == "bits":
+        return bits
+    return u, bits
+
+
 def cgh_direct_scratch_bytes(n: int, w: int, h: int) -> int:
     out = C.c_size_t()
     check(_lib().cgh_direct_scratch_bytes(n, w, h, C.byref(out)))

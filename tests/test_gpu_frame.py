@@ -201,3 +201,36 @@ def test_invalid_frames_are_refused(w, orc):
             w.inverse_haar(wb, 256, 256, 4, want="bits", reference=ref)
     w.sync_status()
     lut.close()
+
+
+@pytest.mark.parametrize("want,band_h", [("bits", 256), ("both", 192), ("complex", 4096)])
+def test_streamed_bands_equal_the_sub_holograms(w, orc, want, band_h):
+    """wasabi_hologram_stream: band k equals the one-call sub-hologram at
+    (origin_x, origin_y + k band_h) (each band is its own job, so its
+    fixed-point scale is its own: equal to rounding; bits up to flips at
+    |Re u| within rounding of zero); the last band is shorter."""
+    L, W, D = 4, 128, 8
+    lut, olut = _lut(w, orc, L, W, 0.1, D)
+    pts, p = _points(w, orc, 41, 3000, 1024, D)
+    wd, ht, origin = 768, 1008, (64, -32)
+    ref = w.spherical_reference(LAM, PITCH, 300.0, -20000.0, -0.4) if want == "both" else None
+    out = w.hologram_stream(lut, p, wd, ht, band_h, want=want, origin=origin, reference=ref)
+    w.sync_status()
+    u_s, bits_s = (out if want == "both" else (out, None) if want == "complex" else (None, out))
+    one_u, one_bits = w.hologram(lut, p, wd, ht, want="both", origin=origin, reference=ref)
+    one_u = one_u.cpu().numpy()
+    if u_s is not None:
+        assert not u_s.is_cuda and rel_l2(u_s.numpy(), one_u) <= 1e-6
+    if bits_s is not None:
+        assert not bits_s.is_cuda
+        if ref is None:
+            diff = _unpack(bits_s, ht, wd) != _unpack(one_bits, ht, wd)
+            assert np.all(np.abs(one_u.real[diff]) <= 1e-5 * np.abs(one_u).max())
+        else:
+            _check_ref_bits(orc, bits_s, one_u, ref, *origin)
+    # Against the oracle too: the streamed field is the sub-hologram's.
+    if u_s is not None:
+        N = 1024
+        u_or = _oracle_u(orc, olut, pts, N, L, *origin, 0)[:ht, :wd]
+        assert rel_l2(u_s.numpy(), u_or) <= 1e-5
+    lut.close()
