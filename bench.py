@@ -87,6 +87,9 @@ def _workload_desc(c):
             "Nh": c.Nh, "N": c.N, "lambda_m": c.lam, "pitch_m": c.pitch, "z_range_m": [c.zmin, c.zmax],
             "depths": c.D, "window": c.W, "levels": c.L, "keep_ratio": c.gamma, "output": c.output,
             "lut_dtype": c.lut_dtype,
+            "reference": (f"spherical, source ({c.reference[0] * 1e3:g} mm, {c.reference[1] * 1e3:g} mm, "
+                          f"{c.reference[2] * 1e3:g} mm) from the hologram centre" if c.reference
+                          else "unit plane wave"),
             "l2": (f"{'outputs larger than L2' if out_bytes > 129e6 else 'outputs NOT larger than L2'} "
                    f"({out_bytes / 1e9:.3g} GB written per step; "
                    f"{c.Nh * c.Nh * 8e-9:.3g} GB wavelet buffer in the two-pass form)")}
@@ -230,6 +233,47 @@ def reference_summary(w, torch, c, depths, pbuf, stream, units):
             "hologram_ms": ms_ref, "plane_reference_hologram_ms": ms_plane,
             "value": units / (ms_ref * 1e-3) / 1e6, "unit": UNIT,
             "note": "complex accumulation (the imaginary parts enter Re(u conj R)) + per-pixel reference phase"}
+
+
+def _reference_of(w, c):
+    """The workload's spherical reference wave in plane pixels (None: R = 1)."""
+    if not c.reference:
+        return None
+    dx, dy, z = c.reference
+    return w.spherical_reference(c.lam, c.pitch, c.Nh / 2 + dx / c.pitch, c.Nh / 2 + dy / c.pitch, z)
+
+
+def paper_setup_summary(w, torch, dev, reps: int = 3):
+    """The geometry of the paper's own experiment (workload P): LUT build
+    and the fused hologram with the spherical reference, timed apart."""
+    c = CONFIGS["P"]
+    pts = c.points()
+    cols = [torch.from_numpy(pts[k]).to(dev) for k in ("x", "y", "z", "a")]
+    pbuf = torch.empty((c.N, 4), dtype=torch.int32, device=dev)
+    w.quantize_points(*cols, c.zmin, c.zmax, c.D, out=pbuf)
+    depths = w.depth_grid(c.zmin, c.zmax, c.D)
+    stream = torch.cuda.Stream(device=dev)
+    ref = _reference_of(w, c)
+    bits = torch.empty(c.Nh * c.Nh // 8, dtype=torch.uint8, device=dev)
+    holder = {}
+
+    def build():
+        if "lut" in holder:
+            holder.pop("lut").close()
+        holder["lut"] = w.build_lut(c.lam, c.pitch, depths, c.W, c.L, c.gamma, stream=stream)
+    lut_ms = _time(torch, stream, build, reps=reps)
+    lut = holder["lut"]
+    scratch = torch.empty(w.scratch_bytes(lut, c.N, c.Nh, c.Nh), dtype=torch.uint8, device=dev)
+    holo_ms = _time(torch, stream, lambda: w.hologram(lut, pbuf, c.Nh, c.Nh, want="bits", bits=bits,
+                                                      scratch=scratch, stream=stream, reference=ref), reps=reps)
+    w.sync_status(stream)
+    nr = lut.counts()
+    units = float(np.sum(nr[pbuf[:, 3].cpu().numpy().view(np.uint32)]))
+    lut.close()
+    return {"workload": _workload_desc(c)["workload"], "reference": _workload_desc(c)["reference"],
+            "lut_ms": lut_ms, "hologram_ms": holo_ms, "step_ms": lut_ms + holo_ms,
+            "value": units / ((lut_ms + holo_ms) * 1e-3) / 1e6, "unit": UNIT, "point_coeff": units,
+            "paper_cpu_s": 354.0}
 
 
 def streaming_summary(w, torch, dev, c, side: int, band_h: int, reps: int = 2):
@@ -394,6 +438,7 @@ def run_gpu(args, c):
     out_dev = bits if want == "bits" else ufield
     stream = torch.cuda.Stream(device=dev)
     fused = args.path == "fused"
+    ref = _reference_of(w, c)
     wbuf = None if fused else torch.empty(c.Nh * c.Nh, dtype=torch.complex64, device=dev)
 
     ev = {k: [] for k in (("lut", "hologram") if fused else ("lut", "superpose", "inverse"))}
@@ -420,10 +465,10 @@ def run_gpu(args, c):
                             scratch=step.scratch, stream=stream)
                 mark()
                 w.inverse_haar(wb if wb is not None else wbuf, c.Nh, c.Nh, c.L, u=o_u, bits=o_b, want=want,
-                               stream=stream)
+                               stream=stream, reference=ref)
             else:
                 w.hologram(lut, pbuf, c.Nh, c.Nh, want=want, rule=0, u=o_u, bits=o_b, scratch=step.scratch,
-                           stream=stream)
+                           stream=stream, reference=ref)
             mark()
             if record:
                 step.marks.append(marks)
@@ -551,7 +596,7 @@ def run_gpu(args, c):
     # part -- the real part alone when only bits are produced (Re u depends
     # only on the real parts), real and imaginary parts otherwise.
     # Peak: one 32-bit access per bank per clock, 32 banks x 152 SMs x max SM clock.
-    parts = 1 if (fused and want == "bits") else 2
+    parts = 1 if (fused and want == "bits" and not c.reference) else 2
     smem_peak = 32 * 152 * 2070e6 / 1e9  # Gop/s
     ach = parts * units / (hot_ms * 1e-3) / 1e9
     roof = {"kernel": (f"superpose_kernel<{c.L},{c.lut_dtype}> with fused inverse"
@@ -589,7 +634,8 @@ def run_gpu(args, c):
         if c.name == "C3" and args.nh == 0 and not args.no_extras:
             out["paper_reference_wave"] = reference_summary(w, torch, c, depths, pbuf, stream, units)
             out["streaming"] = streaming_summary(w, torch, dev, c, args.stream_side, args.stream_band)
-        if not args.no_cpu_baseline:
+            out["paper_setup"] = paper_setup_summary(w, torch, dev)
+        if not args.no_cpu_baseline and c.name != "P":
             out["cpu_baseline"] = oracle_sample(c, pts, os.cpu_count() or 1)
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -603,9 +649,10 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wasabi", choices=["wasabi", "reference"])
-    ap.add_argument("--config", default="C3", choices=["C2", "C3", "C4"],
+    ap.add_argument("--config", default="C3", choices=["C2", "C3", "C4", "P"],
                     help="C3 (default): the 65536^2 binarised hologram; C2: 8192^2 complex field "
-                         "with direct Eq. (1) beside it; C4: C2 with the precision forms")
+                         "with direct Eq. (1) beside it; C4: C2 with the precision forms; P: the paper's own "
+                         "geometry (+-15 mm, 29 depths, spherical reference)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="fused", choices=["fused", "two-pass"],
                     help="fused: wasabi_hologram; two-pass: wasabi_superpose + wasabi_inverse_haar")

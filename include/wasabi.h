@@ -114,8 +114,10 @@ wasabi_status wasabi_quantize_points(const int32_t* x_dev, const int32_t* y_dev,
  * f = t - floor(t); cos/sin of 2 pi (float) f by quadrant reduction and
  * Taylor polynomials in FP32 with fused multiply-adds.
  * Requires 1 <= levels <= 5 (2 <= levels for the inverse), window a multiple
- * of 2^(levels+1) with window / 2^levels <= 512, 2 R(z_d) + 1 <= window for
- * every depth, s = lambda / (2 pitch) < 1, keep_ratio > 0, 1 <= n_depths <= 4096.
+ * of 2^(levels+1) with window <= 16384, window / 2^levels <= 2048 and
+ * n_depths (window / 2^levels)^2 < 2^31, 2 R(z_d) + 1 <= window for every
+ * depth, s = lambda / (2 pitch) < 1, keep_ratio > 0, 1 <= n_depths <= 4096.
+ * The build's temporary device memory is about 16 n_depths window^2 bytes.
  * dtype selects how superposition reads the values: FP32, or FP16 / BF16 with
  * one FP32 scale per 32 consecutive entries (scale = max |re|, |im| of the
  * block; stored value = value / scale, rounded to nearest).

@@ -317,9 +317,10 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
     set_error("build_lut: levels must be in [1, %d]", kMaxLevels);
     return WASABI_E_INVALID;
   }
-  if (window <= 0 || window % (2 << levels) != 0 || (window >> levels) > kMaxWindowTiles) {
-    set_error("build_lut: window must be a positive multiple of 2^(levels+1) with window/2^levels <= %d",
-              kMaxWindowTiles);
+  if (window <= 0 || window % (2 << levels) != 0 || window > kMaxWindow || (window >> levels) > kMaxWindowTiles ||
+      (long long)n_depths * ((long long)(window >> levels) * (window >> levels) + 1) > INT_MAX) {
+    set_error("build_lut: window must be a positive multiple of 2^(levels+1), at most %d, with "
+              "window/2^levels <= %d and n_depths * (window/2^levels)^2 < 2^31", kMaxWindow, kMaxWindowTiles);
     return WASABI_E_INVALID;
   }
   if (!(keep_ratio > 0)) { set_error("build_lut: keep_ratio must be > 0"); return WASABI_E_INVALID; }
@@ -588,7 +589,8 @@ wasabi_status read_depth(const wasabi_lut* lut, int depth, std::vector<uint32_t>
 }
 
 int32_t pos_to_mallat(const wasabi_lut* lut, uint32_t p) {
-  const int P = p & 4095, Q = (p >> 12) & 4095, lev = (p >> 24) & 7, band = (p >> 27) & 3;
+  int P, Q, lev, band;
+  unpack_pos(p, &P, &Q, &lev, &band);
   const int S = lut->W >> lev;
   const int row = Q + ((band == 2 || band == 3) ? S : 0);
   const int col = P + ((band == 1 || band == 3) ? S : 0);

@@ -5,9 +5,9 @@
 //    the pos/val arrays, ordered by window tile (row-major) and then by in-tile
 //    slot.  tile_off[d * (nwt*nwt + 1) + t] is the absolute index of window
 //    tile t's first entry; entry t + 1 is its end.
-//  * pos packs the coefficient's window sub-band position p:12 | q:12 (in
-//    units of its level) | level:3 | band:2 (see pack_pos); its window tile is
-//    (p >> (L - level), q >> (L - level)).
+//  * pos packs the coefficient's window sub-band position p:13 | q:13 (in
+//    units of its level; p, q < W / 2 <= 8192) | level:3 | band:2 (see
+//    pack_pos); its window tile is (p >> (L - level), q >> (L - level)).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,10 +19,20 @@ namespace wsb {
 
 constexpr int kMaxDepths = 4096;
 constexpr int kMaxLevels = 5;
-constexpr int kMaxWindowTiles = 512;  // window / 2^levels
+constexpr int kMaxWindowTiles = 2048;  // window / 2^levels
+constexpr int kMaxWindow = 16384;      // sub-band positions p, q < window / 2 fit 13 bits
+constexpr int kPosBits = 13;
+constexpr uint32_t kPosMask = (1u << kPosBits) - 1u;
 
 __host__ __device__ inline uint32_t pack_pos(int p, int q, int lev, int band) {
-  return (uint32_t)p | ((uint32_t)q << 12) | ((uint32_t)lev << 24) | ((uint32_t)band << 27);
+  return (uint32_t)p | ((uint32_t)q << kPosBits) | ((uint32_t)lev << (2 * kPosBits)) |
+         ((uint32_t)band << (2 * kPosBits + 3));
+}
+__host__ __device__ inline void unpack_pos(uint32_t pos, int* p, int* q, int* lev, int* band) {
+  *p = (int)(pos & kPosMask);
+  *q = (int)((pos >> kPosBits) & kPosMask);
+  *lev = (int)((pos >> (2 * kPosBits)) & 7u);
+  *band = (int)((pos >> (2 * kPosBits + 3)) & 3u);
 }
 
 // Superposition accumulator of one super-tile of k x k tiles (shared memory):
@@ -45,8 +55,8 @@ __host__ __device__ inline int plane_size(int k, int L, int l) {
 }
 __host__ __device__ inline int plane_count(int L, int l) { return l == L ? 4 : 3; }
 __host__ __device__ inline uint32_t plane_code(uint32_t pos, int L, int k) {
-  const int p = (int)(pos & 4095u), q = (int)((pos >> 12) & 4095u);
-  const int lev = (int)((pos >> 24) & 7u), band = (int)((pos >> 27) & 3u);
+  int p, q, lev, band;
+  unpack_pos(pos, &p, &q, &lev, &band);
   if (lev < 1 || lev > L) return 0;  // unused capacity: never visited
   const int bi = lev == L ? band : band - 1;
   return ((uint32_t)lev << 29) | (uint32_t)(bi * plane_size(k, L, lev) + q * plane_row(k, L, lev) + p);

@@ -337,9 +337,11 @@ __global__ void __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
     }
     return;
   }
-  // Ties at the exact key T = prefix: the rem lowest Mallat indices among them.
+  // Ties at the exact key T = prefix: the rem lowest Mallat indices among
+  // them, 12 bits per pass over the 32-bit index (windows above 4,096 pixels
+  // have indices beyond 2^24).
   unsigned iprefix = 0, ihi = 0;
-  for (int ishift = 12; ishift >= 0; ishift -= 12) {
+  for (int ishift = 24; ishift >= 0; ishift -= 12) {
     for (unsigned i = threadIdx.x; i < 4096; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     if (in_list) {

@@ -38,7 +38,7 @@
 namespace wsb {
 namespace {
 
-constexpr int kMaxCellRows = 128;
+constexpr int kMaxCellRows = 256;
 constexpr int kRangeCap = 2048;  // LUT ranges per batch (complex accumulation)
 constexpr int kRangeMax = 4096;  // LUT ranges per batch when only real parts are accumulated
 constexpr int kPerMax = 8;       // range slots per thread (block size >= 256)
@@ -465,11 +465,12 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
       s_rowpre[tid] = row_s1 - row_s0;
     }
     __syncthreads();
-    if (warp == 0) {  // exclusive prefix over <= 128 rows, 4 per lane
-      int v[4], loc = 0;
+    if (warp == 0) {  // exclusive prefix over <= kMaxCellRows rows, RPL per lane
+      constexpr int RPL = kMaxCellRows / 32;
+      int v[RPL], loc = 0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int r = 4 * lane + j;
+      for (int j = 0; j < RPL; ++j) {
+        const int r = RPL * lane + j;
         v[j] = r < ncrows ? s_rowpre[r] : 0;
         loc += v[j];
       }
@@ -481,8 +482,8 @@ __global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
       }
       int run = incl - loc;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int r = 4 * lane + j;
+      for (int j = 0; j < RPL; ++j) {
+        const int r = RPL * lane + j;
         if (r < ncrows) s_rowpre[r] = run;
         run += v[j];
       }

@@ -1,8 +1,12 @@
-"""The five measured workloads (sizes, optics and seeds) as plain data.
+"""The measured workloads (sizes, optics and seeds) as plain data.
 
 C1 small parity case; C2 8192^2 WASABI vs direct Eq. (1); C3 the paper-scale
 65536^2 binarised hologram; C4 the reduced-precision LUT form of C2; C5 the
-serving stream.  Lengths are in metres.
+serving stream; P the geometry of the paper's own experiment (Sec. 2: an
+image-type hologram of ~10^5 points from -15 mm to +15 mm in 29 depth bins,
+pitch 1 um, a spherical reference wave at (0, 30 mm, -400 mm), 65,536^2,
+binarised; the selectivity is not stated there, 1% is taken).  Lengths are in
+metres.
 """
 from __future__ import annotations
 
@@ -31,6 +35,9 @@ class Workload:
     seed: int
     output: str = "complex"   # "complex" | "bits"
     lut_dtype: str = "f32"
+    # Spherical reference wave: source offset (x, y) from the hologram centre
+    # and signed distance z, or None for the unit plane wave.
+    reference: tuple | None = None
 
     def points(self, N: int | None = None, Nh: int | None = None) -> dict:
         n = self.N if N is None else N
@@ -54,6 +61,10 @@ CONFIGS = {
                    "heightfield", 2, lut_dtype="f16s"),
     "C5": Workload("C5", 8192, 532e-9, 1e-6, 200_000, 0.3e-3, 1.0e-3, 64, 1024, 4, 0.02,
                    "heightfield", 5),
+    # W = 9664: the smallest multiple of 2^(L+1) holding 2 R + 1 at the
+    # outermost bin centre (|z| = 14.48 mm, R = 4830.5 px).
+    "P": Workload("P", 65536, 632.8e-9, 1e-6, 95_949, -15e-3, 15e-3, 29, 9664, 3, 0.01,
+                  "heightfield", 6, output="bits", reference=(0.0, 30e-3, -0.4)),
 }
 
 
