@@ -10,13 +10,16 @@
 //   psf_haar_kernel   one block per (bbox tile group, depth): PSF pixels, then
 //                     the tile's Haar levels in shared memory (FP32, fixed
 //                     operation order, no contraction) -> coef scratch, nnz
-//   select_kernel     one block per depth: exact top-N_r of key = re^2 + im^2
-//                     (FP64 bit patterns, MSB radix select), equal keys
-//                     resolved by Mallat index (radix select on the index)
+//   select_kernel     one cluster of 8 blocks per depth: exact top-N_r of
+//                     key = re^2 + im^2 (FP64 bit patterns, MSB radix select,
+//                     histograms summed over distributed shared memory),
+//                     equal keys resolved by Mallat index (radix select on
+//                     the index)
 //   tile_count_kernel one warp per window tile: kept count
 //   tile_scan_kernel  one block per depth: tile offsets (CSR)
 //   scatter_kernel    one warp per window tile: ordered compaction
 //   encode_kernel     one warp per 32 entries: FP16/BF16 + FP32 scale
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -205,56 +208,105 @@ __device__ unsigned block_excl_scan(unsigned v, unsigned* total) {
 constexpr int kModeGE = 0;   // keep key_bits >= T
 constexpr int kModeTie = 1;  // keep key_bits > T, or == T with Mallat index <= I*
 
-constexpr int kCandCap = 2048;  // candidates moved to shared memory
+constexpr int kCandCap = 2048;   // candidates moved to shared memory
+constexpr int kSelCluster = 8;   // CTAs per depth (one thread-block cluster)
+constexpr int kDigit = 11;       // bits per radix pass
+constexpr int kBins = 1 << kDigit;
 
-// One block per depth.  thr[2d] = T, thr[2d+1] = (mode << 32) | I*.
-// MSB-first radix select over the FP64 key bit patterns (keys are >= 0, so
-// their bit patterns order like the values), 11 bits per pass; once the
-// bucket holding the threshold has at most kCandCap members they are copied
-// to shared memory (with their Mallat indices) and the remaining passes run
-// there.  Equal keys at the threshold are resolved by a radix select on the
-// Mallat index (ascending).
-__global__ void __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
-  __shared__ unsigned hist[4096];
+// One thread-block cluster of kSelCluster CTAs per depth.  thr[2d] = T,
+// thr[2d+1] = (mode << 32) | I*.  MSB-first radix select over the FP64 key
+// bit patterns (keys are >= 0, so their bit patterns order like the values),
+// 11 bits per pass: each CTA histograms its share of the depth's window tiles
+// in its own shared memory, and every CTA sums the cluster's histograms
+// through distributed shared memory, so all of them take the same decision.
+// Once the bucket holding the threshold has at most kCandCap members, the
+// CTAs copy them (with their Mallat indices) into the first CTA's shared
+// memory and the others leave; the remaining passes run there.  Equal keys at
+// the threshold are resolved by a radix select on the 32-bit Mallat index
+// (ascending).
+__global__ void __cluster_dims__(kSelCluster, 1, 1) __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ unsigned hist[kBins];   // this CTA's counts (read by the whole cluster)
+  __shared__ unsigned tot[kBins];    // the cluster's sums
   __shared__ unsigned long long ckey[kCandCap];
   __shared__ unsigned cmi[kCandCap];
   __shared__ int s_found, s_nc;
   __shared__ unsigned s_cum;
-  const int d = blockIdx.x;
+  const int crank = (int)cluster.block_rank();
+  const bool leader = crank == 0;
+  const int d = blockIdx.x / kSelCluster;
   const DepthMeta md = a.meta[d];
   const int nb = md.thi - md.tlo + 1;
   const BoxIter it{md.tlo, nb, a.L, a.nwt};
   const int ntb = nb * nb, tsl = 1 << (2 * a.L);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int t0 = crank * nwarps + warp, tstride = kSelCluster * nwarps;  // this warp's tiles
   const unsigned long long* kd = a.keys + (long long)d * a.W * a.W;
   const long long nnz = (long long)a.nnz[d];
   const long long k = min(nnz, a.target_dev[d]);
-  if (threadIdx.x == 0) a.nr_dev[d] = k;
-  if (k == nnz || k <= 0) {
-    if (threadIdx.x == 0) {
+  if (leader && threadIdx.x == 0) a.nr_dev[d] = k;
+  if (k == nnz || k <= 0) {  // the same for every CTA of the cluster
+    if (leader && threadIdx.x == 0) {
       a.thr[2 * d] = k == nnz ? 1ull : ~0ull;  // 1: any nonzero key; ~0: none
       a.thr[2 * d + 1] = (unsigned long long)kModeGE << 32;
     }
     return;
   }
   auto fail = [&]() {  // counts inconsistent with nnz: keep nothing, report
-    if (threadIdx.x == 0) {
+    if (leader && threadIdx.x == 0) {
       a.thr[2 * d] = ~0ull;
       a.thr[2 * d + 1] = (unsigned long long)kModeGE << 32;
       a.nr_dev[d] = 0;
       atomicCAS(a.status, 0, WASABI_E_RANGE);
     }
   };
+  // Threads own kBins / 1024 consecutive bins each.
+  constexpr int BPT = kBins / 1024;
+  // After the counts of a pass are in hist (and, with `shared`, in every CTA
+  // of the cluster): the bin holding the rem-th element, counted from the top
+  // bin down (desc) or from bin 0 up; -1 if none.  tot receives the totals.
+  auto find_bin = [&](bool shared, bool desc, unsigned rem_) -> int {
+    if (shared) cluster.sync();  // every CTA's counts complete
+    unsigned v[BPT], local = 0;
+    const int t = desc ? 1023 - (int)threadIdx.x : (int)threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < BPT; ++j) {
+      const int b = BPT * t + j;
+      unsigned c = hist[b];
+      if (shared)
+        for (int r = 0; r < kSelCluster; ++r)
+          if (r != crank) c += cluster.map_shared_rank(hist, r)[b];
+      v[j] = c;
+      tot[b] = c;
+      local += c;
+    }
+    if (threadIdx.x == 0) s_found = -1;
+    unsigned cum = block_excl_scan(local, nullptr);
+#pragma unroll
+    for (int jj = 0; jj < BPT; ++jj) {
+      const int j = desc ? BPT - 1 - jj : jj;
+      if (cum < rem_ && rem_ <= cum + v[j]) { s_found = BPT * t + j; s_cum = cum; }
+      cum += v[j];
+    }
+    __syncthreads();
+    if (shared) cluster.sync();  // nobody zeroes hist while another CTA reads it
+    return s_found;
+  };
+  auto zero_hist = [&]() {
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+  };
+
   unsigned long long prefix = 0, hi_mask = 0;
   unsigned rem = (unsigned)k;
   int shift = 64, nc = 0;
   bool done = false, in_list = false;
   while (shift > 0 && !done) {
-    const int width = shift >= 11 ? 11 : shift;
+    const int width = shift >= kDigit ? kDigit : shift;
     shift -= width;
     const unsigned nbins = 1u << width;
-    for (unsigned i = threadIdx.x; i < nbins; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
+    zero_hist();
     if (in_list) {
       for (int i = threadIdx.x; i < nc; i += blockDim.x) {
         const unsigned long long kb = ckey[i];
@@ -262,7 +314,7 @@ __global__ void __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
       }
     } else {
       // Eight loads in flight per lane before any is used.
-      for (int ti = warp; ti < ntb; ti += nwarps) {
+      for (int ti = t0; ti < ntb; ti += tstride) {
         int tx, ty;
         it.tile(ti, &tx, &ty);
         const unsigned long long* kt = kd + it.coef_index(tx, ty, 0);
@@ -280,107 +332,84 @@ __global__ void __launch_bounds__(1024) select_kernel(LutBuildArgs a) {
       }
     }
     __syncthreads();
-    // Each thread owns 4 bins (threads 1023, 1022, ... own the top bins);
-    // suffix sums from the top find the bin holding the rem-th largest key.
-    const int t_rev = 1023 - threadIdx.x;
-    unsigned local = 0;
-    for (int j = 0; j < 4; ++j) {
-      const unsigned b = 4u * t_rev + j;
-      if (b < nbins) local += hist[b];
-    }
-    if (threadIdx.x == 0) s_found = -1;
-    unsigned cum = block_excl_scan(local, nullptr);
-    for (int j = 3; j >= 0; --j) {
-      const unsigned b = 4u * t_rev + j;
-      if (b >= nbins) continue;
-      const unsigned hb = hist[b];
-      if (cum < rem && rem <= cum + hb) { s_found = (int)b; s_cum = cum; }
-      cum += hb;
-    }
-    __syncthreads();
-    if (s_found < 0) { fail(); return; }
-    const unsigned bstar = (unsigned)s_found;
-    const unsigned cnt_b = hist[bstar];
+    // Bins above nbins are empty: counting from the top of kBins is the same.
+    const int found = find_bin(!in_list, true, rem);
+    if (found < 0) { fail(); return; }
+    const unsigned bstar = (unsigned)found;
+    const unsigned cnt_b = tot[bstar];
     rem -= s_cum;
     prefix |= (unsigned long long)bstar << shift;
     hi_mask |= (unsigned long long)(nbins - 1) << shift;
     if (cnt_b == rem) {
       done = true;
     } else if (!in_list && cnt_b <= (unsigned)kCandCap && shift > 0) {
-      if (threadIdx.x == 0) s_nc = 0;
-      __syncthreads();
-      for (int ti = warp; ti < ntb; ti += nwarps) {
+      // Gather the bucket into the first CTA's shared memory.
+      if (leader && threadIdx.x == 0) s_nc = 0;
+      cluster.sync();
+      int* nc0 = cluster.map_shared_rank(&s_nc, 0);
+      unsigned long long* ckey0 = cluster.map_shared_rank(ckey, 0);
+      unsigned* cmi0 = cluster.map_shared_rank(cmi, 0);
+      for (int ti = t0; ti < ntb; ti += tstride) {
         int tx, ty;
         it.tile(ti, &tx, &ty);
         const unsigned long long* kt = kd + it.coef_index(tx, ty, 0);
         for (int slot = lane; slot < tsl; slot += 32) {
           const unsigned long long kb = __ldg(&kt[slot]);
           if (kb != 0 && (kb & hi_mask) == prefix) {
-            const int i = atomicAdd(&s_nc, 1);
+            const int i = atomicAdd(nc0, 1);
             if (i < kCandCap) {
-              ckey[i] = kb;
-              cmi[i] = (unsigned)mallat_index(a.W, a.L, tx, ty, slot);
+              ckey0[i] = kb;
+              cmi0[i] = (unsigned)mallat_index(a.W, a.L, tx, ty, slot);
             }
           }
         }
       }
-      __syncthreads();
+      cluster.sync();  // the list is complete; only the first CTA goes on
+      if (!leader) return;
       nc = min(s_nc, kCandCap);
       in_list = true;
     }
     __syncthreads();
   }
   if (done) {
-    if (threadIdx.x == 0) {
+    if (leader && threadIdx.x == 0) {
       a.thr[2 * d] = prefix;
       a.thr[2 * d + 1] = (unsigned long long)kModeGE << 32;
     }
     return;
   }
   // Ties at the exact key T = prefix: the rem lowest Mallat indices among
-  // them, 12 bits per pass over the 32-bit index (windows above 4,096 pixels
-  // have indices beyond 2^24).
+  // them, 11 bits per pass over the 32-bit index.
   unsigned iprefix = 0, ihi = 0;
-  for (int ishift = 24; ishift >= 0; ishift -= 12) {
-    for (unsigned i = threadIdx.x; i < 4096; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
+  for (int ishift = 2 * kDigit; ishift >= 0; ishift -= kDigit) {
+    zero_hist();
     if (in_list) {
       for (int i = threadIdx.x; i < nc; i += blockDim.x) {
         if (ckey[i] != prefix) continue;
         const unsigned mi = cmi[i];
-        if ((mi & ihi) == iprefix) atomicAdd(&hist[(mi >> ishift) & 4095u], 1u);
+        if ((mi & ihi) == iprefix) atomicAdd(&hist[(mi >> ishift) & (kBins - 1)], 1u);
       }
     } else {
-      for (int ti = warp; ti < ntb; ti += nwarps) {
+      for (int ti = t0; ti < ntb; ti += tstride) {
         int tx, ty;
         it.tile(ti, &tx, &ty);
         const unsigned long long* kt = kd + it.coef_index(tx, ty, 0);
         for (int slot = lane; slot < tsl; slot += 32) {
           if (kt[slot] != prefix) continue;
           const unsigned mi = (unsigned)mallat_index(a.W, a.L, tx, ty, slot);
-          if ((mi & ihi) == iprefix) atomicAdd(&hist[(mi >> ishift) & 4095u], 1u);
+          if ((mi & ihi) == iprefix) atomicAdd(&hist[(mi >> ishift) & (kBins - 1)], 1u);
         }
       }
     }
     __syncthreads();
-    unsigned local = 0;
-    for (int j = 0; j < 4; ++j) local += hist[4 * threadIdx.x + j];
-    if (threadIdx.x == 0) s_found = -1;
-    unsigned cum = block_excl_scan(local, nullptr);
-    for (int j = 0; j < 4; ++j) {
-      const unsigned b = 4u * threadIdx.x + j;
-      const unsigned hb = hist[b];
-      if (cum < rem && rem <= cum + hb) { s_found = (int)b; s_cum = cum; }
-      cum += hb;
-    }
-    __syncthreads();
-    if (s_found < 0) { fail(); return; }
+    const int found = find_bin(!in_list, false, rem);
+    if (found < 0) { fail(); return; }
     rem -= s_cum;
-    iprefix |= (unsigned)s_found << ishift;
-    ihi |= 4095u << ishift;
+    iprefix |= (unsigned)found << ishift;
+    ihi |= (unsigned)(kBins - 1) << ishift;
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
+  if (leader && threadIdx.x == 0) {
     a.thr[2 * d] = prefix;
     a.thr[2 * d + 1] = ((unsigned long long)kModeTie << 32) | iprefix;
   }
@@ -555,7 +584,7 @@ cudaError_t launch_lut_build(const LutBuildArgs& a, cudaStream_t s) {
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
-  select_kernel<<<a.D, 1024, 0, s>>>(a);
+  select_kernel<<<a.D * kSelCluster, 1024, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int ntile = a.nwt * a.nwt;
   const dim3 tgrid((unsigned)((ntile + 7) / 8), (unsigned)a.D);
