@@ -320,9 +320,32 @@ def direct_comparison(w, torch, dev, c, depths, pbuf, u_wasabi, stream, wasabi_s
     w.sync_status(stream)
     diff = (u_wasabi.to(torch.complex128) - u_direct.to(torch.complex128)).abs().pow(2).sum().sqrt()
     ref = u_direct.to(torch.complex128).abs().pow(2).sum().sqrt()
+    # Numerical reconstruction of both fields at the middle depth (d = -z):
+    # how alike the images are (the paper compares reconstructions, Fig. 3).
+    zmid = float(depths[len(depths) // 2])
+    rec = {}
+    for name, u in (("wasabi", u_wasabi), ("eq1", u_direct)):
+        rec[name] = w.reconstruct(u, c.Nh, c.Nh, c.lam, c.pitch, -zmid, stream=stream).double()
+    rms = _time(torch, stream, lambda: w.reconstruct(u_wasabi, c.Nh, c.Nh, c.lam, c.pitch, -zmid, stream=stream),
+                reps=3)
+    a_, b_ = rec["wasabi"], rec["eq1"]
+
+    def corr_of(x, y):
+        x, y = x - x.mean(), y - y.mean()
+        return float((x * y).sum() / (x.norm() * y.norm()))
+    corr = corr_of(a_, b_)
+    # The shift rule moves each level's coefficients by less than 2^L pixels,
+    # so the refocused points of the two images sit up to 2^L - 1 pixels apart:
+    # compare them also on 2^L x 2^L blocks.
+    pool = lambda x: torch.nn.functional.avg_pool2d(x[None, None], 1 << c.L)[0, 0]
+    corr_pooled = corr_of(pool(a_), pool(b_))
     return {"kernel": "direct_kernel (Eq. (1), aperture form; FP64 phase reduction)", "ms": ms,
             "wasabi_step_ms": wasabi_step_ms, "speedup": ms / wasabi_step_ms,
-            "rel_l2_wasabi_vs_eq1": float(diff / ref)}
+            "rel_l2_wasabi_vs_eq1": float(diff / ref),
+            "reconstruction": {"d_m": -zmid, "ms": rms, "method": "angular spectrum (cuFFT C2C)",
+                               "intensity_correlation_wasabi_vs_eq1": corr,
+                               f"intensity_correlation_{1 << c.L}px_blocks": corr_pooled,
+                               "intensity_rel_l2_wasabi_vs_eq1": float((a_ - b_).norm() / b_.norm())}}
 
 
 def precision_forms(w, torch, dev, c, depths, pbuf, stream):

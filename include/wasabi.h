@@ -409,6 +409,31 @@ wasabi_status cgh_direct(double lambda, double pitch, const double* depths_host,
                          int aperture, void* u_dev, void* scratch_dev, size_t scratch_bytes,
                          void* stream);
 
+/* ---- Numerical reconstruction (NEXT-4) ----------------------------------
+ * The field of the plane at signed distance d from the hologram, by the
+ * angular spectrum method: U_d = IFFT2( FFT2(U_0) H ), with
+ * H(fx, fy) = exp(i 2 pi d sqrt(1/lambda^2 - fx^2 - fy^2)) for
+ * fx^2 + fy^2 < 1/lambda^2 and 0 for evanescent frequencies,
+ * fx = k / (w pitch), k in FFT order.  In the sign convention of the object
+ * points (Eq. (1) with a +i sign, reading R9), a point at depth z comes to
+ * focus at d = -z.  The transfer function's phase is reduced in FP64; the
+ * FFTs are cuFFT C2C transforms in FP32.
+ * input_kind WASABI_RECON_FIELD: input_dev is a complex64 field (w x h,
+ * row-major).  WASABI_RECON_BITS: input_dev is a packed binary hologram
+ * (w % 8 == 0), an amplitude transmittance t in {0, 1}, illuminated by the
+ * frame's reference wave: U_0 = t R (the frame may be NULL: R = 1, origin 0).
+ * Outputs (either may be NULL, not both): field_out_dev complex64 U_d,
+ * intensity_out_dev float |U_d|^2, both w x h row-major.
+ * scratch_dev: wasabi_reconstruct_scratch_bytes() bytes, 256-byte aligned.
+ * Synchronous: returns after the result is in place (the FFT plan lives
+ * only for the call). */
+typedef enum { WASABI_RECON_FIELD = 0, WASABI_RECON_BITS = 1 } wasabi_recon_input;
+wasabi_status wasabi_reconstruct_scratch_bytes(int w, int h, size_t* bytes_out);
+wasabi_status wasabi_reconstruct(const void* input_dev, int input_kind, int w, int h, double lambda, double pitch,
+                                 double d, const wasabi_frame* frame, void* field_out_dev,
+                                 float* intensity_out_dev, void* scratch_dev, size_t scratch_bytes,
+                                 void* stream);
+
 /* Synchronises `stream`, then returns and clears the current device's status
  * word: WASABI_OK, WASABI_E_RANGE or WASABI_E_TIMEOUT (E_CUDA if the stream
  * itself failed). */

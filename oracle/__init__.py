@@ -19,6 +19,8 @@ Functions and the passages they follow:
 * ``binarize``        — Sec. 2 (binary amplitude hologram; R7)
 * ``reference_wave`` / ``binarize_ref`` — Sec. 2 (spherical reference wave,
   bit = Re(u conj R) > 0; R12)
+* ``reconstruct``     — numerical reconstruction (Sec. 2, Fig. 3(b)): the
+  angular spectrum method, written with numpy's FFT (reading R13)
 * ``cgh_direct``      — Eq. (1)
 
 Parity pins live in ``tests/test_oracle_*.py``.  Functions without an
@@ -337,6 +339,26 @@ def binarize_ref(u: np.ndarray, lam: float, pitch: float, xr: float, yr: float, 
     lib().orc_binarize_ref_f64(_p(uf, _f64p), w, h, lam, pitch, xr, yr, zr, ox, oy, _p(bits, _u8p),
                                _p(val, _f64p))
     return bits, val
+
+
+def reconstruct(u0: np.ndarray, lam: float, pitch: float, d: float) -> np.ndarray:
+    """Reading R13: the field in the plane at signed distance d from the
+    field u0 (h x w) by the angular spectrum method, FP64:
+    U_d = IFFT2(FFT2(u0) H), H = exp(i 2 pi d sqrt(1/lam^2 - fx^2 - fy^2))
+    where fx^2 + fy^2 < 1/lam^2, 0 elsewhere; fx, fy the FFT frequencies of
+    the pitch grid.  A point at depth z (Eq. (1), +i sign) focuses at d = -z."""
+    h, w = u0.shape
+    fx = np.fft.fftfreq(w, d=pitch)[None, :]
+    fy = np.fft.fftfreq(h, d=pitch)[:, None]
+    s = 1.0 / lam ** 2 - fx ** 2 - fy ** 2
+    prop = s > 0
+    H = np.where(prop, np.exp(2j * np.pi * d * np.sqrt(np.where(prop, s, 0.0))), 0.0)
+    return np.fft.ifft2(np.fft.fft2(np.asarray(u0, np.complex128)) * H)
+
+
+def transmittance(bits: np.ndarray, w: int, h: int) -> np.ndarray:
+    """A packed binary hologram (R7 bit order) as amplitudes 0 / 1 (h x w)."""
+    return np.unpackbits(np.asarray(bits, np.uint8), bitorder="little")[: w * h].reshape(h, w).astype(np.float64)
 
 
 def cgh_direct(lam: float, pitch: float, x, y, a, z, ox: int, oy: int, w: int, h: int,

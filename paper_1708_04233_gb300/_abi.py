@@ -40,6 +40,8 @@ SIGNATURES = [
     ("wasabi_hologram_frame", _i, [_VP, _VP, _i64, _i, _i, _i, _VP, _VP, _VP, _VP, _VP, _sz, _VP]),
     ("wasabi_inverse_haar_frame", _i, [_VP, _i, _i, _i, _VP, _VP, _VP, _VP]),
     ("wasabi_hologram_stream", _i, [_VP, _VP, _i64, _i, _i, _i, _i, _VP, _VP, _VP, _VP]),
+    ("wasabi_reconstruct_scratch_bytes", _i, [_i, _i, C.POINTER(_sz)]),
+    ("wasabi_reconstruct", _i, [_VP, _i, _i, _i, _d, _d, _d, _VP, _VP, _VP, _VP, _sz, _VP]),
     ("cgh_direct_scratch_bytes", _i, [_i64, _i, _i, C.POINTER(_sz)]),
     ("cgh_direct", _i, [_d, _d, _F64P, _i, _VP, _i64, _i, _i, _i, _VP, _VP, _sz, _VP]),
     ("wasabi_sync_status", _i, [_VP]),
@@ -60,6 +62,7 @@ SIGNATURES = [
 
 
 REF_PLANE, REF_SPHERICAL = 0, 1
+RECON_FIELD, RECON_BITS = 0, 1
 
 
 class Reference(C.Structure):

@@ -263,6 +263,27 @@ def hologram_stream(lut: Lut, points: torch.Tensor, w: int, h: int, band_h: int,
     return u, bits
 
 
+def reconstruct(hologram: torch.Tensor, w: int, h: int, lam: float, pitch: float, d: float,
+                want: str = "intensity", origin=(0, 0), reference: dict | None = None,
+                out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Numerical reconstruction (wasabi_reconstruct): the field (want =
+    "complex") or intensity (want = "intensity") in the plane at signed
+    distance d, by the angular spectrum method.  hologram: an (h, w) complex64
+    field, or packed bits (uint8) illuminated by `reference` (None: R = 1)."""
+    kind = _abi.RECON_BITS if hologram.dtype == torch.uint8 else _abi.RECON_FIELD
+    dev = hologram.device
+    if out is None:
+        out = torch.empty((h, w), dtype=torch.complex64 if want == "complex" else torch.float32, device=dev)
+    need = C.c_size_t()
+    check(_lib().wasabi_reconstruct_scratch_bytes(w, h, C.byref(need)))
+    scratch = torch.empty(int(need.value), dtype=torch.uint8, device=dev)
+    frame = make_frame(origin, reference)
+    field, inten = (out, None) if want == "complex" else (None, out)
+    check(_lib().wasabi_reconstruct(_ptr(hologram), kind, w, h, lam, pitch, d, C.byref(frame), _ptr(field),
+                                    _ptr(inten), _ptr(scratch), scratch.numel(), _stream(stream)))
+    return out
+
+
 def cgh_direct_scratch_bytes(n: int, w: int, h: int) -> int:
     out = C.c_size_t()
     check(_lib().cgh_direct_scratch_bytes(n, w, h, C.byref(out)))

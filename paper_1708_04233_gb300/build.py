@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, log in results:
             f.write(log)
     tmp = LIB + f".tmp{os.getpid()}"
-    res = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]],
+    res = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcufft"],
                          capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError("link failed:\n" + res.stderr)
