@@ -12,6 +12,8 @@ Functions and the passages they follow:
 * ``depth_grid`` / ``quantize`` — Sec. 1, step 1 and Sec. 2 (Delta z; R2)
 * ``psf_f32`` / ``psf_f64`` — Sec. 1, step 1 (u_z = exp(ikr) circ(...))
 * ``haar_fwd`` / ``haar_inv`` — Sec. 1, steps 1 and 3 (FWT; Haar, R4)
+* ``wavelet_fwd`` / ``wavelet_inv`` / ``coif1_taps`` — the same steps with the
+  paper's coiflets (order 1, periodic filter banks; R14)
 * ``select``          — Sec. 1, step 1 ("N_r strong coefficients"; R5)
 * ``build_lut``       — Sec. 1, step 1 for all depths
 * ``superpose``       — Eq. (2) with the shift rule R6
@@ -70,6 +72,10 @@ def lib():
     for nm, t in (("orc_haar_fwd_f32", _f32p), ("orc_haar_inv_f32", _f32p),
                   ("orc_haar_fwd_f64", _f64p), ("orc_haar_inv_f64", _f64p)):
         getattr(L, nm).argtypes = [t, C.c_int64, C.c_int]
+    for nm, t in (("orc_wavelet_fwd_f32", _f32p), ("orc_wavelet_inv_f32", _f32p),
+                  ("orc_wavelet_fwd_f64", _f64p), ("orc_wavelet_inv_f64", _f64p)):
+        getattr(L, nm).argtypes = [t, C.c_int64, C.c_int, C.c_int]
+    L.orc_coif1_taps.argtypes = [_f64p, _f64p]
     L.orc_mallat_decode.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int,
                                     C.POINTER(C.c_int), C.POINTER(C.c_int), _i64p, _i64p]
     L.orc_select_f32.restype = C.c_int64
@@ -81,7 +87,8 @@ def lib():
         f.restype = C.c_int
         f.argtypes = [C.c_double, C.c_double, _f64p, C.c_int, C.c_int, C.c_int,
                       C.c_double, _i64p, C.c_int64, _i32p, t, C.c_int]
-    L.orc_build_lut_f64.argtypes = L.orc_build_lut_f64.argtypes + [C.c_int]
+    L.orc_build_lut_f32.argtypes = L.orc_build_lut_f32.argtypes + [C.c_int]
+    L.orc_build_lut_f64.argtypes = L.orc_build_lut_f64.argtypes + [C.c_int, C.c_int]
     for nm, t in (("orc_superpose_f32", _f32p), ("orc_superpose_f64", _f64p)):
         f = getattr(L, nm)
         f.restype = C.c_int
@@ -93,7 +100,7 @@ def lib():
         f.restype = C.c_int
         f.argtypes = [C.c_int, C.c_int, C.c_int, _i64p, _i32p, t, _i32p, _i32p,
                       _f32p, _u32p, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
-                      C.c_int, t]
+                      C.c_int, t, C.c_int]
     L.orc_binarize_f32.argtypes = [_f32p, C.c_int64, C.c_int64, _u8p]
     L.orc_reference_wave.argtypes = [C.c_double] * 5 + [C.c_int64] * 4 + [_f64p]
     L.orc_binarize_ref_f64.argtypes = ([_f64p, C.c_int64, C.c_int64] + [C.c_double] * 5 +
@@ -186,6 +193,42 @@ def haar_inv(a: np.ndarray, L: int) -> np.ndarray:
     return out
 
 
+WAVELETS = {"haar": 0, "coif1": 1}
+
+
+def coif1_taps() -> tuple[np.ndarray, np.ndarray]:
+    """Reading R14: the order-1 coiflet scaling filter h_k and wavelet
+    filter g_k = (-1)^k h_{1-k}, k = -2 .. 3 (FP64)."""
+    lo, hi = np.empty(6), np.empty(6)
+    lib().orc_coif1_taps(_p(lo, _f64p), _p(hi, _f64p))
+    return lo, hi
+
+
+def _wavelet_call(a: np.ndarray, L: int, wavelet: str, fwd: bool) -> np.ndarray:
+    out = np.array(a, copy=True, order="C")
+    n = out.shape[0]
+    assert out.shape == (n, n)
+    w = WAVELETS[wavelet]
+    if out.dtype == np.complex64:
+        fn = lib().orc_wavelet_fwd_f32 if fwd else lib().orc_wavelet_inv_f32
+        fn(_p(out, _f32p), n, L, w)
+    else:
+        out = out.astype(np.complex128)
+        fn = lib().orc_wavelet_fwd_f64 if fwd else lib().orc_wavelet_inv_f64
+        fn(_p(out, _f64p), n, L, w)
+    return out
+
+
+def wavelet_fwd(a: np.ndarray, L: int, wavelet: str = "haar") -> np.ndarray:
+    """L-level forward transform (Mallat layout): Haar (R4) or the periodic
+    order-1 coiflet (R14)."""
+    return _wavelet_call(a, L, wavelet, True)
+
+
+def wavelet_inv(a: np.ndarray, L: int, wavelet: str = "haar") -> np.ndarray:
+    return _wavelet_call(a, L, wavelet, False)
+
+
 def mallat_decode(row: int, col: int, n: int, L: int) -> tuple[int, int, int, int]:
     lev, band = C.c_int(), C.c_int()
     p, q = C.c_int64(), C.c_int64()
@@ -220,6 +263,7 @@ class Lut:
     nr: np.ndarray          # (D,) int64
     idx: np.ndarray         # (sum nr,) int32, Mallat linear index, ascending per depth
     val: np.ndarray         # (sum nr,) complex64 or complex128
+    wavelet: str = "haar"
 
     @property
     def offsets(self) -> np.ndarray:
@@ -231,8 +275,9 @@ class Lut:
 
 
 def build_lut(lam, pitch, depths, W, L, gamma, dtype="f32", threads=1,
-              select_fp32=False) -> Lut:
-    """Sec. 1, step 1 at every depth.  dtype 'f32' uses the FP32 PSF form
+              select_fp32=False, wavelet="haar") -> Lut:
+    """Sec. 1, step 1 at every depth, with the Haar (R4) or the order-1
+    coiflet (R14) transform.  dtype 'f32' uses the FP32 PSF form
     (reading R8) that decides the selection; 'f64' is the FP64 definition.
     With select_fp32 (f64 only) the kept index set is the one the FP32 form
     selects and the values are FP64: the reference for precision errors,
@@ -250,17 +295,17 @@ def build_lut(lam, pitch, depths, W, L, gamma, dtype="f32", threads=1,
         val = np.empty(max(cap, 1), np.complex64)
         rc = lib().orc_build_lut_f32(lam, pitch, _p(depths, _f64p), D, W, L, gamma,
                                      _p(nr, _i64p), cap, _p(idx, _i32p),
-                                     _p(val, _f32p), threads)
+                                     _p(val, _f32p), threads, WAVELETS[wavelet])
     else:
         val = np.empty(max(cap, 1), np.complex128)
         rc = lib().orc_build_lut_f64(lam, pitch, _p(depths, _f64p), D, W, L, gamma,
                                      _p(nr, _i64p), cap, _p(idx, _i32p),
-                                     _p(val, _f64p), threads, int(select_fp32))
+                                     _p(val, _f64p), threads, int(select_fp32), WAVELETS[wavelet])
     if rc != 0:
         raise ValueError("oracle build_lut rejected its arguments (window too "
                          "small for a PSF, or capacity)")
     tot = int(nr.sum())
-    return Lut(lam, pitch, depths, W, L, gamma, nr, idx[:tot].copy(), val[:tot].copy())
+    return Lut(lam, pitch, depths, W, L, gamma, nr, idx[:tot].copy(), val[:tot].copy(), wavelet)
 
 
 # ---------------------------------------------------------- superposition
@@ -299,7 +344,7 @@ def subhologram(lut: Lut, points, Ns: int, s: int, t: int, rule: int = 0) -> np.
     tp = _f64p if f64 else _f32p
     rc = fn(lut.W, lut.L, lut.nr.size, _p(lut.nr, _i64p), _p(lut.idx, _i32p),
             _p(lut.val, tp), _p(x, _i32p), _p(y, _i32p), _p(a, _f32p), _p(d, _u32p),
-            x.size, Ns, s, t, rule, _p(u, tp))
+            x.size, Ns, s, t, rule, _p(u, tp), WAVELETS[lut.wavelet])
     if rc != 0:
         raise ValueError("oracle subhologram: a point's depth index is out of range")
     return u

@@ -43,6 +43,12 @@
 //      r = sqrt(n p^2 + z^2), t = r / lambda.
 //   R9 Eq. (1) has no 1/r factor and a +i sign, as printed; a_j is used as an
 //      amplitude.
+//   R14 coiflet wavelet (Sec. 1 uses coiflets at level 3; the order is not
+//      stated): order 1, the 6-tap orthonormal filter below (coif1_taps),
+//      periodic filter banks on the W x W window and on the N_h x N_h buffer,
+//      the same Mallat layout and sub-band letters as R4 (analysis along x
+//      first), the same shift rule R6.  FP32 analysis in a fixed order: the
+//      k = -2 product, then fused multiply-adds for k = -1 .. 3.
 //   R12 reference wave (Sec. 2, a spherical wave from (x_r, y_r, z_r)): the
 //      wave of a unit point source in the object points' convention (R9,
 //      R11), R = exp(i sgn(z_r) 2 pi r / lambda),
@@ -282,6 +288,127 @@ void haar_inv(T* a, int64_t n, int L) {
   for (int l = L; l >= 1; --l) haar_inv_level(a, n, n >> (l - 1), tmp);
 }
 
+// ------------------------------------------------------------ coiflet (R14) --
+
+// Order-1 coiflet: the scaling filter h_k (k = -2 .. 3) solves
+//   sum_k h_k = sqrt 2,  sum_k h_k h_{k+2m} = delta_m (m = 0, 1, 2),
+//   sum_k (-1)^k k h_k = 0  (with the zeroth moment: two vanishing wavelet
+//   moments),  sum_k k h_k = 0  (a vanishing first scaling moment).
+// Of its two real roots this is the one whose largest tap is h_0:
+//   h / sqrt 2 = ((1 - r)/32, (5 + r)/32, (7 + r)/16, (7 - r)/16, (1 - r)/32,
+//                (r - 3)/32),  r = sqrt 7.
+// The wavelet filter is g_k = (-1)^k h_{1-k}, on the same support.
+void coif1_taps(double lo[6], double hi[6]) {
+  const double r = std::sqrt(7.0), s2 = std::sqrt(2.0);
+  lo[0] = s2 * (1.0 - r) / 32.0;
+  lo[1] = s2 * (5.0 + r) / 32.0;
+  lo[2] = s2 * (7.0 + r) / 16.0;
+  lo[3] = s2 * (7.0 - r) / 16.0;
+  lo[4] = s2 * (1.0 - r) / 32.0;
+  lo[5] = s2 * (r - 3.0) / 32.0;
+  for (int i = 0; i < 6; ++i) {
+    const int k = i - 2;         // tap index
+    const int j = (1 - k) + 2;   // array slot of h_{1-k}
+    hi[i] = (k % 2 != 0 ? -1.0 : 1.0) * lo[j];
+  }
+}
+
+int64_t pmod(int64_t a, int64_t n) { return ((a % n) + n) % n; }
+
+// One periodic analysis level on the top-left S x S block of an n x n
+// interleaved complex array: along x (each row: low half, then high half),
+// then along y (each column: low half on top).  Sum order per output: the
+// k = -2 product, then fused multiply-adds for k = -1 .. 3.
+template <typename T>
+void coif_fwd_level(T* a, int64_t n, int64_t S, const T* lo, const T* hi, std::vector<T>& tmp) {
+  const int64_t h = S / 2;
+  tmp.assign((size_t)(2 * S * S), T(0));
+  for (int64_t r = 0; r < S; ++r)
+    for (int64_t m = 0; m < h; ++m)
+      for (int c = 0; c < 2; ++c) {
+        T x = a[2 * (r * n + pmod(2 * m - 2, S)) + c];
+        T sl = lo[0] * x, sh = hi[0] * x;
+        for (int i = 1; i < 6; ++i) {
+          x = a[2 * (r * n + pmod(2 * m + i - 2, S)) + c];
+          sl = std::fma(lo[i], x, sl);
+          sh = std::fma(hi[i], x, sh);
+        }
+        tmp[(size_t)(2 * (r * S + m) + c)] = sl;
+        tmp[(size_t)(2 * (r * S + h + m) + c)] = sh;
+      }
+  for (int64_t col = 0; col < S; ++col)
+    for (int64_t m = 0; m < h; ++m)
+      for (int c = 0; c < 2; ++c) {
+        T x = tmp[(size_t)(2 * (pmod(2 * m - 2, S) * S + col) + c)];
+        T sl = lo[0] * x, sh = hi[0] * x;
+        for (int i = 1; i < 6; ++i) {
+          x = tmp[(size_t)(2 * (pmod(2 * m + i - 2, S) * S + col) + c)];
+          sl = std::fma(lo[i], x, sl);
+          sh = std::fma(hi[i], x, sh);
+        }
+        a[2 * (m * n + col) + c] = sl;
+        a[2 * ((h + m) * n + col) + c] = sh;
+      }
+}
+
+// The transpose of coif_fwd_level (its inverse, the filters being
+// orthonormal): along y, then along x; sample j receives
+// h_k s[m] + g_k d[m] for every k = j - 2m (mod S), k = -2 .. 3.
+template <typename T>
+void coif_inv_level(T* a, int64_t n, int64_t S, const T* lo, const T* hi, std::vector<T>& tmp) {
+  const int64_t h = S / 2;
+  tmp.assign((size_t)(2 * S * S), T(0));
+  for (int64_t col = 0; col < S; ++col)
+    for (int64_t j = 0; j < S; ++j)
+      for (int c = 0; c < 2; ++c) {
+        T acc = T(0);
+        for (int i = 0; i < 6; ++i) {
+          const int k = i - 2;
+          if (((j - k) % 2 + 2) % 2 != 0) continue;
+          const int64_t m = pmod((j - k) / 2, h);
+          acc = std::fma(lo[i], a[2 * (m * n + col) + c], acc);
+          acc = std::fma(hi[i], a[2 * ((h + m) * n + col) + c], acc);
+        }
+        tmp[(size_t)(2 * (j * S + col) + c)] = acc;
+      }
+  for (int64_t r = 0; r < S; ++r)
+    for (int64_t j = 0; j < S; ++j)
+      for (int c = 0; c < 2; ++c) {
+        T acc = T(0);
+        for (int i = 0; i < 6; ++i) {
+          const int k = i - 2;
+          if (((j - k) % 2 + 2) % 2 != 0) continue;
+          const int64_t m = pmod((j - k) / 2, h);
+          acc = std::fma(lo[i], tmp[(size_t)(2 * (r * S + m) + c)], acc);
+          acc = std::fma(hi[i], tmp[(size_t)(2 * (r * S + h + m) + c)], acc);
+        }
+        a[2 * (r * n + j) + c] = acc;
+      }
+}
+
+// Forward / inverse L-level transform, in place: wavelet 0 = Haar (R4),
+// 1 = order-1 coiflet (R14).
+template <typename T>
+void wavelet_fwd(T* a, int64_t n, int L, int wavelet) {
+  if (wavelet == 0) { haar_fwd(a, n, L); return; }
+  double lo[6], hi[6];
+  coif1_taps(lo, hi);
+  T lt[6], ht[6];
+  for (int i = 0; i < 6; ++i) { lt[i] = (T)lo[i]; ht[i] = (T)hi[i]; }
+  std::vector<T> tmp;
+  for (int l = 1; l <= L; ++l) coif_fwd_level(a, n, n >> (l - 1), lt, ht, tmp);
+}
+template <typename T>
+void wavelet_inv(T* a, int64_t n, int L, int wavelet) {
+  if (wavelet == 0) { haar_inv(a, n, L); return; }
+  double lo[6], hi[6];
+  coif1_taps(lo, hi);
+  T lt[6], ht[6];
+  for (int i = 0; i < 6; ++i) { lt[i] = (T)lo[i]; ht[i] = (T)hi[i]; }
+  std::vector<T> tmp;
+  for (int l = L; l >= 1; --l) coif_inv_level(a, n, n >> (l - 1), lt, ht, tmp);
+}
+
 // Position of Mallat entry (row, col) of an n x n, L-level transform:
 // level l (1..L), band 0 = scaling (l = L only), 1 = LH, 2 = HL, 3 = HH,
 // sub-band coordinates p (x, column) and q (y, row).  Fig. 2(a).
@@ -350,7 +477,7 @@ int64_t select_strong(const T* coef, int W, double gamma, double R,
 template <typename T>
 int build_lut(double lambda, double pitch, const double* zd, int D, int W,
               int L, double gamma, int64_t* nr, int64_t cap, int32_t* idx,
-              T* val, int threads, bool fp32_psf, bool select_fp32 = false) {
+              T* val, int threads, bool fp32_psf, bool select_fp32, int wavelet) {
   const int64_t n = (int64_t)W * W;
   std::vector<std::vector<int32_t>> sel((size_t)D);
   std::vector<std::vector<T>> vals((size_t)D);
@@ -371,7 +498,7 @@ int build_lut(double lambda, double pitch, const double* zd, int D, int W,
       psf_f64(lambda, pitch, zd[d], W, tmp.data());
       for (int64_t i = 0; i < 2 * n; ++i) coef[(size_t)i] = (T)tmp[(size_t)i];
     }
-    haar_fwd(coef.data(), W, L);
+    wavelet_fwd(coef.data(), W, L, wavelet);
     std::vector<int32_t> kept((size_t)n);
     int64_t k;
     if (!fp32_psf && select_fp32) {
@@ -380,7 +507,7 @@ int build_lut(double lambda, double pitch, const double* zd, int D, int W,
       // values.
       std::vector<float> c32((size_t)(2 * n));
       psf_f32(lambda, pitch, zd[d], W, c32.data());
-      haar_fwd(c32.data(), W, L);
+      wavelet_fwd(c32.data(), W, L, wavelet);
       k = select_strong(c32.data(), W, gamma, R, kept.data());
     } else {
       k = select_strong(coef.data(), W, gamma, R, kept.data());
@@ -551,6 +678,11 @@ void orc_psf_f64(double lambda, double pitch, double z, int W, double* out) {
 }
 
 void orc_haar_fwd_f32(float* a, int64_t n, int L) { haar_fwd(a, n, L); }
+void orc_wavelet_fwd_f32(float* a, int64_t n, int L, int w) { wavelet_fwd(a, n, L, w); }
+void orc_wavelet_inv_f32(float* a, int64_t n, int L, int w) { wavelet_inv(a, n, L, w); }
+void orc_wavelet_fwd_f64(double* a, int64_t n, int L, int w) { wavelet_fwd(a, n, L, w); }
+void orc_wavelet_inv_f64(double* a, int64_t n, int L, int w) { wavelet_inv(a, n, L, w); }
+void orc_coif1_taps(double* lo, double* hi) { coif1_taps(lo, hi); }
 void orc_haar_inv_f32(float* a, int64_t n, int L) { haar_inv(a, n, L); }
 void orc_haar_fwd_f64(double* a, int64_t n, int L) { haar_fwd(a, n, L); }
 void orc_haar_inv_f64(double* a, int64_t n, int L) { haar_inv(a, n, L); }
@@ -571,16 +703,17 @@ int64_t orc_select_f64(const double* coef, int W, double gamma, double R,
 
 int orc_build_lut_f32(double lambda, double pitch, const double* zd, int D,
                       int W, int L, double gamma, int64_t* nr, int64_t cap,
-                      int32_t* idx, float* val, int threads) {
+                      int32_t* idx, float* val, int threads, int wavelet) {
   return build_lut<float>(lambda, pitch, zd, D, W, L, gamma, nr, cap, idx, val,
-                          threads, true);
+                          threads, true, false, wavelet);
 }
 // select_fp32 != 0: FP64 values at the indices the FP32 path selects.
 int orc_build_lut_f64(double lambda, double pitch, const double* zd, int D,
                       int W, int L, double gamma, int64_t* nr, int64_t cap,
-                      int32_t* idx, double* val, int threads, int select_fp32) {
+                      int32_t* idx, double* val, int threads, int select_fp32,
+                      int wavelet) {
   return build_lut<double>(lambda, pitch, zd, D, W, L, gamma, nr, cap, idx,
-                           val, threads, false, select_fp32 != 0);
+                           val, threads, false, select_fp32 != 0, wavelet);
 }
 
 int orc_superpose_f32(int W, int L, int D, const int64_t* nr, const int32_t* idx,
@@ -605,24 +738,24 @@ int orc_subhologram_f32(int W, int L, int D, const int64_t* nr,
                         const int32_t* idx, const float* val, const int32_t* x,
                         const int32_t* y, const float* a, const uint32_t* d,
                         int64_t N, int64_t Ns, int64_t s, int64_t t, int rule,
-                        float* u_sub) {
+                        float* u_sub, int wavelet) {
   std::memset(u_sub, 0, sizeof(float) * 2 * Ns * Ns);
   const int rc = superpose<float>(W, L, D, nr, idx, val, x, y, a, d, N, Ns,
                                   s * Ns, t * Ns, rule, u_sub);
   if (rc) return rc;
-  haar_inv(u_sub, Ns, L);
+  wavelet_inv(u_sub, Ns, L, wavelet);
   return 0;
 }
 int orc_subhologram_f64(int W, int L, int D, const int64_t* nr,
                         const int32_t* idx, const double* val, const int32_t* x,
                         const int32_t* y, const float* a, const uint32_t* d,
                         int64_t N, int64_t Ns, int64_t s, int64_t t, int rule,
-                        double* u_sub) {
+                        double* u_sub, int wavelet) {
   std::memset(u_sub, 0, sizeof(double) * 2 * Ns * Ns);
   const int rc = superpose<double>(W, L, D, nr, idx, val, x, y, a, d, N, Ns,
                                    s * Ns, t * Ns, rule, u_sub);
   if (rc) return rc;
-  haar_inv(u_sub, Ns, L);
+  wavelet_inv(u_sub, Ns, L, wavelet);
   return 0;
 }
 
