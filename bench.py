@@ -339,6 +339,7 @@ def direct_comparison(w, torch, dev, c, depths, pbuf, u_wasabi, stream, wasabi_s
     # compare them also on 2^L x 2^L blocks.
     pool = lambda x: torch.nn.functional.avg_pool2d(x[None, None], 1 << c.L)[0, 0]
     corr_pooled = corr_of(pool(a_), pool(b_))
+    direct_comparison.u_direct = u_direct
     return {"kernel": "direct_kernel (Eq. (1), aperture form; FP64 phase reduction)", "ms": ms,
             "wasabi_step_ms": wasabi_step_ms, "speedup": ms / wasabi_step_ms,
             "rel_l2_wasabi_vs_eq1": float(diff / ref),
@@ -346,6 +347,42 @@ def direct_comparison(w, torch, dev, c, depths, pbuf, u_wasabi, stream, wasabi_s
                                "intensity_correlation_wasabi_vs_eq1": corr,
                                f"intensity_correlation_{1 << c.L}px_blocks": corr_pooled,
                                "intensity_rel_l2_wasabi_vs_eq1": float((a_ - b_).norm() / b_.norm())}}
+
+
+def coiflet_summary(w, torch, dev, c, depths, pbuf, stream, u_direct, units_haar):
+    """The paper's wavelet family (order-1 coiflet, periodic) on the same
+    workload: LUT build, superposition into the tile-major buffer, the
+    separable periodic inverse, and the WASABI-vs-Eq. (1) error beside
+    Haar's.  The inverse's HBM fraction counts its algorithmic bytes (8 B
+    read + 8 B written per pixel) against its time."""
+    holder = {}
+
+    def build():
+        if "lut" in holder:
+            holder.pop("lut").close()
+        holder["lut"] = w.build_lut(c.lam, c.pitch, depths, c.W, c.L, c.gamma, stream=stream, wavelet="coif1")
+    lut_ms = _time(torch, stream, build, reps=3)
+    lut = holder["lut"]
+    n = pbuf.shape[0]
+    wb = torch.empty(c.Nh * c.Nh, dtype=torch.complex64, device=dev)
+    u = torch.empty((c.Nh, c.Nh), dtype=torch.complex64, device=dev)
+    scratch = torch.empty(w.scratch_bytes(lut, n, c.Nh, c.Nh), dtype=torch.uint8, device=dev)
+    sup_ms = _time(torch, stream, lambda: w.superpose(lut, pbuf, c.Nh, c.Nh, wbuf=wb, scratch=scratch, stream=stream),
+                   reps=5)
+    inv_ms = _time(torch, stream, lambda: w.inverse_wavelet(wb, c.Nh, c.Nh, c.L, "coif1", u=u, stream=stream), reps=5)
+    w.sync_status(stream)
+    nr = lut.counts()
+    units = float(np.sum(nr[pbuf[:, 3].cpu().numpy().view(np.uint32)]))
+    lut.close()
+    err = float((u.to(torch.complex128) - u_direct.to(torch.complex128)).norm() / u_direct.to(torch.complex128).norm())
+    peak, peak_kind = _peaks()
+    inv_gbs = 16.0 * c.Nh * c.Nh / (inv_ms * 1e-3) / 1e9
+    return {"wavelet": "coif1 (order-1 coiflet, 6 taps, periodic)", "lut_ms": lut_ms, "superpose_ms": sup_ms,
+            "inverse_ms": inv_ms, "step_ms": lut_ms + sup_ms + inv_ms, "point_coeff": units,
+            "point_coeff_haar": units_haar, "value": units / ((lut_ms + sup_ms + inv_ms) * 1e-3) / 1e6,
+            "unit": UNIT, "rel_l2_vs_eq1": err,
+            "inverse_hbm": {"algorithmic_bytes": 16 * c.Nh * c.Nh, "gbs": inv_gbs, "frac": inv_gbs / peak,
+                            "peak": peak, "peak_source": peak_kind}}
 
 
 def precision_forms(w, torch, dev, c, depths, pbuf, stream):
@@ -650,6 +687,8 @@ def run_gpu(args, c):
                "clocks": clk.summary()}
         if c.name == "C2":
             out["direct_eq1"] = direct_comparison(w, torch, dev, c, depths, pbuf, out_dev, stream, ms)
+            out["coiflet"] = coiflet_summary(w, torch, dev, c, depths, pbuf, stream, direct_comparison.u_direct,
+                                             units)
         if c.name == "C4":
             out["precision_forms"] = precision_forms(w, torch, dev, c, depths, pbuf, stream)
         if not args.no_serving and c.name == "C3":

@@ -75,6 +75,7 @@ typedef struct {
 typedef struct wasabi_lut wasabi_lut; /* opaque, library-owned, device-resident */
 
 typedef enum { WASABI_F32 = 0, WASABI_F16S = 1, WASABI_BF16S = 2 } wasabi_lut_dtype;
+typedef enum { WASABI_HAAR = 0, WASABI_COIF1 = 1 } wasabi_wavelet;
 typedef enum { WASABI_SHIFT_FLOOR = 0, WASABI_SHIFT_NEAREST = 1 } wasabi_shift_rule;
 
 /* Thread-local description of the last failure on this thread ("" if none). */
@@ -128,6 +129,25 @@ wasabi_status wasabi_quantize_points(const int32_t* x_dev, const int32_t* y_dev,
 wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths_host,
                                int n_depths, int window, int levels, double keep_ratio,
                                int dtype, void* stream, wasabi_lut** out);
+
+/* wasabi_build_lut with a choice of wavelet (Sec. 1 uses coiflets at level 3,
+ * order unstated).  WASABI_HAAR: as above.  WASABI_COIF1: the order-1 coiflet,
+ * 6-tap orthonormal filters h_k (k = -2 .. 3) with
+ * h / sqrt 2 = ((1 - r)/32, (5 + r)/32, (7 + r)/16, (7 - r)/16, (1 - r)/32, (r - 3)/32),
+ * r = sqrt 7 (the solution of the coiflet equations whose largest tap is h_0),
+ * wavelet filter g_k = (-1)^k h_{1-k}; periodic filter banks on the W x W
+ * window, analysis along x then y per level, the Haar layout and letters
+ * (Mallat, LH = high along x).  Its filters overlap window tiles, so the
+ * whole window is transformed (PSF written out over W^2, analysis passes in
+ * FP32 in a fixed order: the k = -2 product, then fused multiply-adds for
+ * k = -1 .. 3), every window tile may hold kept coefficients and the
+ * superposition reach is W/2 + 2^(L+1).  A coiflet LUT superposes into the
+ * tile-major buffer with wasabi_superpose; its inverse is
+ * wasabi_inverse_wavelet (the fused wasabi_hologram is Haar's alone).
+ * Temporary device memory: about 24 n_depths W^2 bytes. */
+wasabi_status wasabi_build_lut_wavelet(double lambda, double pitch, const double* depths_host,
+                                       int n_depths, int window, int levels, double keep_ratio,
+                                       int dtype, int wavelet, void* stream, wasabi_lut** out);
 
 /* Releases a LUT (stream-ordered on the stream it was built on). */
 wasabi_status wasabi_lut_destroy(wasabi_lut* lut);
@@ -240,6 +260,21 @@ wasabi_status wasabi_inverse_haar(const void* wbuf_dev, int holo_w, int holo_h, 
 wasabi_status wasabi_inverse_haar_frame(const void* wbuf_dev, int holo_w, int holo_h, int levels,
                                         const wasabi_frame* frame, void* u_dev, uint8_t* bits_dev,
                                         void* stream);
+
+/* Inverse transformation for either wavelet of wasabi_build_lut_wavelet:
+ * WASABI_HAAR runs wasabi_inverse_haar_frame (scratch unused); WASABI_COIF1
+ * permutes the tile-major buffer into the Mallat layout and runs L periodic
+ * synthesis levels over the holo_w x holo_h buffer (along y, then x, the
+ * transpose of the analysis), then writes u and/or the bits against the
+ * frame's reference (phase of a spherical R reduced in FP64 per pixel).
+ * 1 <= levels <= 5; COIF1 needs a square hologram (holo_w == holo_h, the
+ * periodic transform's domain), side a multiple of 2^levels (and of 8 for bits).
+ * scratch_dev: wasabi_inverse_wavelet_scratch_bytes() bytes (two buffers
+ * of holo_w holo_h complex64), 256-byte aligned. */
+wasabi_status wasabi_inverse_wavelet_scratch_bytes(int holo_w, int holo_h, size_t* bytes_out);
+wasabi_status wasabi_inverse_wavelet(const void* wbuf_dev, int holo_w, int holo_h, int levels, int wavelet,
+                                     const wasabi_frame* frame, void* u_dev, uint8_t* bits_dev,
+                                     void* scratch_dev, size_t scratch_bytes, void* stream);
 
 /* A4 + A5 + A6 + A7 in one pass: superposition (Eq. (2)) fused with the
  * inverse transformation (Sec. 1, step 3) and binarisation (Sec. 2).  Each

@@ -28,6 +28,7 @@ SIGNATURES = [
     ("wasabi_depth_grid", _i, [_d, _d, _i, _F64P]),
     ("wasabi_quantize_points", _i, [_VP, _VP, _VP, _VP, _i64, _d, _d, _i, _VP, _VP]),
     ("wasabi_build_lut", _i, [_d, _d, _F64P, _i, _i, _i, _d, _i, _VP, C.POINTER(_VP)]),
+    ("wasabi_build_lut_wavelet", _i, [_d, _d, _F64P, _i, _i, _i, _d, _i, _i, _VP, C.POINTER(_VP)]),
     ("wasabi_lut_destroy", _i, [_VP]),
     ("wasabi_lut_counts", _i, [_VP, _I64P]),
     ("wasabi_lut_selection", _i, [_VP, _i, _I32P, _I64P]),
@@ -41,6 +42,8 @@ SIGNATURES = [
     ("wasabi_inverse_haar_frame", _i, [_VP, _i, _i, _i, _VP, _VP, _VP, _VP]),
     ("wasabi_hologram_stream", _i, [_VP, _VP, _i64, _i, _i, _i, _i, _VP, _VP, _VP, _VP]),
     ("wasabi_reconstruct_scratch_bytes", _i, [_i, _i, C.POINTER(_sz)]),
+    ("wasabi_inverse_wavelet_scratch_bytes", _i, [_i, _i, C.POINTER(_sz)]),
+    ("wasabi_inverse_wavelet", _i, [_VP, _i, _i, _i, _i, _VP, _VP, _VP, _VP, _sz, _VP]),
     ("wasabi_reconstruct", _i, [_VP, _i, _i, _i, _d, _d, _d, _VP, _VP, _VP, _VP, _sz, _VP]),
     ("cgh_direct_scratch_bytes", _i, [_i64, _i, _i, C.POINTER(_sz)]),
     ("cgh_direct", _i, [_d, _d, _F64P, _i, _VP, _i64, _i, _i, _i, _VP, _VP, _sz, _VP]),
@@ -63,6 +66,7 @@ SIGNATURES = [
 
 REF_PLANE, REF_SPHERICAL = 0, 1
 RECON_FIELD, RECON_BITS = 0, 1
+WAVELETS = {"haar": 0, "coif1": 1}
 
 
 class Reference(C.Structure):

@@ -45,6 +45,7 @@ class Lut:
         self.lam, self.pitch = lam, pitch
         self.depths = np.asarray(depths, np.float64)
         self.window, self.levels, self.keep_ratio, self.dtype = window, levels, keep_ratio, dtype
+        self.wavelet = "haar"
         self._stream = stream
 
     @property
@@ -91,13 +92,17 @@ class Lut:
 
 
 def build_lut(lam: float, pitch: float, depths, window: int, levels: int, keep_ratio: float,
-              dtype: str = "f32", stream=None) -> Lut:
+              dtype: str = "f32", stream=None, wavelet: str = "haar") -> Lut:
+    """The per-depth LUT (wasabi_build_lut_wavelet); wavelet "haar" or
+    "coif1" (the order-1 coiflet)."""
     d = np.ascontiguousarray(depths, np.float64)
     h = C.c_void_p()
-    check(_lib().wasabi_build_lut(lam, pitch, d.ctypes.data_as(C.POINTER(C.c_double)), d.size,
-                                  window, levels, keep_ratio, _DTYPES[dtype], _stream(stream),
-                                  C.byref(h)))
-    return Lut(h, lam, pitch, d, window, levels, keep_ratio, dtype, stream)
+    check(_lib().wasabi_build_lut_wavelet(lam, pitch, d.ctypes.data_as(C.POINTER(C.c_double)), d.size,
+                                          window, levels, keep_ratio, _DTYPES[dtype], _abi.WAVELETS[wavelet],
+                                          _stream(stream), C.byref(h)))
+    lut = Lut(h, lam, pitch, d, window, levels, keep_ratio, dtype, stream)
+    lut.wavelet = wavelet
+    return lut
 
 
 def pack_points(x, y, a, d, device="cuda") -> torch.Tensor:
@@ -163,6 +168,29 @@ def superpose_static(lut: Lut, points: torch.Tensor, w: int, h: int, rule: int =
     check(_lib().wasabi_superpose_static(lut.handle, _ptr(points) if n else C.c_void_p(None), n, w,
                                          h, rule, _ptr(wbuf), _stream(stream)))
     return wbuf
+
+
+def inverse_wavelet(wbuf: torch.Tensor, w: int, h: int, levels: int, wavelet: str = "coif1",
+                    want: str = "complex", u: torch.Tensor | None = None, bits: torch.Tensor | None = None,
+                    origin=(0, 0), reference: dict | None = None, stream=None):
+    """Inverse transformation of a tile-major wavelet buffer for either
+    wavelet (wasabi_inverse_wavelet): want = "complex" | "bits" | "both"."""
+    dev = wbuf.device
+    if want in ("complex", "both") and u is None:
+        u = torch.empty((h, w), dtype=torch.complex64, device=dev)
+    if want in ("bits", "both") and bits is None:
+        bits = torch.empty((h * w + 7) // 8, dtype=torch.uint8, device=dev)
+    need = C.c_size_t()
+    check(_lib().wasabi_inverse_wavelet_scratch_bytes(w, h, C.byref(need)))
+    scratch = torch.empty(int(need.value), dtype=torch.uint8, device=dev)
+    frame = make_frame(origin, reference)
+    check(_lib().wasabi_inverse_wavelet(_ptr(wbuf), w, h, levels, _abi.WAVELETS[wavelet], C.byref(frame), _ptr(u),
+                                        _ptr(bits), _ptr(scratch), scratch.numel(), _stream(stream)))
+    if want == "complex":
+        return u
+    if want == "bits":
+        return bits
+    return u, bits
 
 
 def spherical_reference(lam: float, pitch: float, x: float, y: float, z: float) -> dict:

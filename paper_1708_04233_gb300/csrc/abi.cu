@@ -303,7 +303,16 @@ wasabi_status wasabi_quantize_points(const int32_t* x_dev, const int32_t* y_dev,
 wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths_host, int n_depths,
                                int window, int levels, double keep_ratio, int dtype, void* stream,
                                wasabi_lut** out) {
+  return wasabi_build_lut_wavelet(lambda, pitch, depths_host, n_depths, window, levels, keep_ratio, dtype,
+                                  WASABI_HAAR, stream, out);
+}
+
+wasabi_status wasabi_build_lut_wavelet(double lambda, double pitch, const double* depths_host, int n_depths,
+                                       int window, int levels, double keep_ratio, int dtype, int wavelet,
+                                       void* stream, wasabi_lut** out) {
   if (!out) { set_error("build_lut: out is NULL"); return WASABI_E_INVALID; }
+  if (wavelet != WASABI_HAAR && wavelet != WASABI_COIF1) { set_error("build_lut: unknown wavelet %d", wavelet); return WASABI_E_INVALID; }
+  const bool coif = wavelet == WASABI_COIF1;
   *out = nullptr;
   if (!(lambda > 0) || !(pitch > 0) || !(lambda / (2.0 * pitch) < 1.0)) {
     set_error("build_lut: need lambda > 0, pitch > 0 and lambda / (2 pitch) < 1");
@@ -355,8 +364,10 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
     const int fr = (int)std::floor(R);
     max_fr = std::max(max_fr, fr);
     DepthMeta m;
-    m.tlo = std::max(0, (window / 2 - fr) >> levels);
-    m.thi = std::min(lut->nwt - 1, (window / 2 + fr) >> levels);
+    // Haar coefficients stay in the tiles the disk meets; coiflet filters
+    // spread over the periodic window, so every tile is searched.
+    m.tlo = coif ? 0 : std::max(0, (window / 2 - fr) >> levels);
+    m.thi = coif ? lut->nwt - 1 : std::min(lut->nwt - 1, (window / 2 + fr) >> levels);
     const int nb = m.thi - m.tlo + 1;
     max_nb = std::max(max_nb, nb);
     const long long box = (long long)nb * nb * TSL;
@@ -376,7 +387,8 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   }
   if (base > INT_MAX) { delete lut; set_error("build_lut: table too large"); return WASABI_E_INVALID; }
   lut->total_cap = base;
-  lut->reach = max_fr + (2 << levels);
+  lut->reach = (coif ? window / 2 : max_fr) + (2 << levels);
+  lut->wavelet = wavelet;
   const int ntpd = 2 * lut->nwt * (lut->nwt + 1);  // per depth: rows x segments x (tiles + 1)
   const cudaStream_t s = (cudaStream_t)stream;
   int* status;
@@ -429,6 +441,7 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   sc.take<double>((size_t)n_depths);
   sc.take<int>((size_t)n_depths + 1);
   sc.take<long long>((size_t)n_depths);
+  if (coif) sc.take<float2>((size_t)n_depths * window * window);  // coiflet image
   void* scratch = nullptr;
   e = cudaMallocAsync(&scratch, align_up(sc.off, 256), s);
   if (e != cudaSuccess) {
@@ -453,6 +466,13 @@ wasabi_status wasabi_build_lut(double lambda, double pitch, const double* depths
   double* c_dev = sc.take<double>((size_t)n_depths);
   int* blk0_dev = sc.take<int>((size_t)n_depths + 1);
   long long* target_dev = sc.take<long long>((size_t)n_depths);
+  a.wavelet = wavelet;
+  a.img = coif ? sc.take<float2>((size_t)n_depths * window * window) : nullptr;
+  {
+    double lo[6], hi[6];
+    coif1_filters(lo, hi);
+    for (int i = 0; i < 6; ++i) { a.ctap_lo[i] = (float)lo[i]; a.ctap_hi[i] = (float)hi[i]; }
+  }
   a.z_dev = z_dev; a.R2_dev = R2_dev; a.target_dev = target_dev; a.c_dev = c_dev;
   // Phase constants of reading R8 (plain IEEE double operations).
   const double pl = pitch / lambda;
@@ -720,6 +740,10 @@ wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* poi
   if (!frame_to_dev(frame, &fox, &foy, &fref, &why)) { set_error("hologram: %s", why); return WASABI_E_INVALID; }
   if ((u_dev || bits_dev) && lut->L < 2) {
     set_error("hologram: the fused inverse needs levels >= 2");
+    return WASABI_E_INVALID;
+  }
+  if ((u_dev || bits_dev) && lut->wavelet != WASABI_HAAR) {
+    set_error("hologram: the fused inverse is Haar's; use wasabi_superpose + wasabi_inverse_wavelet");
     return WASABI_E_INVALID;
   }
   if (bits_dev && holo_w % 8) { set_error("hologram: bits output needs holo_w %% 8 == 0"); return WASABI_E_INVALID; }

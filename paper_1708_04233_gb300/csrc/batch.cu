@@ -57,6 +57,10 @@ wasabi_status check_job(const wasabi_lut* lut, const wasabi_job& j, int idx) {
     set_error("batch: job %d has bad arguments", idx);
     return WASABI_E_INVALID;
   }
+  if ((j.u_dev || j.bits_dev) && lut->wavelet != WASABI_HAAR) {
+    set_error("batch: job %d asks for the fused inverse, which is Haar's", idx);
+    return WASABI_E_INVALID;
+  }
   if ((j.u_dev || j.bits_dev) && lut->L < 2) {
     set_error("batch: job %d asks for an inverse, which needs levels >= 2", idx);
     return WASABI_E_INVALID;

@@ -159,8 +159,19 @@ struct LutBuildArgs {
   int code_k[kMaxCodes];    // super-tile width (tiles) of each code array
   long long total;          // LUT entries (all depths' capacities)
   int* status;
+  int wavelet;              // WASABI_HAAR or WASABI_COIF1
+  float ctap_lo[6], ctap_hi[6];  // coiflet analysis filters, taps k = -2 .. 3
+  float2* img;              // coiflet scratch D * W * W: PSF, then its Mallat transform
 };
 cudaError_t launch_lut_build(const LutBuildArgs& a, cudaStream_t s);
+
+// Order-1 coiflet filters (FP64): scaling filter h_k and wavelet filter
+// g_k = (-1)^k h_{1-k}, k = -2 .. 3.
+void coif1_filters(double lo[6], double hi[6]);
+// Inverse of an L-level periodic order-1 coiflet transform of a tile-major
+// wavelet buffer: tile-major -> Mallat (into a), L synthesis levels (a <-> b),
+// complex result left in a.
+cudaError_t launch_coif_inverse(const float2* wbuf, int w, int h, int L, float2* a, float2* b, cudaStream_t s);
 // Window tiles one PSF block transforms (1,024 threads, one per pixel).
 inline int psf_tiles_per_block(int L) {
   const int tsl = 1 << (2 * L);

@@ -19,6 +19,8 @@
 //   tile_scan_kernel  one block per depth: tile offsets (CSR)
 //   scatter_kernel    one warp per window tile: ordered compaction
 //   encode_kernel     one warp per 32 entries: FP16/BF16 + FP32 scale
+#include <algorithm>
+
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -91,6 +93,29 @@ struct BoxIter {
   }
 };
 
+// PSF value at offset (du, dv) from the window centre: exp(i 2 pi r / lambda)
+// on the open disk n < R^2 and the centre pixel, 0 elsewhere; conjugate for a
+// depth behind the plane.
+__device__ __forceinline__ float2 psf_pixel(const LutBuildArgs& a, int d, long long du, long long dv) {
+  float2 val = make_float2(0.f, 0.f);
+  const long long n = du * du + dv * dv;
+  if (n == 0 || (double)n < a.R2_dev[d]) {  // the open disk and the centre pixel
+    // r / lambda = sqrt(s), s = n (p/lambda)^2 + (z/lambda)^2: FP32 square
+    // root plus one FP64 Newton step (residual by a fused multiply-add).
+    const double s = __fma_rn((double)n, a.q, a.c_dev[d]);
+    const float t0f = __fsqrt_rn(__double2float_rn(s));
+    const double t0 = (double)t0f;
+    const double res = __fma_rn(-t0, t0, s);
+    const float inv = __frcp_rn(2.0f * t0f);
+    // s = 0 (a point on the plane, at its own pixel): t = 0.
+    const double t = t0f > 0.0f ? __dadd_rn(t0, __dmul_rn(res, (double)inv)) : 0.0;
+    const double f = __dsub_rn(t, floor(t));
+    sincos2pi(__double2float_rn(f), &val.x, &val.y);
+    if (a.z_dev[d] < 0.0) val.y = -val.y;  // behind the plane: the conjugate PSF
+  }
+  return val;
+}
+
 template <int L>
 __global__ void __launch_bounds__(1024) psf_haar_kernel(LutBuildArgs a) {
   constexpr int TS = 1 << L;
@@ -119,26 +144,8 @@ __global__ void __launch_bounds__(1024) psf_haar_kernel(LutBuildArgs a) {
 
   // PSF pixel (Eq. (1) PSF with the circular aperture of step 1).
   const int pu = pix % TS, pv = pix / TS;
-  float2 val = make_float2(0.f, 0.f);
-  if (valid) {
-    const long long du = (long long)(tx * TS + pu) - a.W / 2;
-    const long long dv = (long long)(ty * TS + pv) - a.W / 2;
-    const long long n = du * du + dv * dv;
-    if (n == 0 || (double)n < a.R2_dev[d]) {  // the open disk and the centre pixel
-      // r / lambda = sqrt(s), s = n (p/lambda)^2 + (z/lambda)^2: FP32 square
-      // root plus one FP64 Newton step (residual by a fused multiply-add).
-      const double s = __fma_rn((double)n, a.q, a.c_dev[d]);
-      const float t0f = __fsqrt_rn(__double2float_rn(s));
-      const double t0 = (double)t0f;
-      const double res = __fma_rn(-t0, t0, s);
-      const float inv = __frcp_rn(2.0f * t0f);
-      // s = 0 (a point on the plane, at its own pixel): t = 0.
-      const double t = t0f > 0.0f ? __dadd_rn(t0, __dmul_rn(res, (double)inv)) : 0.0;
-      const double f = __dsub_rn(t, floor(t));
-      sincos2pi(__double2float_rn(f), &val.x, &val.y);
-      if (a.z_dev[d] < 0.0) val.y = -val.y;  // behind the plane: the conjugate PSF
-    }
-  }
+  const float2 val = valid ? psf_pixel(a, d, (long long)(tx * TS + pu) - a.W / 2, (long long)(ty * TS + pv) - a.W / 2)
+                           : make_float2(0.f, 0.f);
   sa[tl][pix] = val;
   __syncthreads();
 
@@ -203,6 +210,116 @@ __device__ unsigned block_excl_scan(unsigned v, unsigned* total) {
   if (total) *total = warp_sum[31];
   __syncthreads();
   return before;
+}
+
+// ---- Order-1 coiflet (periodic filter banks on the whole window) --------
+// The transform is not tile-local, so the PSF of every depth is written out
+// over the whole window (img, row-major), transformed level by level in
+// place (analysis along x into coef as scratch, then along y back into img),
+// and gathered into the tile-major coefficient order the rest of the build
+// uses.  Sum order of every output: the k = -2 product, then fused
+// multiply-adds for k = -1 .. 3 (the oracle's order, so that selections match).
+
+__global__ void psf_plain_kernel(LutBuildArgs a) {
+  const long long WW = (long long)a.W * a.W, n = WW * a.D;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int d = (int)(i / WW);
+    const long long p = i - (long long)d * WW;
+    const long long v = p / a.W, u = p - v * a.W;
+    a.img[i] = psf_pixel(a, d, u - a.W / 2, v - a.W / 2);
+  }
+}
+
+__device__ __forceinline__ int pmod(int x, int n) { return ((x % n) + n) % n; }
+
+// One analysis step of 6 taps over x[(2m + k) mod S], k = -2 .. 3, at
+// stride `step` (1: along a row, W: down a column).
+__device__ __forceinline__ void coif_analyse(const LutBuildArgs& a, const float2* base, long long step, int S, int m,
+                                             float2* lo, float2* hi) {
+  float2 x = base[(long long)pmod(2 * m - 2, S) * step];
+  float2 sl = make_float2(__fmul_rn(a.ctap_lo[0], x.x), __fmul_rn(a.ctap_lo[0], x.y));
+  float2 sh = make_float2(__fmul_rn(a.ctap_hi[0], x.x), __fmul_rn(a.ctap_hi[0], x.y));
+#pragma unroll
+  for (int i = 1; i < 6; ++i) {
+    x = base[(long long)pmod(2 * m + i - 2, S) * step];
+    sl.x = __fmaf_rn(a.ctap_lo[i], x.x, sl.x);
+    sl.y = __fmaf_rn(a.ctap_lo[i], x.y, sl.y);
+    sh.x = __fmaf_rn(a.ctap_hi[i], x.x, sh.x);
+    sh.y = __fmaf_rn(a.ctap_hi[i], x.y, sh.y);
+  }
+  *lo = sl;
+  *hi = sh;
+}
+
+// Along x on the top-left S x S block of each depth: src rows -> dst rows
+// (low half, then high half).
+__global__ void coif_rows_kernel(LutBuildArgs a, const float2* src, float2* dst, int S) {
+  const int d = blockIdx.y, h = S / 2;
+  const long long WW = (long long)a.W * a.W;
+  const long long n = (long long)S * h;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / h), m = (int)(i - (long long)r * h);
+    const long long row = (long long)d * WW + (long long)r * a.W;
+    float2 lo, hi;
+    coif_analyse(a, src + row, 1, S, m, &lo, &hi);
+    dst[row + m] = lo;
+    dst[row + h + m] = hi;
+  }
+}
+
+// Along y on the top-left S x S block: src columns -> dst columns (low half
+// on top).  Consecutive threads take consecutive columns.
+__global__ void coif_cols_kernel(LutBuildArgs a, const float2* src, float2* dst, int S) {
+  const int d = blockIdx.y, h = S / 2;
+  const long long WW = (long long)a.W * a.W;
+  const long long n = (long long)S * h;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(i / S), col = (int)(i - (long long)m * S);
+    const long long base = (long long)d * WW + col;
+    float2 lo, hi;
+    coif_analyse(a, src + base, a.W, S, m, &lo, &hi);
+    dst[base + (long long)m * a.W] = lo;
+    dst[base + (long long)(h + m) * a.W] = hi;
+  }
+}
+
+// Mallat image -> tile-major coefficients, selection keys and nonzero counts.
+__global__ void __launch_bounds__(256) coif_gather_kernel(LutBuildArgs a) {
+  const int d = blockIdx.y;
+  const long long WW = (long long)a.W * a.W;
+  const int tsl = 1 << (2 * a.L);
+  unsigned nz = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < WW; i += (long long)gridDim.x * blockDim.x) {
+    const int tile = (int)(i >> (2 * a.L)), slot = (int)(i & (tsl - 1));
+    const int tx = tile % a.nwt, ty = tile / a.nwt;
+    const float2 c = a.img[(long long)d * WW + mallat_index(a.W, a.L, tx, ty, slot)];
+    const bool nzc = c.x != 0.f || c.y != 0.f;
+    a.coef[(long long)d * WW + i] = c;
+    a.keys[(long long)d * WW + i] = nzc ? key_bits(c) : 0ull;
+    nz += nzc ? 1u : 0u;
+  }
+  for (int o = 16; o > 0; o >>= 1) nz += __shfl_xor_sync(0xffffffffu, nz, o);
+  if ((threadIdx.x & 31) == 0 && nz) atomicAdd(&a.nnz[d], (unsigned long long)nz);
+}
+
+cudaError_t launch_coif_forward(const LutBuildArgs& a, cudaStream_t s) {
+  psf_plain_kernel<<<1024, 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  for (int l = 1; l <= a.L && e == cudaSuccess; ++l) {
+    const int S = a.W >> (l - 1);
+    const long long n = (long long)S * (S / 2);
+    const dim3 grid((unsigned)std::min<long long>((n + 255) / 256, 4096), (unsigned)a.D);
+    coif_rows_kernel<<<grid, 256, 0, s>>>(a, a.img, a.coef, S);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    coif_cols_kernel<<<grid, 256, 0, s>>>(a, a.coef, a.img, S);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return e;
+  const long long WW = (long long)a.W * a.W;
+  const dim3 g((unsigned)std::min<long long>((WW + 255) / 256, 4096), (unsigned)a.D);
+  coif_gather_kernel<<<g, 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 constexpr int kModeGE = 0;   // keep key_bits >= T
@@ -575,13 +692,17 @@ cudaError_t launch_lut_build(const LutBuildArgs& a, cudaStream_t s) {
   // The largest per-depth box sizes the psf grid (smaller boxes idle out).
   const int max_nb = a.max_nb;
   cudaError_t e;
-  switch (a.L) {
-    case 1: e = launch_psf_haar<1>(a, max_nb, s); break;
-    case 2: e = launch_psf_haar<2>(a, max_nb, s); break;
-    case 3: e = launch_psf_haar<3>(a, max_nb, s); break;
-    case 4: e = launch_psf_haar<4>(a, max_nb, s); break;
-    case 5: e = launch_psf_haar<5>(a, max_nb, s); break;
-    default: return cudaErrorInvalidValue;
+  if (a.wavelet == WASABI_COIF1) {
+    e = launch_coif_forward(a, s);
+  } else {
+    switch (a.L) {
+      case 1: e = launch_psf_haar<1>(a, max_nb, s); break;
+      case 2: e = launch_psf_haar<2>(a, max_nb, s); break;
+      case 3: e = launch_psf_haar<3>(a, max_nb, s); break;
+      case 4: e = launch_psf_haar<4>(a, max_nb, s); break;
+      case 5: e = launch_psf_haar<5>(a, max_nb, s); break;
+      default: return cudaErrorInvalidValue;
+    }
   }
   if (e != cudaSuccess) return e;
   select_kernel<<<a.D * kSelCluster, 1024, 0, s>>>(a);

@@ -32,6 +32,7 @@ struct wasabi_lut {
   int ncode = 0;
   int code_k[wsb::kMaxCodes] = {};
   int lmin = 1;                // finest kept level (host copy)
+  int wavelet = 0;             // WASABI_HAAR or WASABI_COIF1
   // Autotuned superposition configurations: hologram size class -> (super-tile, threads).
   mutable std::mutex tune_mu;
   std::map<int, std::pair<int, int>> tuned;

@@ -315,6 +315,7 @@ wasabi_status wasabi_server_create(const wasabi_lut* lut, size_t hbm_budget_byte
     return WASABI_E_INVALID;
   }
   if (lut->L < 2) { set_error("server_create: the fused inverse needs levels >= 2"); return WASABI_E_INVALID; }
+  if (lut->wavelet != WASABI_HAAR) { set_error("server_create: the fused inverse is Haar's"); return WASABI_E_INVALID; }
   *out = nullptr;
   int* status;
   int sms;
