@@ -235,14 +235,18 @@ __device__ __forceinline__ int pmod(int x, int n) { return ((x % n) + n) % n; }
 
 // One analysis step of 6 taps over x[(2m + k) mod S], k = -2 .. 3, at
 // stride `step` (1: along a row, W: down a column).
+__device__ __forceinline__ int coif_wrap(int x, int S) {
+  if (S < 8) return pmod(x, S);  // taps may wrap more than once
+  return x < 0 ? x + S : (x >= S ? x - S : x);
+}
 __device__ __forceinline__ void coif_analyse(const LutBuildArgs& a, const float2* base, long long step, int S, int m,
                                              float2* lo, float2* hi) {
-  float2 x = base[(long long)pmod(2 * m - 2, S) * step];
+  float2 x = base[(long long)coif_wrap(2 * m - 2, S) * step];
   float2 sl = make_float2(__fmul_rn(a.ctap_lo[0], x.x), __fmul_rn(a.ctap_lo[0], x.y));
   float2 sh = make_float2(__fmul_rn(a.ctap_hi[0], x.x), __fmul_rn(a.ctap_hi[0], x.y));
 #pragma unroll
   for (int i = 1; i < 6; ++i) {
-    x = base[(long long)pmod(2 * m + i - 2, S) * step];
+    x = base[(long long)coif_wrap(2 * m + i - 2, S) * step];
     sl.x = __fmaf_rn(a.ctap_lo[i], x.x, sl.x);
     sl.y = __fmaf_rn(a.ctap_lo[i], x.y, sl.y);
     sh.x = __fmaf_rn(a.ctap_hi[i], x.x, sh.x);

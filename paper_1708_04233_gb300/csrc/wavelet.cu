@@ -39,20 +39,23 @@ struct CoifTaps {
   float lo[6], hi[6];
 };
 
-__device__ __forceinline__ int pmod(int x, int n) { return ((x % n) + n) % n; }
-
 // One synthesis output: sample j of a line of S samples receives
 // h_k s[m] + g_k d[m] for every k = j - 2m (mod S), k = -2 .. 3; s and d are
 // the line's low and high halves (S / 2 each), `step` apart in memory.
+// The taps with k = j - 2m of j's parity pair with m = j/2 + 1, j/2, j/2 - 1
+// (k = -2, 0, 2 for even j; -1, 1, 3 for odd j), taken in that order, each
+// m wrapped once (h = 1: every m is 0).
 __device__ __forceinline__ float2 coif_synth(const CoifTaps& t, const float2* line, long long step, int S, int j) {
-  const int h = S / 2;
+  const int h = S / 2, m0 = j >> 1, par = j & 1;
+  int mp = m0 + 1, mm = m0 - 1;
+  if (mp >= h) mp -= h;
+  if (mm < 0) mm += h;
+  const int ms[3] = {mp, m0, mm};
   float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const int k = i - 2;
-    if ((j - k) & 1) continue;
-    const int m = pmod((j - k) / 2, h);
-    const float2 sv = line[(long long)m * step], dv = line[(long long)(h + m) * step];
+  for (int q = 0; q < 3; ++q) {
+    const int i = 2 * q + par;  // tap slot of k = 2q - 2 + par
+    const float2 sv = line[(long long)ms[q] * step], dv = line[(long long)(h + ms[q]) * step];
     acc.x = __fmaf_rn(t.lo[i], sv.x, acc.x);
     acc.y = __fmaf_rn(t.lo[i], sv.y, acc.y);
     acc.x = __fmaf_rn(t.hi[i], dv.x, acc.x);
