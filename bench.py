@@ -38,7 +38,7 @@ UNIT = "Mpoint*coeff/s"
 # dram__bytes_write.sum, one ncu capture of the full workload), valid only
 # while the kernel source is the one that was profiled (sha256 prefix of
 # superpose.cu); see profiles/launches_C3_65536sq_fused.md.
-TRAFFIC = {("C3", "fused"): ("3efdf601d49c0444", 38.1e6 + 475.4e6)}
+TRAFFIC = {("C3", "fused"): ("0792bcedcf496b4c", 38.1e6 + 475.4e6)}
 
 
 def _traffic(c, path):
