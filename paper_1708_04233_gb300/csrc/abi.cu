@@ -442,6 +442,17 @@ wasabi_status wasabi_build_lut_wavelet(double lambda, double pitch, const double
   sc.take<int>((size_t)n_depths + 1);
   sc.take<long long>((size_t)n_depths);
   if (coif) sc.take<float2>((size_t)n_depths * window * window);  // coiflet image
+  // The PSF's octant table: (floor(R) + 1)(floor(R) + 2) / 2 values per depth.
+  std::vector<long long> tri_off(n_depths + 1, 0);
+  std::vector<int> tri_rd(n_depths);
+  for (int d = 0; d < n_depths; ++d) {
+    tri_rd[d] = (int)std::floor(lut->R[d]);
+    const long long r1 = tri_rd[d] + 1;
+    tri_off[d + 1] = tri_off[d] + r1 * (r1 + 1) / 2;
+  }
+  sc.take<float2>((size_t)tri_off[n_depths]);
+  sc.take<long long>((size_t)n_depths + 1);
+  sc.take<int>((size_t)n_depths);
   void* scratch = nullptr;
   e = cudaMallocAsync(&scratch, align_up(sc.off, 256), s);
   if (e != cudaSuccess) {
@@ -468,6 +479,11 @@ wasabi_status wasabi_build_lut_wavelet(double lambda, double pitch, const double
   long long* target_dev = sc.take<long long>((size_t)n_depths);
   a.wavelet = wavelet;
   a.img = coif ? sc.take<float2>((size_t)n_depths * window * window) : nullptr;
+  a.tri = sc.take<float2>((size_t)tri_off[n_depths]);
+  long long* tri_off_dev = sc.take<long long>((size_t)n_depths + 1);
+  int* tri_rd_dev = sc.take<int>((size_t)n_depths);
+  a.tri_off = tri_off_dev;
+  a.tri_rd = tri_rd_dev;
   {
     double lo[6], hi[6];
     coif1_filters(lo, hi);
@@ -508,6 +524,8 @@ wasabi_status wasabi_build_lut_wavelet(double lambda, double pitch, const double
       {c_dev, cz.data(), sizeof(double) * n_depths},
       {blk0_dev, blk0.data(), sizeof(int) * (n_depths + 1)},
       {target_dev, target.data(), sizeof(long long) * n_depths},
+      {tri_off_dev, tri_off.data(), sizeof(long long) * (n_depths + 1)},
+      {tri_rd_dev, tri_rd.data(), sizeof(int) * n_depths},
       {lut->meta_dev, lut->meta.data(), sizeof(DepthMeta) * n_depths},
   };
   bool okc = staged_upload(lut->device, s, ups, (int)(sizeof ups / sizeof ups[0])) == cudaSuccess;

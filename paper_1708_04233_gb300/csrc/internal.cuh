@@ -162,6 +162,12 @@ struct LutBuildArgs {
   int wavelet;              // WASABI_HAAR or WASABI_COIF1
   float ctap_lo[6], ctap_hi[6];  // coiflet analysis filters, taps k = -2 .. 3
   float2* img;              // coiflet scratch D * W * W: PSF, then its Mallat transform
+  // PSF values on one octant: the PSF depends on n = du^2 + dv^2 alone, so
+  // depth d's values for 0 <= dv <= du <= tri_rd[d] are computed once, at
+  // tri[tri_off[d] + du (du + 1) / 2 + dv], and every pixel reads them.
+  float2* tri;
+  const long long* tri_off; // D + 1 prefix
+  const int* tri_rd;        // D: floor(R_d)
 };
 cudaError_t launch_lut_build(const LutBuildArgs& a, cudaStream_t s);
 

@@ -116,6 +116,35 @@ __device__ __forceinline__ float2 psf_pixel(const LutBuildArgs& a, int d, long l
   return val;
 }
 
+// The octant table: entry i of depth d is (du, dv) with du (du + 1) / 2 + dv = i,
+// 0 <= dv <= du, holding psf_pixel(d, du, dv).
+__global__ void psf_table_kernel(LutBuildArgs a) {
+  const long long n = a.tri_off[a.D];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
+    int lo = 0, hi = a.D - 1;  // depth: last d with tri_off[d] <= g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(&a.tri_off[mid]) <= g) lo = mid; else hi = mid - 1;
+    }
+    const int d = lo;
+    const long long i = g - a.tri_off[d];
+    long long u = (long long)((sqrt(8.0 * (double)i + 1.0) - 1.0) * 0.5);
+    while (u * (u + 1) / 2 > i) --u;
+    while ((u + 1) * (u + 2) / 2 <= i) ++u;
+    a.tri[g] = psf_pixel(a, d, u, i - u * (u + 1) / 2);
+  }
+}
+
+// PSF value at (du, dv) from the octant table (0 outside floor(R), where the
+// disk holds no pixel).
+__device__ __forceinline__ float2 psf_lookup(const LutBuildArgs& a, int d, long long du, long long dv) {
+  const long long x = du < 0 ? -du : du, y = dv < 0 ? -dv : dv;
+  const long long hi = x > y ? x : y, lo = x > y ? y : x;
+  if (hi > __ldg(&a.tri_rd[d])) return make_float2(0.f, 0.f);
+  return a.tri[__ldg(&a.tri_off[d]) + hi * (hi + 1) / 2 + lo];
+}
+
 template <int L>
 __global__ void __launch_bounds__(1024) psf_haar_kernel(LutBuildArgs a) {
   constexpr int TS = 1 << L;
@@ -144,7 +173,7 @@ __global__ void __launch_bounds__(1024) psf_haar_kernel(LutBuildArgs a) {
 
   // PSF pixel (Eq. (1) PSF with the circular aperture of step 1).
   const int pu = pix % TS, pv = pix / TS;
-  const float2 val = valid ? psf_pixel(a, d, (long long)(tx * TS + pu) - a.W / 2, (long long)(ty * TS + pv) - a.W / 2)
+  const float2 val = valid ? psf_lookup(a, d, (long long)(tx * TS + pu) - a.W / 2, (long long)(ty * TS + pv) - a.W / 2)
                            : make_float2(0.f, 0.f);
   sa[tl][pix] = val;
   __syncthreads();
@@ -227,7 +256,7 @@ __global__ void psf_plain_kernel(LutBuildArgs a) {
     const int d = (int)(i / WW);
     const long long p = i - (long long)d * WW;
     const long long v = p / a.W, u = p - v * a.W;
-    a.img[i] = psf_pixel(a, d, u - a.W / 2, v - a.W / 2);
+    a.img[i] = psf_lookup(a, d, u - a.W / 2, v - a.W / 2);
   }
 }
 
@@ -696,6 +725,8 @@ cudaError_t launch_lut_build(const LutBuildArgs& a, cudaStream_t s) {
   // The largest per-depth box sizes the psf grid (smaller boxes idle out).
   const int max_nb = a.max_nb;
   cudaError_t e;
+  psf_table_kernel<<<2048, 256, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.wavelet == WASABI_COIF1) {
     e = launch_coif_forward(a, s);
   } else {
