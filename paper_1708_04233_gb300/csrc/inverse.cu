@@ -73,7 +73,9 @@ struct InvCfg {
   static constexpr size_t SMEM = kStages * STAGE_BYTES + 64;
 };
 
-template <int L>
+// REF: bits against a spherical reference wave (a kernel of its own, so that
+// the plane-reference kernel carries none of its code).
+template <int L, bool REF>
 __global__ void __launch_bounds__(InvCfg<L>::NT) inverse_kernel(const __grid_constant__ InverseArgs a) {
   using C = InvCfg<L>;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(InvCfg<L>::NT) inverse_kernel(const __grid_con
   int* status = a.status;
   const int spr = (a.ntx + C::G - 1) / C::G;  // strips per tile row
   __shared__ RefAnchor s_anc[2];  // reference phase anchors of items i and i + 1
-  const bool ref = a.ref.kind != 0 && a.bits != nullptr;
+  constexpr bool ref = REF;
 
   // Tile row and strip column of the CTA's i-th item.
   auto locate = [&](long long i, int* ty, int* sx) {
@@ -309,21 +311,27 @@ __global__ void wbuf_to_mallat_kernel(const float2* __restrict__ wbuf, int w, in
   out[row * w + col] = wbuf[i];
 }
 
-template <int L>
-cudaError_t launch_inv_l(const InverseArgs& a, cudaStream_t s) {
+template <int L, bool REF>
+cudaError_t launch_inv_lr(const InverseArgs& a, cudaStream_t s) {
   using C = InvCfg<L>;
-  cudaError_t e = cudaFuncSetAttribute(inverse_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(inverse_kernel<L, REF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)C::SMEM);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, inverse_kernel<L>, C::NT, C::SMEM);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, inverse_kernel<L, REF>, C::NT, C::SMEM);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   // No more CTAs than strips.
   const long long grid = std::min<long long>((long long)a.num_sms * per_sm, a.nstrips);
   if (grid <= 0) return cudaSuccess;
-  inverse_kernel<L><<<(unsigned)grid, C::NT, C::SMEM, s>>>(a);
+  inverse_kernel<L, REF><<<(unsigned)grid, C::NT, C::SMEM, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int L>
+cudaError_t launch_inv_l(const InverseArgs& a, cudaStream_t s) {
+  if (a.ref.kind != 0 && a.bits != nullptr) return launch_inv_lr<L, true>(a, s);
+  return launch_inv_lr<L, false>(a, s);
 }
 
 template <int L>
