@@ -87,7 +87,7 @@ const char* wasabi_last_error(void);
  * zmax <= zmin. */
 wasabi_status wasabi_depth_grid(double zmin, double zmax, int n_depths, double* depths_host);
 
-/* A0, point preparation (Sec. 1, step 1 depth discretisation): for i < n,
+/* Point preparation (Sec. 1, step 1 depth discretisation): for i < n,
  * out_dev[i] = {x[i], y[i], a[i], d} with d = min(D - 1, floor((z[i] - zmin) / dz)),
  * dz = (zmax - zmin) / D, in FP64.  All arrays are device arrays of n
  * elements.  A z outside [zmin, zmax] (or NaN) gets d = D and records
@@ -97,7 +97,7 @@ wasabi_status wasabi_quantize_points(const int32_t* x_dev, const int32_t* y_dev,
                                      double zmin, double zmax, int n_depths,
                                      wasabi_point* out_dev, void* stream);
 
-/* A1-A3, the look-up table (Sec. 1, step 1): for each depth z_d
+/* The look-up table (Sec. 1, step 1): for each depth z_d
  * (depths_host[0..n_depths)), the PSF u_z = exp(i 2 pi r / lambda) on the
  * W x W window centred at pixel (W/2, W/2) with r = sqrt(n pitch^2 + z^2),
  * n = du^2 + dv^2, restricted to the disk n < R(|z|)^2 and the centre pixel;
@@ -177,7 +177,7 @@ wasabi_status wasabi_scratch_bytes(const wasabi_lut* lut, int64_t n, int holo_w,
 /* Size of the fixed scratch array behind wasabi_superpose_static: 32 MiB. */
 #define WASABI_STATIC_SCRATCH_BYTES (32 * 1024 * 1024)
 
-/* A4 + A5, superposition in the wavelet domain (Eq. (2)):
+/* Binning and superposition in the wavelet domain (Eq. (2)):
  *   psi = sum_j a_j sum_k c_{d_j,k} placed by the shift rule,
  * written to wbuf_dev (tile-major, holo_w * holo_h complex64, fully
  * overwritten: no prior zeroing needed).  points_dev: n wasabi_point;
@@ -243,7 +243,7 @@ typedef struct {
   wasabi_reference ref;       /* reference wave of the binarisation */
 } wasabi_frame;
 
-/* A6 + A7, inverse transformation (Sec. 1, step 3; Sec. 2 binary hologram):
+/* Inverse transformation (Sec. 1, step 3; Sec. 2 binary hologram):
  * the L-level inverse Haar of the tile-major wbuf_dev gives the field u.
  * u_dev (may be NULL): holo_w x holo_h complex64, row-major.
  * bits_dev (may be NULL): the binary hologram bit = (Re u > 0) for a unit
@@ -276,8 +276,9 @@ wasabi_status wasabi_inverse_wavelet(const void* wbuf_dev, int holo_w, int holo_
                                      const wasabi_frame* frame, void* u_dev, uint8_t* bits_dev,
                                      void* scratch_dev, size_t scratch_bytes, void* stream);
 
-/* A4 + A5 + A6 + A7 in one pass: superposition (Eq. (2)) fused with the
- * inverse transformation (Sec. 1, step 3) and binarisation (Sec. 2).  Each
+/* Binning, superposition, inverse and binarisation in one call: the
+ * superposition (Eq. (2)) fused with the inverse transformation (Sec. 1,
+ * step 3) and binarisation (Sec. 2).  Each
  * super-tile's wavelet coefficients are accumulated in shared memory and
  * inverse-transformed there, so the wavelet buffer is never written to (or
  * read back from) device memory unless asked for.  Outputs as in
@@ -317,7 +318,7 @@ wasabi_status wasabi_hologram_stream(const wasabi_lut* lut, const wasabi_point* 
                                      int holo_w, int holo_h, int band_h, int rule, const wasabi_frame* frame,
                                      uint8_t* bits_host, void* u_host, void* stream);
 
-/* ---- Batches: many holograms through one launch sequence (A10) ----------
+/* ---- Batches: many holograms through one launch sequence ---------------
  * One job = one hologram with its own points, wavelet buffer and outputs, all
  * sharing the LUT.  A batch runs every job through five launches (binning:
  * zero, count, scan, scatter; superposition with the fused inverse of
@@ -372,7 +373,7 @@ wasabi_status wasabi_batch_run(wasabi_batch* batch, const wasabi_job* jobs_host,
 wasabi_status wasabi_autotune(wasabi_lut* lut, int holo_side, int64_t n_points, void* stream, int* cell_out,
                               int* threads_out);
 
-/* ---- Serving loop (A11) -------------------------------------------------
+/* ---- Serving loop ---------------------------------------------------------
  * Hologram requests of mixed size and point count, admitted by a device-memory
  * budget and continuously batched.  The server reserves hbm_budget_bytes of
  * device memory once (an arena for every request's points, outputs and
@@ -444,7 +445,7 @@ wasabi_status cgh_direct(double lambda, double pitch, const double* depths_host,
                          int aperture, void* u_dev, void* scratch_dev, size_t scratch_bytes,
                          void* stream);
 
-/* ---- Numerical reconstruction (NEXT-4) ----------------------------------
+/* ---- Numerical reconstruction (Sec. 2, Fig. 3(b)) -----------------------
  * The field of the plane at signed distance d from the hologram, by the
  * angular spectrum method: U_d = IFFT2( FFT2(U_0) H ), with
  * H(fx, fy) = exp(i 2 pi d sqrt(1/lambda^2 - fx^2 - fy^2)) for
