@@ -451,7 +451,7 @@ wasabi_status cgh_direct(double lambda, double pitch, const double* depths_host,
  * H(fx, fy) = exp(i 2 pi d sqrt(1/lambda^2 - fx^2 - fy^2)) for
  * fx^2 + fy^2 < 1/lambda^2 and 0 for evanescent frequencies,
  * fx = k / (w pitch), k in FFT order.  In the sign convention of the object
- * points (Eq. (1) with a +i sign, reading R9), a point at depth z comes to
+ * points (Eq. (1) as printed, with a +i sign), a point at depth z comes to
  * focus at d = -z.  The transfer function's phase is reduced in FP64; the
  * FFTs are cuFFT C2C transforms in FP32.
  * input_kind WASABI_RECON_FIELD: input_dev is a complex64 field (w x h,

@@ -490,7 +490,7 @@ wasabi_status wasabi_build_lut_wavelet(double lambda, double pitch, const double
     for (int i = 0; i < 6; ++i) { a.ctap_lo[i] = (float)lo[i]; a.ctap_hi[i] = (float)hi[i]; }
   }
   a.z_dev = z_dev; a.R2_dev = R2_dev; a.target_dev = target_dev; a.c_dev = c_dev;
-  // Phase constants of reading R8 (plain IEEE double operations).
+  // Phase constants (pitch / lambda)^2 and (z / lambda)^2, plain IEEE double operations.
   const double pl = pitch / lambda;
   a.q = pl * pl;
   std::vector<double> cz(n_depths);
