@@ -420,13 +420,20 @@ class Server:
         self._live = {}
 
     def submit(self, points: torch.Tensor, w: int, h: int, want: str = "bits", rule: int = 0,
-               origin=(0, 0), reference: dict | None = None) -> int:
+               origin=(0, 0), reference: dict | None = None, bits: torch.Tensor | None = None,
+               u: torch.Tensor | None = None) -> int:
+        """Queue a request; its outputs go to `bits` / `u` (host tensors, pinned
+        for asynchronous copies), allocated here when not given."""
         if points.is_cuda or not points.is_contiguous() or points.dtype != torch.int32:
             raise ValueError("points: contiguous (N, 4) int32 host tensor")
         pin = points.is_pinned()
-        bits = (torch.empty((h * w + 7) // 8, dtype=torch.uint8, pin_memory=pin)
-                if want in ("bits", "both") else None)
-        u = torch.empty((h, w), dtype=torch.complex64, pin_memory=pin) if want in ("complex", "both") else None
+        if bits is None and want in ("bits", "both"):
+            bits = torch.empty((h * w + 7) // 8, dtype=torch.uint8, pin_memory=pin)
+        if u is None and want in ("complex", "both"):
+            u = torch.empty((h, w), dtype=torch.complex64, pin_memory=pin)
+        for t in (bits, u):
+            if t is not None and (t.is_cuda or not t.is_contiguous()):
+                raise ValueError("outputs: contiguous host tensors")
         req = _abi.Request(points.data_ptr() if points.shape[0] else None, points.shape[0], w, h, rule,
                            bits.data_ptr() if bits is not None else None,
                            u.data_ptr() if u is not None else None, make_frame(origin, reference))

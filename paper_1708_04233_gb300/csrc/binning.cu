@@ -110,10 +110,10 @@ __global__ void __launch_bounds__(256) count_kernel(BinArgs b) {
 }
 
 // Exclusive scan of each job's cell counts into off[0..ncells] and
-// cursor[0..ncells): one block per job at a time, chunks of 4,096 counts,
-// each thread four consecutive counts, a running carry between chunks.
+// cursor[0..ncells): one block per job at a time, chunks of 16,384 counts,
+// each thread sixteen consecutive counts, a running carry between chunks.
 __global__ void __launch_bounds__(1024) scan_kernel(BinArgs b) {
-  constexpr int CPT = 4;  // counts per thread
+  constexpr int CPT = 16;  // counts per thread
   __shared__ unsigned warp_sum[32];
   __shared__ unsigned s_carry;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -127,11 +127,19 @@ __global__ void __launch_bounds__(1024) scan_kernel(BinArgs b) {
       const int i0 = base + CPT * threadIdx.x;
       int c[CPT];
       unsigned local = 0;
+      const bool whole = i0 + CPT <= ncells;  // the arrays are 256-byte aligned: 16-byte vectors
+      if (whole) {
 #pragma unroll
-      for (int q = 0; q < CPT; ++q) {
-        c[q] = i0 + q < ncells ? J.cnt[i0 + q] : 0;
-        local += (unsigned)c[q];
+        for (int q = 0; q < CPT / 4; ++q) {
+          const int4 v = reinterpret_cast<const int4*>(J.cnt + i0)[q];
+          c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) c[q] = i0 + q < ncells ? J.cnt[i0 + q] : 0;
       }
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) local += (unsigned)c[q];
       unsigned x = local;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -152,13 +160,26 @@ __global__ void __launch_bounds__(1024) scan_kernel(BinArgs b) {
       __syncthreads();
       const unsigned carry = s_carry;
       unsigned run = carry + (wid ? warp_sum[wid - 1] : 0u) + x - local;
+      int o[CPT];
 #pragma unroll
       for (int q = 0; q < CPT; ++q) {
-        if (i0 + q < ncells) {
-          J.off[i0 + q] = (int)run;
-          J.cursor[i0 + q] = (int)run;
-        }
+        o[q] = (int)run;
         run += (unsigned)c[q];
+      }
+      if (whole) {
+#pragma unroll
+        for (int q = 0; q < CPT / 4; ++q) {
+          const int4 v = make_int4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+          reinterpret_cast<int4*>(J.off + i0)[q] = v;
+          reinterpret_cast<int4*>(J.cursor + i0)[q] = v;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q)
+          if (i0 + q < ncells) {
+            J.off[i0 + q] = o[q];
+            J.cursor[i0 + q] = o[q];
+          }
       }
       __syncthreads();
       if (threadIdx.x == 0) s_carry = carry + warp_sum[31];
