@@ -39,17 +39,31 @@ UNIT = "Mpoint*coeff/s"
 # while the kernel source is the one that was profiled (sha256 prefix of
 # superpose.cu); see profiles/launches_C3_65536sq_fused.md.
 TRAFFIC = {("C3", "fused"): ("0792bcedcf496b4c", 38.1e6 + 475.4e6)}
+# The same kernel's issue-slot utilisation and instructions per
+# point·coefficient from its full ncu capture (32,768^2 slice of C3,
+# profiles/superpose_fused_bits_C3_32768sq.md): the instruction roofline it
+# is bound by.
+ISSUE = {("C3", "fused"): ("0792bcedcf496b4c", 0.747, 4.85)}
+
+
+def _superpose_sha():
+    import hashlib
+    src = os.path.join(ROOT, "paper_1708_04233_gb300", "csrc", "superpose.cu")
+    with open(src, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def _traffic(c, path):
-    import hashlib
     ent = TRAFFIC.get((c.name, path))
-    if ent is None:
+    return ent[1] if ent is not None and _superpose_sha() == ent[0] else None
+
+
+def _issue(c, path):
+    ent = ISSUE.get((c.name, path))
+    if ent is None or _superpose_sha() != ent[0]:
         return None
-    src = os.path.join(ROOT, "paper_1708_04233_gb300", "csrc", "superpose.cu")
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    return ent[1] if sha == ent[0] else None
+    return {"ncu_issue_active": ent[1], "warp_instructions_per_point_coeff": ent[2],
+            "profile": "profiles/superpose_fused_bits_C3_32768sq.md"}
 
 
 def max_over_ranks(x: float, device) -> float:
@@ -667,7 +681,8 @@ def run_gpu(args, c):
                        else f"superpose_kernel<{c.L},{c.lut_dtype}>") + " (+ binning kernels, one ABI call)",
             "bound": "alu", "achieved": ach, "peak": smem_peak, "unit": "Gop/s", "frac": ach / smem_peak,
             "peak_source": "derived: 32 banks x 152 SMs x 2070 MHz (shared-memory 32-bit ops)",
-            "algorithmic_ops": parts * units, "ops_per_point_coeff": parts, "traffic": _traffic(c, args.path)}
+            "algorithmic_ops": parts * units, "ops_per_point_coeff": parts, "traffic": _traffic(c, args.path),
+            "issue": _issue(c, args.path)}
     # psf, select, tile count/scan, scatter, codes, level-mask readback (+ encode for FP16/BF16)
     lut_kernels = 7 + (0 if c.lut_dtype in ("f32", 0) else 1)
     per_step = lut_kernels + 1 + 6 + (0 if fused else 1)
