@@ -365,8 +365,8 @@ wasabi_status wasabi_batch_run(wasabi_batch* batch, const wasabi_job* jobs_host,
                                size_t scratch_bytes, void* stream);
 
 /* Autotuner: times the superposition of n synthetic points on a
- * holo_side^2 hologram for super-tiles {64, 128, 256} x blocks {256, 384,
- * 512} (those that fit), keeps the fastest in the LUT for that size class
+ * holo_side^2 hologram for super-tiles {64, 128, 192, 256} x blocks {256,
+ * 384, 512, 1024} (those that fit), keeps the fastest in the LUT for that size class
  * (holo_side rounded up to a power of two) and returns it.  Later
  * superposition calls and batches of that class use it.  Synchronising;
  * allocates temporary device memory. */

@@ -186,9 +186,10 @@ using namespace wsb;
 
 namespace wsb {
 
-void superpose_config(const wasabi_lut* lut, int w, int h, int* cell, int* threads) {
-  int T = superpose_default_cell(lut->L, lut->lmin, lut->D);
-  int nt = 512;
+void superpose_config(const wasabi_lut* lut, int w, int h, int kind, int* cell, int* threads) {
+  int T, nt;
+  if (std::max(w, h) < kConfigLargeSide) kind = kConfigShared;
+  superpose_default_config(lut->L, lut->lmin, lut->D, kind, &T, &nt);
   {
     std::lock_guard<std::mutex> lk(lut->tune_mu);
     const auto it = lut->tuned.find(size_class(w, h));
@@ -203,7 +204,7 @@ void superpose_config(const wasabi_lut* lut, int w, int h, int* cell, int* threa
   T = std::max(unit, T / unit * unit);
   while (T > unit && superpose_smem_bytes(T, lut->L, lut->lmin, lut->D, false, 2048) > 220 * 1024)
     T = std::max(unit, T / 2 / unit * unit);
-  nt = std::max(superpose_min_threads(), std::min(512, nt / 32 * 32));
+  nt = std::max(superpose_min_threads(), std::min(1024, nt / 32 * 32));
   *cell = T;
   *threads = nt;
 }
@@ -686,7 +687,7 @@ wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points
                                void* stream) {
   if (!lut) { set_error("superpose: NULL argument"); return WASABI_E_INVALID; }
   int cell, threads;
-  superpose_config(lut, holo_w, holo_h, &cell, &threads);
+  superpose_config(lut, holo_w, holo_h, kConfigComplex, &cell, &threads);
   if (!wbuf_dev) { set_error("superpose: NULL wavelet buffer"); return WASABI_E_INVALID; }
   return superpose_impl(lut, points_dev, n, holo_w, holo_h, rule, wbuf_dev, nullptr, nullptr, scratch_dev,
                         scratch_bytes, (cudaStream_t)stream, cell, threads);
@@ -698,7 +699,7 @@ wasabi_status wasabi_hologram(const wasabi_lut* lut, const wasabi_point* points_
   if (!lut) { set_error("hologram: NULL argument"); return WASABI_E_INVALID; }
   if (!u_dev && !bits_dev) { set_error("hologram: need u_dev or bits_dev"); return WASABI_E_INVALID; }
   int cell, threads;
-  superpose_config(lut, holo_w, holo_h, &cell, &threads);
+  superpose_config(lut, holo_w, holo_h, superpose_config_kind(wbuf_dev, u_dev, bits_dev, nullptr), &cell, &threads);
   return superpose_impl(lut, points_dev, n, holo_w, holo_h, rule, wbuf_dev, u_dev, bits_dev, scratch_dev,
                         scratch_bytes, (cudaStream_t)stream, cell, threads);
 }
@@ -708,7 +709,7 @@ wasabi_status wasabi_hologram_frame(const wasabi_lut* lut, const wasabi_point* p
                                     uint8_t* bits_dev, void* scratch_dev, size_t scratch_bytes, void* stream) {
   if (!lut) { set_error("hologram_frame: NULL argument"); return WASABI_E_INVALID; }
   int cell, threads;
-  superpose_config(lut, holo_w, holo_h, &cell, &threads);
+  superpose_config(lut, holo_w, holo_h, superpose_config_kind(wbuf_dev, u_dev, bits_dev, frame), &cell, &threads);
   return superpose_impl(lut, points_dev, n, holo_w, holo_h, rule, wbuf_dev, u_dev, bits_dev, scratch_dev,
                         scratch_bytes, (cudaStream_t)stream, cell, threads, frame);
 }
@@ -778,7 +779,7 @@ wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* poi
   int sms;
   if (!device_info(&status, &sms)) return WASABI_E_CUDA;
   if (cell < std::max(1 << lut->L, 32) || cell > 256 || cell % std::max(1 << lut->L, 32) ||
-      threads < superpose_min_threads() || threads > 512 || threads % 32) {
+      threads < superpose_min_threads() || threads > 1024 || threads % 32) {
     set_error("superpose: bad configuration (super-tile %d, %d threads)", cell, threads);
     return WASABI_E_INVALID;
   }

@@ -151,7 +151,7 @@ wasabi_status wasabi_batch_create(const wasabi_lut* lut, int max_jobs, int holo_
   b->max_jobs = max_jobs;
   b->use_graph = use_graph != 0;
   const int side = holo_side_hint > 0 ? holo_side_hint : 4096;
-  superpose_config(lut, side, side, &b->cell, &b->threads);
+  superpose_config(lut, side, side, kConfigShared, &b->cell, &b->threads);
   cudaError_t e = cudaMallocHost(&b->staging_jobs, sizeof(JobDev) * max_jobs);
   if (e == cudaSuccess) e = cudaMallocHost(&b->staging_batch, sizeof(BatchDev));
   if (e == cudaSuccess) e = cudaMalloc(&b->jobs_dev, sizeof(JobDev) * max_jobs);
@@ -333,8 +333,8 @@ wasabi_status wasabi_autotune(wasabi_lut* lut, int holo_side, int64_t n_points, 
   cudaEventCreate(&t1);
   int best_cell = 0, best_threads = 0;
   float best = 1e30f;
-  const int cells[] = {64, 128, 256};
-  const int tcounts[] = {256, 384, 512};
+  const int cells[] = {64, 128, 192, 256};
+  const int tcounts[] = {256, 384, 512, 1024};
   for (int cell : cells) {
     if (cell < std::max(1 << lut->L, 32) || superpose_smem_bytes(cell, lut->L, lut->lmin, lut->D, false, 2048) > 220 * 1024)
       continue;

@@ -349,7 +349,13 @@ size_t superpose_smem_bytes(int cell, int L, int lmin, int D, bool re_only, int 
 // Range capacity for a launch: larger when only real parts are accumulated
 // and the freed shared memory still lets two CTAs share an SM.
 int superpose_range_cap(int cell, int L, int lmin, int D, bool re_only, int threads);
-int superpose_default_cell(int L, int lmin, int D);
+// Kinds of superposition launch, for the default configuration.
+// kConfigShared: the configuration batches use, and every call on a hologram
+// below kConfigLargeSide pixels a side (so such a call and a batch job give
+// the same fixed-point results).
+constexpr int kConfigComplex = 0, kConfigRe = 1, kConfigRef = 2, kConfigShared = 3;
+constexpr int kConfigLargeSide = 8192;
+void superpose_default_config(int L, int lmin, int D, int kind, int* cell, int* threads);
 
 struct InverseArgs {
   const float2* wbuf;       // tile-major wavelet buffer

@@ -81,7 +81,15 @@ inline int size_class(int w, int h) {
 
 // Super-tile side and block size for a hologram: an environment override,
 // else the autotuned choice for its size class, else the default.
-void superpose_config(const wasabi_lut* lut, int w, int h, int* cell, int* threads);
+// kind: kConfigComplex / kConfigRe / kConfigRef / kConfigShared (the default
+// of a hologram of at least kConfigLargeSide pixels a side depends on it);
+// see superpose_config_kind for a call's kind.
+void superpose_config(const wasabi_lut* lut, int w, int h, int kind, int* cell, int* threads);
+// The kind of launch a superposition call makes from its outputs and frame.
+inline int superpose_config_kind(bool wbuf, bool u, bool bits, const wasabi_frame* frame) {
+  if (bits && frame && frame->ref.kind != WASABI_REF_PLANE) return kConfigRef;
+  return (!wbuf && !u && bits) ? kConfigRe : kConfigComplex;
+}
 
 // wasabi_superpose / wasabi_hologram with an explicit configuration: any of
 // the wavelet buffer, the complex field and the packed bits may be written.

@@ -74,7 +74,7 @@ wasabi_status wasabi_hologram_stream(const wasabi_lut* lut, const wasabi_point* 
   if (e != cudaSuccess) st = cuda_fail("hologram_stream: setup", e);
 
   int cell, threads;
-  superpose_config(lut, holo_w, bh, &cell, &threads);
+  superpose_config(lut, holo_w, bh, superpose_config_kind(false, u_host, bits_host, frame), &cell, &threads);
   for (int k = 0; k < nbands && st == WASABI_OK; ++k) {
     Slot& sl = slot[k & 1];
     const cudaStream_t s = ss[k & 1];

@@ -40,7 +40,7 @@ namespace {
 
 constexpr int kMaxCellRows = 256;
 constexpr int kRangeCap = 2048;  // LUT ranges per batch (complex accumulation)
-constexpr int kRangeMax = 4096;  // LUT ranges per batch when only real parts are accumulated
+constexpr int kRangeMax = 8192;  // LUT ranges per batch, at most (threads x kPerMax)
 constexpr int kPerMax = 8;       // range slots per thread (block size >= 256)
 constexpr int kLookahead = 32;   // range starts one visit lookup reads (one per lane)
 // Dynamic shared memory per CTA that still lets two CTAs share an SM (with
@@ -362,7 +362,7 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
 constexpr int kModeComplex = 0, kModeRe = 1, kModeRef = 2;
 
 template <int L, int DT, int MODE>
-__global__ void __launch_bounds__(512, 2) superpose_kernel(SuperposeArgs a) {
+__global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
   constexpr int TSL = 1 << (2 * L);
   static_assert(TSL <= kRangeCap, "the write-out slot table lives in the range records");
   extern __shared__ __align__(16) unsigned char smem[];
@@ -767,24 +767,53 @@ int superpose_range_cap(int cell, int L, int lmin, int D, bool re_only, int thre
     const int r = std::max(kRangeCap, std::min(big, std::atoi(v)));
     if (superpose_smem_bytes(cell, L, lmin, D, re_only, r) <= 220 * 1024) return r;
   }
+  // Two CTAs per SM (up to 512 threads) share the SM's shared memory; a
+  // 1,024-thread CTA has it alone.  The larger range capacity when it fits.
+  if (threads > 512) {
+    for (int r = big; r > kRangeCap; r >>= 1)
+      if (superpose_smem_bytes(cell, L, lmin, D, re_only, r) <= 220 * 1024) return r;
+    return kRangeCap;
+  }
   if (re_only && big > kRangeCap && superpose_smem_bytes(cell, L, lmin, D, true, big) <= kTwoCtaSmem) return big;
   return kRangeCap;
 }
 
-// Largest power-of-two super-tile side (at most 256 pixels) whose shared
-// memory lets two CTAs share an SM.
-int superpose_default_cell(int L, int lmin, int D) {
+// Default configuration per kind of launch (measured on C2, C3 and the
+// paper's geometry):
+//  - real parts only (bits, plane reference): one 1,024-thread CTA per SM on
+//    the widest super-tile (128 to 256 pixels) whose shared memory fits the
+//    SM -- wider tiles mean fewer candidates and LUT ranges per pixel;
+//  - complex accumulation: one 1,024-thread CTA per SM on 192, else 128;
+//  - the reference-wave epilogue and the shared configuration (batches and
+//    holograms below 8,192 pixels a side, where more, smaller CTAs keep the
+//    SMs busy and latency low): two
+//    512-thread CTAs per SM on the largest power-of-two side whose shared
+//    memory fits half the SM, or one 1,024-thread CTA on 128 pixels when that
+//    side would be below 128.
+void superpose_default_config(int L, int lmin, int D, int kind, int* cell, int* threads) {
   const int unit = (1 << L) > 32 ? (1 << L) : 32;
+  const bool re = kind == kConfigRe;
+  auto fits_one = [&](int T) { return superpose_smem_bytes(T, L, lmin, D, re, kRangeCap) <= 220 * 1024; };
+  if (kind == kConfigRe) {
+    for (int T = 256 / unit * unit; T >= 128 && T >= unit; T -= unit)
+      if (fits_one(T)) { *cell = T; *threads = 1024; return; }
+  } else if (kind == kConfigComplex) {
+    for (int T : {192, 128})
+      if (T % unit == 0 && fits_one(T)) { *cell = T; *threads = 1024; return; }
+  }
   int T = 256;
   while (T > unit && superpose_smem_bytes(T, L, lmin, D, false, kRangeCap) > kTwoCtaSmem) T >>= 1;
-  return T < unit ? unit : T;
+  if (T < unit) T = unit;
+  if (T < 128 && 128 % unit == 0 && fits_one(128)) { *cell = 128; *threads = 1024; return; }
+  *cell = T;
+  *threads = 512;
 }
 
 int superpose_max_cell_rows() { return kMaxCellRows; }
 int superpose_min_threads() { return kRangeCap / kPerMax; }
 
 cudaError_t launch_superpose(const SuperposeArgs& a, cudaStream_t s) {
-  if (a.threads > 512 || a.threads < kRangeCap / kPerMax || a.threads % 32 || !a.lut.code ||
+  if (a.threads > 1024 || a.threads < kRangeCap / kPerMax || a.threads % 32 || !a.lut.code ||
       a.rcap < kRangeCap || a.rcap > kRangeMax || a.rcap > a.threads * kPerMax)
     return cudaErrorInvalidValue;
   switch (a.lut.L) {

@@ -91,7 +91,7 @@ def test_batch_rejects_bad_jobs(setup, orc):
 def test_autotune_picks_a_valid_configuration(setup, orc):
     w, lut, _ = setup
     cell, threads = w.autotune(lut, 512, 2000)
-    assert cell in (64, 128, 256) and threads in (256, 384, 512)
+    assert cell in (64, 128, 192, 256) and threads in (256, 384, 512, 1024)
     _, j = _job(w, orc, 12, 300, 512, "none")
     a = w.superpose(lut, j["points"], 512, 512).cpu().numpy()
     b = w.Batch(lut, 1, side_hint=512, use_graph=False)
