@@ -38,12 +38,12 @@ UNIT = "Mpoint*coeff/s"
 # dram__bytes_write.sum, one ncu capture of the full workload), valid only
 # while the kernel source is the one that was profiled (sha256 prefix of
 # superpose.cu); see profiles/launches_C3_65536sq_fused.md.
-TRAFFIC = {("C3", "fused"): ("0792bcedcf496b4c", 38.1e6 + 475.4e6)}
+TRAFFIC = {("C3", "fused"): ("1063342d70b6fe2c", 36.8e6 + 478.7e6)}
 # The same kernel's issue-slot utilisation and instructions per
 # point·coefficient from its full ncu capture (32,768^2 slice of C3,
 # profiles/superpose_fused_bits_C3_32768sq.md): the instruction roofline it
 # is bound by.
-ISSUE = {("C3", "fused"): ("0792bcedcf496b4c", 0.747, 4.85)}
+ISSUE = {("C3", "fused"): ("1063342d70b6fe2c", 0.711, 4.10)}
 
 
 def _superpose_sha():
