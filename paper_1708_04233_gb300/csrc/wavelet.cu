@@ -120,7 +120,8 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
 
-cudaError_t launch_coif_inverse(const float2* wbuf, int w, int h, int L, float2* a, float2* b, cudaStream_t s) {
+cudaError_t launch_coif_inverse(const float2* wbuf, int w, int h, int L, float2* a, float2* b, cudaStream_t s,
+                                float2* out) {
   double lo[6], hi[6];
   coif1_filters(lo, hi);
   CoifTaps t;
@@ -131,7 +132,8 @@ cudaError_t launch_coif_inverse(const float2* wbuf, int w, int h, int L, float2*
     const long long n = (long long)Sx * Sy;
     coif_syn_cols_kernel<<<grid_for(n), 256, 0, s>>>(a, b, w, Sx, Sy, t);
     if ((e = cudaGetLastError()) != cudaSuccess) break;
-    coif_syn_rows_kernel<<<grid_for(n), 256, 0, s>>>(b, a, w, Sx, Sy, t);
+    // The last level writes the field straight into `out` when given.
+    coif_syn_rows_kernel<<<grid_for(n), 256, 0, s>>>(b, (l == 1 && out) ? out : a, w, Sx, Sy, t);
     e = cudaGetLastError();
   }
   return e;
@@ -183,11 +185,11 @@ wasabi_status wasabi_inverse_wavelet(const void* wbuf_dev, int holo_w, int holo_
   const cudaStream_t s = (cudaStream_t)stream;
   float2* a = static_cast<float2*>(scratch_dev);
   float2* b = reinterpret_cast<float2*>(static_cast<char*>(scratch_dev) + need / 2);
-  cudaError_t e = launch_coif_inverse(static_cast<const float2*>(wbuf_dev), holo_w, holo_h, levels, a, b, s);
-  if (e == cudaSuccess) {
-    const long long groups = (long long)holo_w * holo_h / (bits_dev ? 8 : 1);
-    coif_out_kernel<<<grid_for(groups), 256, 0, s>>>(a, holo_w, holo_h, static_cast<float2*>(u_dev), bits_dev, ox, oy,
-                                                     ref);
+  float2* u = static_cast<float2*>(u_dev);
+  cudaError_t e = launch_coif_inverse(static_cast<const float2*>(wbuf_dev), holo_w, holo_h, levels, a, b, s, u);
+  if (e == cudaSuccess && bits_dev) {  // the field is in u when it was asked for, else in a
+    const long long groups = (long long)holo_w * holo_h / 8;
+    coif_out_kernel<<<grid_for(groups), 256, 0, s>>>(u ? u : a, holo_w, holo_h, nullptr, bits_dev, ox, oy, ref);
     e = cudaGetLastError();
   }
   return e == cudaSuccess ? WASABI_OK : cuda_fail("inverse_wavelet", e);
