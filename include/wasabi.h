@@ -183,7 +183,15 @@ wasabi_status wasabi_scratch_bytes(const wasabi_lut* lut, int64_t n, int holo_w,
  * overwritten: no prior zeroing needed).  points_dev: n wasabi_point;
  * scratch_dev: at least wasabi_scratch_bytes() bytes, 256-byte aligned.
  * holo_w, holo_h: multiples of 2^L (the LUT's levels), >= 2^L.
- * A point with d >= D records WASABI_E_RANGE and contributes nothing. */
+ * A point with d >= D records WASABI_E_RANGE and contributes nothing.
+ * Configuration (super-tile side T, threads per CTA): the autotuned one for
+ * the hologram's size class if wasabi_autotune ran, else a default: below
+ * 8,192 pixels a side, and in batches, two 512-thread CTAs per SM on the
+ * largest power-of-two T whose shared memory fits half an SM; from 8,192 up,
+ * one 1,024-thread CTA per SM on T = 256 for bits with the plane reference
+ * (real parts only), T = 192 for complex accumulation, and the two-CTA
+ * choice for the spherical-reference epilogue.  Results depend on T only
+ * through the rounding of each super-tile's fixed-point scale. */
 wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n,
                                int holo_w, int holo_h, int rule, void* wbuf_dev,
                                void* scratch_dev, size_t scratch_bytes, void* stream);
