@@ -191,7 +191,12 @@ wasabi_status wasabi_scratch_bytes(const wasabi_lut* lut, int64_t n, int holo_w,
  * one 1,024-thread CTA per SM on T = 256 for bits with the plane reference
  * (real parts only), T = 192 for complex accumulation, and the two-CTA
  * choice for the spherical-reference epilogue.  Results depend on T only
- * through the rounding of each super-tile's fixed-point scale. */
+ * through the rounding of each super-tile's fixed-point scale.
+ * Environment overrides (tuning and tests; read at each call):
+ * WASABI_SUPERPOSE_T and WASABI_SUPERPOSE_THREADS force the super-tile side
+ * and threads per CTA (clamped to valid values), WASABI_RANGE_CAP the LUT
+ * ranges per candidate batch, and WASABI_ACC_FLOAT=1 replaces the exact
+ * fixed-point accumulation with FP32 shared-memory atomics. */
 wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n,
                                int holo_w, int holo_h, int rule, void* wbuf_dev,
                                void* scratch_dev, size_t scratch_bytes, void* stream);
