@@ -465,17 +465,23 @@ wasabi_status cgh_direct(double lambda, double pitch, const double* depths_host,
  * fx^2 + fy^2 < 1/lambda^2 and 0 for evanescent frequencies,
  * fx = k / (w pitch), k in FFT order.  In the sign convention of the object
  * points (Eq. (1) as printed, with a +i sign), a point at depth z comes to
- * focus at d = -z.  The transfer function's phase is reduced in FP64; the
- * FFTs are cuFFT C2C transforms in FP32.
+ * focus at d = -z.  The phases of the transfer function and of the reference
+ * wave are carried in double-float (pairs of FP32 values, about 44 bits) and
+ * reduced to [0, 1); the FFTs are cuFFT C2C transforms in FP32.  Plane
+ * pixels (origin plus index) must stay below 2^24 in magnitude.
  * input_kind WASABI_RECON_FIELD: input_dev is a complex64 field (w x h,
  * row-major).  WASABI_RECON_BITS: input_dev is a packed binary hologram
  * (w % 8 == 0), an amplitude transmittance t in {0, 1}, illuminated by the
  * frame's reference wave: U_0 = t R (the frame may be NULL: R = 1, origin 0).
  * Outputs (either may be NULL, not both): field_out_dev complex64 U_d,
  * intensity_out_dev float |U_d|^2, both w x h row-major.
- * scratch_dev: wasabi_reconstruct_scratch_bytes() bytes, 256-byte aligned.
- * Synchronous: returns after the result is in place (the FFT plan lives
- * only for the call). */
+ * scratch_dev: wasabi_reconstruct_scratch_bytes() bytes, 256-byte aligned
+ * (the cuFFT work area; calls in flight at once need separate scratch).
+ * The cuFFT plans of the first 8 (device, w, h) shapes either function meets
+ * are kept for the life of the process, and a call on such a shape is
+ * asynchronous on `stream`; for any other shape the plan lives for the call
+ * only and the call returns after the result is in place.  Calls are
+ * serialised on the host by one mutex. */
 typedef enum { WASABI_RECON_FIELD = 0, WASABI_RECON_BITS = 1 } wasabi_recon_input;
 wasabi_status wasabi_reconstruct_scratch_bytes(int w, int h, size_t* bytes_out);
 wasabi_status wasabi_reconstruct(const void* input_dev, int input_kind, int w, int h, double lambda, double pitch,

@@ -21,6 +21,17 @@ def _stream(stream=None) -> C.c_void_p:
     return C.c_void_p(s.cuda_stream)
 
 
+def _keep(stream, *tensors) -> None:
+    """Tensors allocated on the current stream that a call used on another
+    stream: the caching allocator is told, so their memory is not handed out
+    again before that stream's work on them is done."""
+    if stream is None or stream == torch.cuda.current_stream():
+        return
+    for t in tensors:
+        if t is not None and t.is_cuda:
+            t.record_stream(stream)
+
+
 def _ptr(t: torch.Tensor | None) -> C.c_void_p | None:
     if t is None:
         return None
@@ -124,6 +135,7 @@ def quantize_points(x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, a: torch.
         out = torch.empty((n, 4), dtype=torch.int32, device=x.device)
     check(_lib().wasabi_quantize_points(_ptr(x), _ptr(y), _ptr(z), _ptr(a), n, zmin, zmax,
                                         n_depths, _ptr(out), _stream(stream)))
+    _keep(stream, out)
     return out
 
 
@@ -154,6 +166,7 @@ def superpose(lut: Lut, points: torch.Tensor, w: int, h: int, rule: int = 0,
         frame = make_frame(origin, None)
         check(_lib().wasabi_hologram_frame(lut.handle, pts, n, w, h, rule, C.byref(frame), _ptr(wbuf),
                                            None, None, _ptr(scratch), scratch.numel(), _stream(stream)))
+    _keep(stream, wbuf, scratch)
     return wbuf
 
 
@@ -167,6 +180,7 @@ def superpose_static(lut: Lut, points: torch.Tensor, w: int, h: int, rule: int =
         wbuf = torch.empty(h * w, dtype=torch.complex64, device=points.device)
     check(_lib().wasabi_superpose_static(lut.handle, _ptr(points) if n else C.c_void_p(None), n, w,
                                          h, rule, _ptr(wbuf), _stream(stream)))
+    _keep(stream, wbuf)
     return wbuf
 
 
@@ -186,6 +200,7 @@ def inverse_wavelet(wbuf: torch.Tensor, w: int, h: int, levels: int, wavelet: st
     frame = make_frame(origin, reference)
     check(_lib().wasabi_inverse_wavelet(_ptr(wbuf), w, h, levels, _abi.WAVELETS[wavelet], C.byref(frame), _ptr(u),
                                         _ptr(bits), _ptr(scratch), scratch.numel(), _stream(stream)))
+    _keep(stream, u, bits, scratch)
     if want == "complex":
         return u
     if want == "bits":
@@ -225,6 +240,7 @@ def inverse_haar(wbuf: torch.Tensor, w: int, h: int, levels: int, u: torch.Tenso
     frame = make_frame(origin, reference)
     check(_lib().wasabi_inverse_haar_frame(_ptr(wbuf), w, h, levels, C.byref(frame), _ptr(u), _ptr(bits),
                                            _stream(stream)))
+    _keep(stream, u, bits)
     if want == "complex":
         return u
     if want == "bits":
@@ -258,6 +274,7 @@ def hologram(lut: Lut, points: torch.Tensor, w: int, h: int, want: str = "comple
         check(_lib().wasabi_hologram_frame(lut.handle, _ptr(points) if n else C.c_void_p(None), n, w, h, rule,
                                            C.byref(frame), _ptr(wbuf), _ptr(u), _ptr(bits), _ptr(scratch),
                                            scratch.numel(), _stream(stream)))
+    _keep(stream, u, bits, wbuf, scratch)
     if want == "complex":
         return u
     if want == "bits":
@@ -309,6 +326,7 @@ def reconstruct(hologram: torch.Tensor, w: int, h: int, lam: float, pitch: float
     field, inten = (out, None) if want == "complex" else (None, out)
     check(_lib().wasabi_reconstruct(_ptr(hologram), kind, w, h, lam, pitch, d, C.byref(frame), _ptr(field),
                                     _ptr(inten), _ptr(scratch), scratch.numel(), _stream(stream)))
+    _keep(stream, out, scratch)
     return out
 
 
@@ -332,6 +350,7 @@ def cgh_direct(lam: float, pitch: float, depths, points: torch.Tensor, w: int, h
     check(_lib().cgh_direct(lam, pitch, d.ctypes.data_as(C.POINTER(C.c_double)), d.size,
                             _ptr(points) if n else C.c_void_p(None), n, w, h, int(aperture),
                             _ptr(u), _ptr(scratch), scratch.numel(), _stream(stream)))
+    _keep(stream, u, scratch)
     return u
 
 
@@ -388,6 +407,7 @@ class Batch:
         scratch = torch.empty(max(int(need.value), 256), dtype=torch.uint8, device=dev)
         check(_lib().wasabi_batch_run(self._h, C.cast(arr, C.c_void_p), n, _ptr(scratch),
                                       scratch.numel(), _stream(stream)))
+        _keep(stream, scratch, *[o[k] for o in out for k in ("wbuf", "u", "bits")])
         self._keep = (scratch, out)
         return out
 
@@ -487,10 +507,12 @@ def haar_forward(u: torch.Tensor, levels: int, stream=None) -> torch.Tensor:
     h, w = u.shape
     wbuf = torch.empty(h * w, dtype=torch.complex64, device=u.device)
     check(_lib().wasabi_haar_forward(_ptr(u), w, h, levels, _ptr(wbuf), _stream(stream)))
+    _keep(stream, wbuf)
     return wbuf
 
 
 def wbuf_to_mallat(wbuf: torch.Tensor, w: int, h: int, levels: int, stream=None) -> torch.Tensor:
     out = torch.empty((h, w), dtype=torch.complex64, device=wbuf.device)
     check(_lib().wasabi_wbuf_to_mallat(_ptr(wbuf), w, h, levels, _ptr(out), _stream(stream)))
+    _keep(stream, out)
     return out

@@ -4,12 +4,13 @@
 // space (evanescent frequencies dropped).  Three element-wise kernels around
 // two cuFFT C2C transforms: the input (a complex field, or a binary
 // hologram's transmittance times the reference wave), the transfer function
-// (phase reduced in FP64, then FP32 sine and cosine), the outputs.
+// (phase in double-float FP32 pairs, then FP32 sine and cosine), the outputs.
 #include <cufft.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "lut_object.h"
 
@@ -19,9 +20,72 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+// A real number as an unevaluated sum hi + lo of two FP32 values
+// ("double-float"): the error-free transformations are Knuth's two-sum and
+// the exact product through one fused multiply-add.  Products that feed
+// them are rounded explicitly (__fmul_rn) so that no contraction into an FMA
+// changes them.
+struct Dbf {
+  float hi, lo;
+};
+__device__ __forceinline__ Dbf two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// (c.hi + c.lo) x for a float x exact in FP32.
+__device__ __forceinline__ Dbf dbf_mul_f(Dbf c, float x) {
+  const float p = __fmul_rn(c.hi, x);
+  return {p, __fmaf_rn(c.lo, x, __fmaf_rn(c.hi, x, -p))};
+}
+// (a.hi + a.lo)^2.
+__device__ __forceinline__ Dbf dbf_sqr(Dbf a) {
+  const float p = __fmul_rn(a.hi, a.hi);
+  return {p, __fmaf_rn(2.0f * a.hi, a.lo, __fmaf_rn(a.hi, a.hi, -p))};
+}
+
+// A double as a double-float.
+Dbf split(double x) {
+  const float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
+
+// The spherical reference wave in double-float: source position (x, y) in
+// pixels, a2 = (pitch / lambda)^2, c = (z / lambda)^2, sgn = sign of z.
+struct RefDbf {
+  Dbf x, y, a2, c;
+  float sgn;
+  int kind;
+};
+
+// A real a.hi + a.lo + b, renormalised.
+__device__ __forceinline__ Dbf dbf_add_f(Dbf a, float b) {
+  const Dbf s = two_sum(a.hi, b);
+  return two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+// frac(t) of the reference phase t = sqrt(a2 ((X - x)^2 + (Y - y)^2) + c)
+// cycles at plane pixel (X, Y), |X|, |Y| < 2^24: t reaches 10^6 cycles for a
+// source some 0.4 m away, so it is carried in double-float like the transfer
+// function's phase.
+__device__ __forceinline__ float ref_frac(const RefDbf& r, float X, float Y) {
+  const Dbf ex = dbf_add_f(two_sum(X, -r.x.hi), -r.x.lo), ey = dbf_add_f(two_sum(Y, -r.y.hi), -r.y.lo);
+  const Dbf px = dbf_sqr(ex), py = dbf_sqr(ey);
+  const Dbf rho = two_sum(px.hi, py.hi);
+  const float rl = __fadd_rn(rho.lo, __fadd_rn(px.lo, py.lo));
+  const float p = __fmul_rn(r.a2.hi, rho.hi);
+  const float pe = __fmaf_rn(r.a2.hi, rho.hi, -p) + (r.a2.hi * rl + r.a2.lo * rho.hi);
+  const Dbf t0 = two_sum(p, r.c.hi);
+  const Dbf tt = two_sum(t0.hi, __fadd_rn(t0.lo, __fadd_rn(pe, r.c.lo)));
+  const float y = __fsqrt_rn(tt.hi);
+  const float yy = __fmul_rn(y, y), ye = __fmaf_rn(y, y, -yy);
+  const float corr = __fmul_rn(__fadd_rn(__fsub_rn(__fsub_rn(tt.hi, yy), ye), tt.lo), __fdividef(0.5f, y));
+  float f = __fadd_rn(__fsub_rn(y, floorf(y)), corr);
+  return f - floorf(f);
+}
+
 // U_0 = field, or t R with t the hologram's bit (reference R of the frame).
 __global__ void recon_input_kernel(const float2* __restrict__ field, const uint8_t* __restrict__ bits, int w,
-                                   long long n, int ox, int oy, RefDev ref, float2* __restrict__ buf) {
+                                   long long n, int ox, int oy, RefDbf ref, float2* __restrict__ buf) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     if (field) {
@@ -32,32 +96,47 @@ __global__ void recon_input_kernel(const float2* __restrict__ field, const uint8
     float2 r = make_float2(1.f, 0.f);
     if (ref.kind != 0) {
       const long long y = i / w, x = i - y * w;
-      const double ex = (double)(ox + x) - ref.x, ey = (double)(oy + y) - ref.y;
-      const double tr = sqrt(fma(ref.a2, fma(ex, ex, ey * ey), ref.c));
       float sn, cs;
-      sincospif(2.0f * (float)(tr - floor(tr)), &sn, &cs);
+      sincospif(2.0f * ref_frac(ref, (float)(ox + x), (float)(oy + y)), &sn, &cs);
       r = make_float2(cs, ref.sgn * sn);
     }
     buf[i] = make_float2(t * r.x, t * r.y);
   }
 }
 
-// Spectrum times H / (w h) (the inverse transform is unnormalised).
-__global__ void recon_transfer_kernel(float2* __restrict__ buf, int w, int h, double lambda, double pitch, double d) {
+// Spectrum times H / (w h) (the inverse transform is unnormalised).  The
+// phase d/lambda sqrt(1 - (lambda fx)^2 - (lambda fy)^2) reaches 10^4 cycles
+// and more, so it is carried in double-float to about 2^-44 relative (the
+// square root is one Newton step from the FP32 root), then reduced to
+// [0, 1): FP32 arithmetic only.  ax, ay: lambda / (w pitch) and
+// lambda / (h pitch); cyc: d / lambda.
+__global__ void recon_transfer_kernel(float2* __restrict__ buf, int w, int h, Dbf ax, Dbf ay, Dbf cyc, float norm) {
   const long long n = (long long)w * h;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  const float norm = (float)(1.0 / (double)n);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const int ky = (int)(i / w), kx = (int)(i - (long long)ky * w);
     const int sx = kx <= (w - 1) / 2 ? kx : kx - w;  // FFT frequency order
     const int sy = ky <= (h - 1) / 2 ? ky : ky - h;
-    const double ax = lambda * sx / (w * pitch), ay = lambda * sy / (h * pitch);  // lambda fx, lambda fy
-    const double s = 1.0 - ax * ax - ay * ay;
+    // q = (lambda fx)^2 + (lambda fy)^2, s = 1 - q.
+    const Dbf px = dbf_sqr(dbf_mul_f(ax, (float)sx)), py = dbf_sqr(dbf_mul_f(ay, (float)sy));
+    const Dbf q = two_sum(px.hi, py.hi);
+    const float ql = __fadd_rn(q.lo, __fadd_rn(px.lo, py.lo));
+    const Dbf s0 = two_sum(1.0f, -q.hi);
+    const Dbf sv = two_sum(s0.hi, __fsub_rn(s0.lo, ql));
     float2 v = make_float2(0.f, 0.f);
-    if (s > 0.0) {
-      const double ph = d / lambda * sqrt(s);  // cycles
+    if (sv.hi > 0.f) {
+      // sqrt(s) = y + r: y the FP32 root, r = (s - y^2) / (2 y) with y^2
+      // split exactly (s.hi - y^2 is exact: y^2 lies within a factor 2 of s.hi).
+      const float y = __fsqrt_rn(sv.hi);
+      const float yy = __fmul_rn(y, y), ye = __fmaf_rn(y, y, -yy);
+      const float r = __fmul_rn(__fadd_rn(__fsub_rn(__fsub_rn(sv.hi, yy), ye), sv.lo), __fdividef(0.5f, y));
+      // Phase in cycles: cyc (y + r); p - floor(p) is exact in FP32.
+      const float p = __fmul_rn(cyc.hi, y);
+      const float pe = __fmaf_rn(cyc.hi, y, -p) + (cyc.hi * r + cyc.lo * y);
+      float f = __fadd_rn(__fsub_rn(p, floorf(p)), pe);
+      f -= floorf(f);
       float sn, cs;
-      sincospif(2.0f * (float)(ph - floor(ph)), &sn, &cs);
+      sincospif(2.0f * f, &sn, &cs);
       const float2 u = buf[i];
       v = make_float2((u.x * cs - u.y * sn) * norm, (u.x * sn + u.y * cs) * norm);
     }
@@ -86,19 +165,50 @@ bool make_plan(int w, int h, cufftHandle* plan, size_t* work) {
   return true;
 }
 
+// Plans of the first kPlanCache (device, w, h) shapes live for the process;
+// one mutex serialises every use of them (stream and work area are set per
+// call, then the transforms are enqueued).  Other shapes get a plan for the
+// call only.
+constexpr int kPlanCache = 8;
+struct PlanEntry {
+  int dev, w, h;
+  cufftHandle plan;
+  size_t work;
+};
+PlanEntry g_plans[kPlanCache];
+int g_nplans = 0;
+std::mutex g_plan_mu;
+
+// With g_plan_mu held: the plan of (current device, w, h); *owned is true
+// when the caller must destroy it (the cache is full).
+bool get_plan(int w, int h, cufftHandle* plan, size_t* work, bool* owned) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  for (int i = 0; i < g_nplans; ++i)
+    if (g_plans[i].dev == dev && g_plans[i].w == w && g_plans[i].h == h) {
+      *plan = g_plans[i].plan;
+      *work = g_plans[i].work;
+      *owned = false;
+      return true;
+    }
+  if (!make_plan(w, h, plan, work)) return false;
+  *owned = g_nplans == kPlanCache;
+  if (!*owned) g_plans[g_nplans++] = PlanEntry{dev, w, h, *plan, *work};
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
 
 wasabi_status wasabi_reconstruct_scratch_bytes(int w, int h, size_t* bytes_out) {
   if (w <= 0 || h <= 0 || !bytes_out) { set_error("reconstruct_scratch_bytes: bad arguments"); return WASABI_E_INVALID; }
+  std::lock_guard<std::mutex> lock(g_plan_mu);
   cufftHandle plan;
   size_t work = 0;
-  if (cufftCreate(&plan) != CUFFT_SUCCESS) { set_error("reconstruct: cufftCreate failed"); return WASABI_E_CUDA; }
-  long long dims[2] = {h, w};
-  const cufftResult r = cufftGetSizeMany64(plan, 2, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2C, 1, &work);
-  cufftDestroy(plan);
-  if (r != CUFFT_SUCCESS) { set_error("reconstruct: cufftGetSizeMany64 failed (%d)", (int)r); return WASABI_E_CUDA; }
+  bool owned = false;
+  if (!get_plan(w, h, &plan, &work, &owned)) { set_error("reconstruct: cuFFT plan failed for %d x %d", w, h); return WASABI_E_CUDA; }
+  if (owned) cufftDestroy(plan);  // never executed
   *bytes_out = align256((size_t)w * h * sizeof(float2)) + align256(work);
   return WASABI_OK;
 }
@@ -128,17 +238,31 @@ wasabi_status wasabi_reconstruct(const void* input_dev, int input_kind, int w, i
   RefDev ref;
   const char* why = "";
   if (!frame_to_dev(frame, &ox, &oy, &ref, &why)) { set_error("reconstruct: %s", why); return WASABI_E_INVALID; }
+  // Plane pixel coordinates are exact in FP32 below 2^24.
+  if (std::abs((long long)ox) + w >= (1LL << 24) || std::abs((long long)oy) + h >= (1LL << 24)) {
+    set_error("reconstruct: plane pixels must stay below 2^24 in magnitude");
+    return WASABI_E_INVALID;
+  }
+  RefDbf rd;
+  rd.kind = ref.kind;
+  rd.sgn = ref.sgn;
+  rd.x = split(ref.x);
+  rd.y = split(ref.y);
+  rd.a2 = split(ref.a2);
+  rd.c = split(ref.c);
   int* status;
   int sms;
   if (!device_info(&status, &sms)) return WASABI_E_CUDA;
   const cudaStream_t s = (cudaStream_t)stream;
   const long long n = (long long)w * h;
+  std::lock_guard<std::mutex> lock(g_plan_mu);
   cufftHandle plan;
   size_t work = 0;
-  if (!make_plan(w, h, &plan, &work)) { set_error("reconstruct: cuFFT plan failed for %d x %d", w, h); return WASABI_E_CUDA; }
+  bool owned = false;
+  if (!get_plan(w, h, &plan, &work, &owned)) { set_error("reconstruct: cuFFT plan failed for %d x %d", w, h); return WASABI_E_CUDA; }
   const size_t need = align256((size_t)n * sizeof(float2)) + align256(work);
   if (scratch_bytes < need) {
-    cufftDestroy(plan);
+    if (owned) cufftDestroy(plan);
     set_error("reconstruct: scratch too small (%zu < %zu bytes)", scratch_bytes, need);
     return WASABI_E_NOMEM;
   }
@@ -151,12 +275,13 @@ wasabi_status wasabi_reconstruct(const void* input_dev, int input_kind, int w, i
   if (fr == CUFFT_SUCCESS) {
     recon_input_kernel<<<grid, 256, 0, s>>>(input_kind == WASABI_RECON_FIELD ? static_cast<const float2*>(input_dev)
                                                                              : nullptr,
-                                            static_cast<const uint8_t*>(input_dev), w, n, ox, oy, ref, buf);
+                                            static_cast<const uint8_t*>(input_dev), w, n, ox, oy, rd, buf);
     fr = cufftExecC2C(plan, reinterpret_cast<cufftComplex*>(buf), reinterpret_cast<cufftComplex*>(buf),
                       CUFFT_FORWARD);
   }
   if (fr == CUFFT_SUCCESS) {
-    recon_transfer_kernel<<<grid, 256, 0, s>>>(buf, w, h, lambda, pitch, d);
+    recon_transfer_kernel<<<grid, 256, 0, s>>>(buf, w, h, split(lambda / (w * pitch)), split(lambda / (h * pitch)),
+                                               split(d / lambda), (float)(1.0 / (double)n));
     fr = cufftExecC2C(plan, reinterpret_cast<cufftComplex*>(buf), reinterpret_cast<cufftComplex*>(buf),
                       CUFFT_INVERSE);
   }
@@ -166,9 +291,11 @@ wasabi_status wasabi_reconstruct(const void* input_dev, int input_kind, int w, i
     set_error("reconstruct: cuFFT failed (%d)", (int)fr);
     st = WASABI_E_CUDA;
   }
-  const cudaError_t e = cudaStreamSynchronize(s);  // the plan is destroyed below
-  cufftDestroy(plan);
-  if (st == WASABI_OK && e != cudaSuccess) st = cuda_fail("reconstruct", e);
+  if (owned) {  // a plan for this call only: wait for its transforms before destroying it
+    const cudaError_t e = cudaStreamSynchronize(s);
+    cufftDestroy(plan);
+    if (st == WASABI_OK && e != cudaSuccess) st = cuda_fail("reconstruct", e);
+  }
   if (st == WASABI_OK) {
     const cudaError_t e2 = cudaGetLastError();
     if (e2 != cudaSuccess) st = cuda_fail("reconstruct: launch", e2);

@@ -21,7 +21,8 @@ def w():
     return w
 
 
-@pytest.mark.parametrize("h,wd,d", [(256, 384, -0.5e-3), (200, 136, 1.2e-3), (512, 512, 0.0)])
+# 20 mm: about 3.2e4 cycles of phase, far beyond what FP32 alone carries.
+@pytest.mark.parametrize("h,wd,d", [(256, 384, -0.5e-3), (200, 136, 1.2e-3), (512, 512, 0.0), (128, 160, 20e-3)])
 def test_field_reconstruction_matches_the_oracle(w, orc, h, wd, d):
     rng = np.random.default_rng(h + wd)
     u0 = (rng.normal(size=(h, wd)) + 1j * rng.normal(size=(h, wd))).astype(np.complex64)
@@ -67,3 +68,24 @@ def test_bad_arguments_are_refused(w):
     f = torch.zeros((64, 64), dtype=torch.complex64, device="cuda")
     with pytest.raises(w.WasabiError, match="INVALID"):
         w.reconstruct(f, 64, 64, -LAM, PITCH, 1e-3)
+
+
+def test_plan_cache_shapes_and_streams(w, orc):
+    """More shapes than the plan cache holds (the later ones get a plan per
+    call), then a cached shape again on a side stream: every result matches
+    the oracle."""
+    rng = np.random.default_rng(11)
+    fields = []
+    for i in range(10):
+        h, wd = 32 + 8 * i, 40
+        u0 = (rng.normal(size=(h, wd)) + 1j * rng.normal(size=(h, wd))).astype(np.complex64)
+        got = w.reconstruct(torch.from_numpy(u0).cuda(), wd, h, LAM, PITCH, 0.2e-3, want="complex")
+        assert rel_l2(got.cpu().numpy(), orc.reconstruct(u0, LAM, PITCH, 0.2e-3)) <= 1e-5
+        fields.append(u0)
+    side = torch.cuda.Stream()
+    u0 = fields[0]
+    src = torch.from_numpy(u0).cuda()
+    side.wait_stream(torch.cuda.current_stream())
+    got = w.reconstruct(src, 40, 32, LAM, PITCH, -0.1e-3, want="complex", stream=side)
+    side.synchronize()
+    assert rel_l2(got.cpu().numpy(), orc.reconstruct(u0, LAM, PITCH, -0.1e-3)) <= 1e-5
