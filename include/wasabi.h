@@ -450,7 +450,8 @@ wasabi_status wasabi_server_destroy(wasabi_server* server);
  * z < 0, contributes the conjugate term); aperture = 1 restricts each term to
  * the PSF disk n < R(|z|)^2 and the point's own pixel (the second form of
  * Eq. (1)), 0 sums every pixel.  u_dev: holo_w x holo_h complex64, row-major, overwritten.
- * FP64 is used for the phase reduction r / lambda mod 1, FP32 elsewhere.
+ * The phase r / lambda mod 1 is carried in double-float (pairs of FP32 values,
+ * about 44 bits) and the disk test is exact in integers; FP32 elsewhere.
  * scratch_dev: at least cgh_direct_scratch_bytes() bytes. */
 wasabi_status cgh_direct_scratch_bytes(int64_t n, int holo_w, int holo_h, size_t* bytes_out);
 wasabi_status cgh_direct(double lambda, double pitch, const double* depths_host, int n_depths,

@@ -8,10 +8,13 @@
 // over the kept points in FP32.
 //
 // Phase: r / lambda = sqrt(q) with q = n (p / lambda)^2 + (z / lambda)^2 and
-// n = dx^2 + dy^2.  q is formed in FP64; an FP32 estimate s0 of sqrt(q) is
-// refined by one Newton step whose residual q - s0^2 is taken in FP64 (the
-// reduction r / lambda mod 1 is thus carried out at FP64 accuracy, ~1e-11
-// cycles), and the fractional cycle feeds an FP32 sincospi.
+// n = dx^2 + dy^2.  q is formed in double-float (pairs of FP32 values; the
+// error-free transformations are Knuth's two-sum and the exact product
+// through one fused multiply-add), an FP32 estimate s0 of sqrt(q) is refined
+// by one Newton step whose residual q - s0^2 is exact, so r / lambda mod 1 is
+// carried to about 1e-10 cycles in FP32 arithmetic alone (FP64 runs far
+// slower), and the fractional cycle feeds an FP32 sincospi.  Whether a pixel
+// lies in a disk stays an exact integer test.
 #include "internal.cuh"
 
 namespace wsb {
@@ -27,9 +30,15 @@ __device__ __forceinline__ int floor_div(int a, int b) {
   return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
 }
 
+// a + b = s + e exactly (Knuth's two-sum).
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
 __global__ void __launch_bounds__(kNT) direct_kernel(DirectArgs a) {
   __shared__ int4 list[kCap];
-  __shared__ double lbeta[kCap];
+  __shared__ float4 lbeta[kCap];  // |beta| as hi + lo, the sign of z
   __shared__ long long lnlim[kCap];
   __shared__ int s_tile, s_n, s_nrows, s_total;
   __shared__ int s_rowstart[kMaxRows], s_rowpre[kMaxRows + 1];
@@ -41,6 +50,7 @@ __global__ void __launch_bounds__(kNT) direct_kernel(DirectArgs a) {
   const int ntx = (a.w + kTile - 1) / kTile, nty = (a.h + kTile - 1) / kTile;
   const int ntiles = ntx * nty;
   const int col = tid & 31, row0 = tid >> 5;  // pixels (col, row0 + 8 q), q < 4
+  const float al_h = (float)a.alpha, al_l = (float)(a.alpha - (double)al_h);  // (p / lambda)^2
 
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(a.counter, 1);
@@ -86,7 +96,9 @@ __global__ void __launch_bounds__(kNT) direct_kernel(DirectArgs a) {
         if (ddx * ddx + ddy * ddy < nlim) {
           const int slot = atomicAdd(&s_n, 1);
           list[slot] = p;
-          lbeta[slot] = __ldg(&a.beta_dev[p.w]);
+          const double b = __ldg(&a.beta_dev[p.w]), bm = fabs(b);
+          const float bh = (float)bm;
+          lbeta[slot] = make_float4(bh, (float)(bm - (double)bh), b < 0.0 ? -1.0f : 1.0f, 0.f);
           lnlim[slot] = nlim;
         }
       }
@@ -95,22 +107,33 @@ __global__ void __launch_bounds__(kNT) direct_kernel(DirectArgs a) {
       const int px = X0 + col;
       for (int s = 0; s < n; ++s) {
         const int4 p = list[s];
-        const double beta = fabs(lbeta[s]);
-        const float sgn = lbeta[s] < 0.0 ? -1.0f : 1.0f;  // conjugate term for a point behind the plane
+        const float4 lb = lbeta[s];
+        const float sgn = lb.z;  // conjugate term for a point behind the plane
         const long long nlim = lnlim[s];
         const float amp = __int_as_float(p.z);
         const long long dx = px - p.x;
+        // dx^2 as hi + lo, both exact (|dx| < 2^24).
+        const float fdx = (float)dx, xx = __fmul_rn(fdx, fdx), xe = __fmaf_rn(fdx, fdx, -xx);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const long long dy = Y0 + row0 + 8 * q - p.y;
           const long long nn = dx * dx + dy * dy;
           if (nn < nlim) {
-            const double qd = __fma_rn((double)nn, a.alpha, beta);
-            const float qf = __double2float_rn(qd);
+            // n = dx^2 + dy^2 as hi + lo (exact), then q = alpha n + beta.
+            const float fdy = (float)dy, yy = __fmul_rn(fdy, fdy), ye = __fmaf_rn(fdy, fdy, -yy);
+            const float2 n2 = two_sum(xx, yy);
+            const float nl = __fadd_rn(n2.y, __fadd_rn(xe, ye));
+            const float pa = __fmul_rn(al_h, n2.x);
+            const float pe = __fmaf_rn(al_h, n2.x, -pa) + (al_h * nl + al_l * n2.x);
+            const float2 q0 = two_sum(pa, lb.x);
+            const float2 qv = two_sum(q0.x, __fadd_rn(q0.y, __fadd_rn(pe, lb.y)));
+            // sqrt(q) = s0 + corr: s0 in FP32, the residual q - s0^2 exact
+            // (s0^2 lies within a factor 2 of q.hi).
+            const float qf = qv.x;
             const float r0 = rsqrtf(qf);
-            const float s0 = qf * r0;
-            const double e = __fma_rn(-(double)s0, (double)s0, qd);
-            const float corr = __double2float_rn(e) * (0.5f * r0);
+            const float s0 = __fmul_rn(qf, r0);
+            const float ss = __fmul_rn(s0, s0), se = __fmaf_rn(s0, s0, -ss);
+            const float corr = __fadd_rn(__fsub_rn(__fsub_rn(qf, ss), se), qv.y) * (0.5f * r0);
             const float f = qf > 0.f ? (s0 - floorf(s0)) + corr : 0.f;  // q = 0: a point on the plane
             float sn, cs;
             sincospif(2.0f * f, &sn, &cs);
