@@ -279,7 +279,8 @@ wasabi_status wasabi_inverse_haar_frame(const void* wbuf_dev, int holo_w, int ho
  * permutes the tile-major buffer into the Mallat layout and runs L periodic
  * synthesis levels over the holo_w x holo_h buffer (along y, then x, the
  * transpose of the analysis), then writes u and/or the bits against the
- * frame's reference (phase of a spherical R reduced in FP64 per pixel).
+ * frame's reference (phase of a spherical R carried in double-float, pairs of
+ * FP32 values, per pixel; plane pixels below 2^24 in magnitude).
  * 1 <= levels <= 5; COIF1 needs a square hologram (holo_w == holo_h, the
  * periodic transform's domain), side a multiple of 2^levels (and of 8 for bits).
  * scratch_dev: wasabi_inverse_wavelet_scratch_bytes() bytes (two buffers

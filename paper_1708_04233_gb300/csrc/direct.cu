@@ -15,7 +15,7 @@
 // carried to about 1e-10 cycles in FP32 arithmetic alone (FP64 runs far
 // slower), and the fractional cycle feeds an FP32 sincospi.  Whether a pixel
 // lies in a disk stays an exact integer test.
-#include "internal.cuh"
+#include "dbf.cuh"
 
 namespace wsb {
 namespace {
@@ -28,12 +28,6 @@ constexpr int kMaxRows = 128;
 __device__ __forceinline__ int floor_div(int a, int b) {
   const int q = a / b;
   return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
-}
-
-// a + b = s + e exactly (Knuth's two-sum).
-__device__ __forceinline__ float2 two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
-  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
 }
 
 __global__ void __launch_bounds__(kNT) direct_kernel(DirectArgs a) {
@@ -121,19 +115,19 @@ __global__ void __launch_bounds__(kNT) direct_kernel(DirectArgs a) {
           if (nn < nlim) {
             // n = dx^2 + dy^2 as hi + lo (exact), then q = alpha n + beta.
             const float fdy = (float)dy, yy = __fmul_rn(fdy, fdy), ye = __fmaf_rn(fdy, fdy, -yy);
-            const float2 n2 = two_sum(xx, yy);
-            const float nl = __fadd_rn(n2.y, __fadd_rn(xe, ye));
-            const float pa = __fmul_rn(al_h, n2.x);
-            const float pe = __fmaf_rn(al_h, n2.x, -pa) + (al_h * nl + al_l * n2.x);
-            const float2 q0 = two_sum(pa, lb.x);
-            const float2 qv = two_sum(q0.x, __fadd_rn(q0.y, __fadd_rn(pe, lb.y)));
+            const Dbf n2 = two_sum(xx, yy);
+            const float nl = __fadd_rn(n2.lo, __fadd_rn(xe, ye));
+            const float pa = __fmul_rn(al_h, n2.hi);
+            const float pe = __fmaf_rn(al_h, n2.hi, -pa) + (al_h * nl + al_l * n2.hi);
+            const Dbf q0 = two_sum(pa, lb.x);
+            const Dbf qv = two_sum(q0.hi, __fadd_rn(q0.lo, __fadd_rn(pe, lb.y)));
             // sqrt(q) = s0 + corr: s0 in FP32, the residual q - s0^2 exact
             // (s0^2 lies within a factor 2 of q.hi).
-            const float qf = qv.x;
+            const float qf = qv.hi;
             const float r0 = rsqrtf(qf);
             const float s0 = __fmul_rn(qf, r0);
             const float ss = __fmul_rn(s0, s0), se = __fmaf_rn(s0, s0, -ss);
-            const float corr = __fadd_rn(__fsub_rn(__fsub_rn(qf, ss), se), qv.y) * (0.5f * r0);
+            const float corr = __fadd_rn(__fsub_rn(__fsub_rn(qf, ss), se), qv.lo) * (0.5f * r0);
             const float f = qf > 0.f ? (s0 - floorf(s0)) + corr : 0.f;  // q = 0: a point on the plane
             float sn, cs;
             sincospif(2.0f * f, &sn, &cs);

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "dbf.cuh"
 #include "lut_object.h"
 
 namespace wsb {
@@ -86,19 +87,17 @@ __global__ void coif_syn_rows_kernel(const float2* __restrict__ b, float2* __res
 }
 
 // Re(u conj R) for the frame's reference (R = 1 for the plane wave), phase
-// reduced in FP64 per pixel.
-__device__ __forceinline__ float ref_re(const RefDev& ref, float2 u, long long X, long long Y) {
+// in double-float per pixel.
+__device__ __forceinline__ float ref_re(const RefDbf& ref, float2 u, long long X, long long Y) {
   if (ref.kind == 0) return u.x;
-  const double ex = (double)X - ref.x, ey = (double)Y - ref.y;
-  const double t = sqrt(fma(ref.a2, fma(ex, ex, ey * ey), ref.c));
   float sn, cs;
-  sincospif(2.0f * (float)(t - floor(t)), &sn, &cs);
+  sincospif(2.0f * ref_frac(ref, (float)X, (float)Y), &sn, &cs);
   return fmaf(u.x, cs, ref.sgn * u.y * sn);
 }
 
 // Field and/or bits (eight pixels of a row per thread when bits are wanted).
 __global__ void coif_out_kernel(const float2* __restrict__ a, int w, int h, float2* __restrict__ u,
-                                uint8_t* __restrict__ bits, int ox, int oy, RefDev ref) {
+                                uint8_t* __restrict__ bits, int ox, int oy, RefDbf ref) {
   const int per = bits ? 8 : 1;
   const long long n = (long long)w * h / per;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
@@ -176,6 +175,11 @@ wasabi_status wasabi_inverse_wavelet(const void* wbuf_dev, int holo_w, int holo_
   RefDev ref;
   const char* why = "";
   if (!frame_to_dev(frame, &ox, &oy, &ref, &why)) { set_error("inverse_wavelet: %s", why); return WASABI_E_INVALID; }
+  // Plane pixel coordinates are exact in FP32 below 2^24.
+  if (std::abs((long long)ox) + holo_w >= (1LL << 24) || std::abs((long long)oy) + holo_h >= (1LL << 24)) {
+    set_error("inverse_wavelet: plane pixels must stay below 2^24 in magnitude");
+    return WASABI_E_INVALID;
+  }
   size_t need = 0;
   wasabi_inverse_wavelet_scratch_bytes(holo_w, holo_h, &need);
   if (scratch_bytes < need) {
@@ -189,7 +193,8 @@ wasabi_status wasabi_inverse_wavelet(const void* wbuf_dev, int holo_w, int holo_
   cudaError_t e = launch_coif_inverse(static_cast<const float2*>(wbuf_dev), holo_w, holo_h, levels, a, b, s, u);
   if (e == cudaSuccess && bits_dev) {  // the field is in u when it was asked for, else in a
     const long long groups = (long long)holo_w * holo_h / 8;
-    coif_out_kernel<<<grid_for(groups), 256, 0, s>>>(u ? u : a, holo_w, holo_h, nullptr, bits_dev, ox, oy, ref);
+    coif_out_kernel<<<grid_for(groups), 256, 0, s>>>(u ? u : a, holo_w, holo_h, nullptr, bits_dev, ox, oy,
+                                                     ref_dbf(ref));
     e = cudaGetLastError();
   }
   return e == cudaSuccess ? WASABI_OK : cuda_fail("inverse_wavelet", e);

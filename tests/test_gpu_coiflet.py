@@ -111,3 +111,21 @@ def test_generic_inverse_with_haar_is_the_haar_inverse(w, orc):
     with pytest.raises(w.WasabiError, match="INVALID"):
         w.inverse_wavelet(wb[: 256 * 128], 256, 128, L, "coif1")  # the coiflet inverse is square only
     lut.close()
+
+
+@pytest.mark.parametrize("N,L", [(8, 3), (40, 3), (96, 2), (160, 5)])
+def test_coiflet_inverse_small_and_ragged_regions(w, orc, N, L):
+    """The per-level synthesis on regions narrower than a 32-pixel CTA tile
+    and not multiples of it (wrap-around of the periodic filters inside one
+    tile): field and bits against the oracle's inverse of the same Mallat
+    array."""
+    g = torch.Generator(device="cuda").manual_seed(N + L)
+    wb = torch.randn(N * N, dtype=torch.complex64, device="cuda", generator=g)
+    mallat = w.wbuf_to_mallat(wb, N, N, L).cpu().numpy().astype(np.complex128)
+    ref = orc.wavelet_inv(mallat, L, "coif1")
+    u, bits = w.inverse_wavelet(wb, N, N, L, "coif1", want="both")
+    u_np = u.cpu().numpy()
+    assert rel_l2(u_np, ref) <= 1e-5
+    mine = np.unpackbits(bits.cpu().numpy(), bitorder="little").reshape(N, N).astype(bool)
+    diff = mine != (ref.real > 0)
+    assert np.all(np.abs(ref.real[diff]) <= 1e-5 * np.abs(ref).max())
