@@ -50,3 +50,25 @@ def test_c1_direct(w, orc):
 def test_empty_points(w, orc):
     u = w.cgh_direct(633e-9, 1e-6, [1e-4], torch.empty((0, 4), dtype=torch.int32, device="cuda"), 64, 64)
     assert not u.abs().max().item()
+
+
+def test_far_points_and_large_depths(w, orc):
+    """Aperture off, depths of +-15 mm and points up to 20,000 pixels away:
+    phases of some 4e4 cycles and pixel distances^2 beyond 2^24, where FP32
+    alone would be off by ~1e-3 cycles; the double-float reduction holds the
+    FP64 oracle's rel-L2 <= 1e-5."""
+    lam, pitch, D, Nh, Nv = 633e-9, 1e-6, 4, 96, 64
+    rng = np.random.default_rng(5)
+    n = 24
+    x = rng.integers(-20000, 20000, size=n).astype(np.int32)
+    y = rng.integers(-20000, 20000, size=n).astype(np.int32)
+    x[:4] = [10, 50, -3, 20000]
+    y[:4] = [5, 60, 30, -19999]
+    a = rng.uniform(0.5, 1.0, size=n).astype(np.float32)
+    zd = orc.depth_grid(-15e-3, 15e-3, D)
+    d = rng.integers(0, D, size=n).astype(np.int32)
+    p = w.pack_points(x, y, a, d)
+    u = w.cgh_direct(lam, pitch, zd, p, Nh, Nv, aperture=False).cpu().numpy()
+    w.sync_status()
+    ref = orc.cgh_direct(lam, pitch, x, y, a, zd[d], 0, 0, Nh, Nv, False)
+    assert rel_l2(u, ref) <= 1e-5
