@@ -314,7 +314,8 @@ def reconstruct(hologram: torch.Tensor, w: int, h: int, lam: float, pitch: float
     """Numerical reconstruction (wasabi_reconstruct): the field (want =
     "complex") or intensity (want = "intensity") in the plane at signed
     distance d, by the angular spectrum method.  hologram: an (h, w) complex64
-    field, or packed bits (uint8) illuminated by `reference` (None: R = 1)."""
+    field, or packed bits (uint8) illuminated by `reference` (None: R = 1).
+    Asynchronous on `stream`, like the other calls."""
     kind = _abi.RECON_BITS if hologram.dtype == torch.uint8 else _abi.RECON_FIELD
     dev = hologram.device
     if out is None:
