@@ -371,7 +371,7 @@ class Batch:
         h = C.c_void_p()
         check(_lib().wasabi_batch_create(lut.handle, max_jobs, side_hint, int(use_graph), C.byref(h)))
         self._h = h
-        self._keep = None
+        self._held = None  # the last run's scratch and outputs
 
     def config(self) -> tuple[int, int]:
         c, t = C.c_int(), C.c_int()
@@ -409,7 +409,7 @@ class Batch:
         check(_lib().wasabi_batch_run(self._h, C.cast(arr, C.c_void_p), n, _ptr(scratch),
                                       scratch.numel(), _stream(stream)))
         _keep(stream, scratch, *[o[k] for o in out for k in ("wbuf", "u", "bits")])
-        self._keep = (scratch, out)
+        self._held = (scratch, out)
         return out
 
     def close(self) -> None:
