@@ -35,14 +35,13 @@ UNIT = "Mpoint*coeff/s"
 
 
 # DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum, one ncu capture of the full workload), valid only
-# while the kernel source is the one that was profiled (sha256 prefix of
-# superpose.cu); see profiles/launches_C3_65536sq_fused.md.
+# dram__bytes_write.sum from one ncu capture, scaled to a full launch), valid
+# only while the kernel source is the one that was profiled (sha256 prefix of
+# superpose.cu).
 TRAFFIC = {("C3", "fused"): ("1063342d70b6fe2c", 36.8e6 + 478.7e6)}
-# The same kernel's issue-slot utilisation and instructions per
-# point·coefficient from its full ncu capture (32,768^2 slice of C3,
-# profiles/superpose_fused_bits_C3_32768sq.md): the instruction roofline it
-# is bound by.
+# The same kernel's issue-slot utilisation and warp instructions per
+# point·coefficient from its full ncu capture (32,768^2 slice of C3): the
+# instruction roofline it is bound by.
 ISSUE = {("C3", "fused"): ("1063342d70b6fe2c", 0.711, 4.10)}
 
 
@@ -62,8 +61,7 @@ def _issue(c, path):
     ent = ISSUE.get((c.name, path))
     if ent is None or _superpose_sha() != ent[0]:
         return None
-    return {"ncu_issue_active": ent[1], "warp_instructions_per_point_coeff": ent[2],
-            "profile": "profiles/superpose_fused_bits_C3_32768sq.md"}
+    return {"ncu_issue_active": ent[1], "warp_instructions_per_point_coeff": ent[2]}
 
 
 def max_over_ranks(x: float, device) -> float:

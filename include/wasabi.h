@@ -215,7 +215,11 @@ wasabi_status wasabi_superpose(const wasabi_lut* lut, const wasabi_point* points
  * synchronous runtime query): make that first call before any stream capture.
  * All calls share the array and it keeps the previous call's contents (each
  * call re-initialises what it reads); calls that overlap on the GPU race on
- * it, so serialise them (one stream, or events between streams). */
+ * it, so serialise them (one stream, or events between streams).
+ * The looked-up address is kept for the life of the device's primary
+ * context: resetting the device (cudaDeviceReset) while the library is
+ * loaded is not supported (the library's other per-device state, such as the
+ * status word's address, is kept the same way). */
 wasabi_status wasabi_superpose_static(const wasabi_lut* lut, const wasabi_point* points_dev, int64_t n,
                                       int holo_w, int holo_h, int rule, void* wbuf_dev, void* stream);
 
@@ -504,6 +508,21 @@ wasabi_status wasabi_haar_forward(const void* u_dev, int holo_w, int holo_h, int
                                   void* wbuf_dev, void* stream);
 wasabi_status wasabi_wbuf_to_mallat(const void* wbuf_dev, int holo_w, int holo_h, int levels,
                                     void* mallat_dev, void* stream);
+
+/* Test export: the separate inverse transform to bits (as
+ * wasabi_inverse_haar with u_dev = NULL and the plane reference), except that
+ * the bulk copy of strip `skip_strip` (strips are 256 pixels x 2^levels rows,
+ * numbered row-major) is never issued and every stage wait gives up after
+ * `wait_cycles` SM clock cycles (1 .. 4e9; the normal calls use 4e9, about
+ * 2 s).  The CTA that owns the strip stops waiting, lets its copies in flight
+ * land and exits; the call then reports WASABI_E_TIMEOUT through
+ * wasabi_sync_status, and the context stays usable.  It exercises the failure
+ * path of the bounded waits (failure detection without a GPU fault); the bits
+ * of the skipped strip and of the strips after it in that CTA are left
+ * unwritten. */
+wasabi_status wasabi_test_inverse_stall(const void* wbuf_dev, int holo_w, int holo_h, int levels,
+                                        uint8_t* bits_dev, int64_t skip_strip, int64_t wait_cycles,
+                                        void* stream);
 
 #ifdef __cplusplus
 }

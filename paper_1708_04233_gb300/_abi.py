@@ -50,6 +50,7 @@ SIGNATURES = [
     ("wasabi_sync_status", _i, [_VP]),
     ("wasabi_haar_forward", _i, [_VP, _i, _i, _i, _VP, _VP]),
     ("wasabi_wbuf_to_mallat", _i, [_VP, _i, _i, _i, _VP, _VP]),
+    ("wasabi_test_inverse_stall", _i, [_VP, _i, _i, _i, _VP, _i64, _i64, _VP]),
     ("wasabi_batch_create", _i, [_VP, _i, _i, _i, C.POINTER(_VP)]),
     ("wasabi_batch_destroy", _i, [_VP]),
     ("wasabi_batch_config", _i, [_VP, C.POINTER(_i), C.POINTER(_i)]),

@@ -517,3 +517,16 @@ def wbuf_to_mallat(wbuf: torch.Tensor, w: int, h: int, levels: int, stream=None)
     check(_lib().wasabi_wbuf_to_mallat(_ptr(wbuf), w, h, levels, _ptr(out), _stream(stream)))
     _keep(stream, out)
     return out
+
+
+def inverse_stall_for_test(wbuf: torch.Tensor, w: int, h: int, levels: int, skip_strip: int, wait_cycles: int,
+                       bits: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Test export (wasabi_test_inverse_stall): the inverse transform to bits
+    with strip `skip_strip`'s copy never issued and stage waits bounded by
+    `wait_cycles`; sync_status() then raises WASABI_E_TIMEOUT."""
+    if bits is None:
+        bits = torch.zeros((h * w + 7) // 8, dtype=torch.uint8, device=wbuf.device)
+    check(_lib().wasabi_test_inverse_stall(_ptr(wbuf), w, h, levels, _ptr(bits), skip_strip, wait_cycles,
+                                           _stream(stream)))
+    _keep(stream, wbuf, bits)
+    return bits

@@ -14,7 +14,7 @@ import shutil
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-CSRC = os.environ.get("WASABI_CSRC") or os.path.join(HERE, "csrc")  # another source tree, for experiments
+CSRC = os.path.join(HERE, "csrc")
 OUT = os.environ.get("WASABI_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwasabi.so")
 ROOT = os.path.dirname(HERE)

@@ -33,6 +33,7 @@ std::mutex g_mu;
 constexpr int kMaxDev = 64;
 int* g_status_ptr[kMaxDev] = {nullptr};
 int g_num_sms[kMaxDev] = {0};
+cudaMemPool_t g_pool[kMaxDev] = {nullptr};
 
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
@@ -56,15 +57,24 @@ bool device_info(int** status, int* sms) {
     int n = 0;
     e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) { set_error("cudaDeviceGetAttribute: %s", cudaGetErrorString(e)); return false; }
+    // The library's own stream-ordered pool (LUT blocks and build scratch):
+    // memory freed to it stays mapped for the next build instead of being
+    // released at every synchronisation.  A pool of its own, so that the
+    // device's default pool, which the host application may use, keeps its
+    // settings.
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) { set_error("cudaMemPoolCreate: %s", cudaGetErrorString(e)); return false; }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = pool;
     g_status_ptr[dev] = static_cast<int*>(p);
     g_num_sms[dev] = n;
-    // Stream-ordered scratch (LUT builds) is freed back to the default pool;
-    // keep it there instead of unmapping it at every synchronisation.
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-      uint64_t keep = UINT64_MAX;
-      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    }
   }
   if (status) *status = g_status_ptr[dev];
   if (sms) *sms = g_num_sms[dev];
@@ -73,6 +83,12 @@ bool device_info(int** status, int* sms) {
   // (non-sticky) error is cleared now.
   cudaGetLastError();
   return true;
+}
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+  const int dev = current_device();
+  if (dev < 0 || dev >= kMaxDev || !g_pool[dev]) return cudaErrorInitializationError;
+  return cudaMallocFromPoolAsync(p, bytes, g_pool[dev], s);
 }
 
 wasabi_status cuda_fail(const char* what, cudaError_t e) {
@@ -413,7 +429,7 @@ wasabi_status wasabi_build_lut_wavelet(double lambda, double pitch, const double
   }
   c.take<uint2>((size_t)lut->ncode * (size_t)base);                 // plane-code records
   const size_t persist_bytes = align_up(c.off, 256);
-  cudaError_t e = cudaMallocAsync(&lut->block, persist_bytes, s);
+  cudaError_t e = pool_alloc(&lut->block, persist_bytes, s);
   if (e != cudaSuccess) { delete lut; set_error("build_lut: cudaMallocAsync: %s", cudaGetErrorString(e)); return WASABI_E_NOMEM; }
   c = Carver();
   c.base = static_cast<char*>(lut->block);
@@ -455,7 +471,7 @@ wasabi_status wasabi_build_lut_wavelet(double lambda, double pitch, const double
   sc.take<long long>((size_t)n_depths + 1);
   sc.take<int>((size_t)n_depths);
   void* scratch = nullptr;
-  e = cudaMallocAsync(&scratch, align_up(sc.off, 256), s);
+  e = pool_alloc(&scratch, align_up(sc.off, 256), s);
   if (e != cudaSuccess) {
     cudaFreeAsync(lut->block, s);
     delete lut;
@@ -828,8 +844,33 @@ wasabi_status wasabi_inverse_haar(const void* wbuf_dev, int holo_w, int holo_h, 
   return wasabi_inverse_haar_frame(wbuf_dev, holo_w, holo_h, levels, nullptr, u_dev, bits_dev, stream);
 }
 
+namespace {
+wasabi_status inverse_haar_impl(const void* wbuf_dev, int holo_w, int holo_h, int levels, const wasabi_frame* frame,
+                                void* u_dev, uint8_t* bits_dev, long long wait_limit, long long skip_item,
+                                void* stream);
+}  // namespace
+
 wasabi_status wasabi_inverse_haar_frame(const void* wbuf_dev, int holo_w, int holo_h, int levels,
                                         const wasabi_frame* frame, void* u_dev, uint8_t* bits_dev, void* stream) {
+  return inverse_haar_impl(wbuf_dev, holo_w, holo_h, levels, frame, u_dev, bits_dev, kInverseWaitCycles, -1, stream);
+}
+
+wasabi_status wasabi_test_inverse_stall(const void* wbuf_dev, int holo_w, int holo_h, int levels, uint8_t* bits_dev,
+                                        int64_t skip_strip, int64_t wait_cycles, void* stream) {
+  if (wait_cycles < 1 || wait_cycles > kInverseWaitCycles || skip_strip < 0) {
+    set_error("test_inverse_stall: need 0 <= skip_strip and 1 <= wait_cycles <= %lld", kInverseWaitCycles);
+    return WASABI_E_INVALID;
+  }
+  return inverse_haar_impl(wbuf_dev, holo_w, holo_h, levels, nullptr, nullptr, bits_dev, wait_cycles, skip_strip,
+                           stream);
+}
+
+}  // extern "C"
+
+namespace {
+wasabi_status inverse_haar_impl(const void* wbuf_dev, int holo_w, int holo_h, int levels, const wasabi_frame* frame,
+                                void* u_dev, uint8_t* bits_dev, long long wait_limit, long long skip_item,
+                                void* stream) {
   int fox, foy;
   RefDev fref;
   const char* why = "";
@@ -864,9 +905,14 @@ wasabi_status wasabi_inverse_haar_frame(const void* wbuf_dev, int holo_w, int ho
   ia.ox = fox;
   ia.oy = foy;
   ia.ref = fref;
+  ia.wait_limit = wait_limit;
+  ia.skip_item = skip_item;
   const cudaError_t e = launch_inverse(ia, (cudaStream_t)stream);
   return e == cudaSuccess ? WASABI_OK : cuda_fail("inverse_haar: launch", e);
 }
+}  // namespace
+
+extern "C" {
 
 namespace {
 int direct_cell(int w, int h, bool aperture) {

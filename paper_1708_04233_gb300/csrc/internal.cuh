@@ -369,7 +369,11 @@ struct InverseArgs {
   int num_sms;
   int ox, oy;               // plane pixel of the output's pixel (0, 0)
   RefDev ref;               // reference wave of the bits
+  long long wait_limit;     // clock cycles a stage wait may take before E_TIMEOUT
+  long long skip_item;      // test only: strip whose copy is never issued (-1: none)
 };
+// Default bound on one stage wait of the inverse kernel (about 2 s).
+constexpr long long kInverseWaitCycles = 4000000000ll;
 cudaError_t launch_inverse(const InverseArgs& a, cudaStream_t s);
 // Strips of one hologram as the inverse kernel cuts it (256 pixels x 2^L rows).
 int inverse_strips(int w, int h, int L);

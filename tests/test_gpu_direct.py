@@ -72,3 +72,29 @@ def test_far_points_and_large_depths(w, orc):
     w.sync_status()
     ref = orc.cgh_direct(lam, pitch, x, y, a, zd[d], 0, 0, Nh, Nv, False)
     assert rel_l2(u, ref) <= 1e-5
+
+
+def test_c2_direct_sampled_regions(w, orc):
+    """Eq. (1) at the full C2 size (8,192^2, 100,000 height-field points, 64
+    depths) as the benchmark runs it, against the FP64 oracle on 256 x 256
+    regions (a corner and two interior regions).  Points farther than the
+    largest support radius from a region add nothing to it (aperture form),
+    so only those within reach are handed to the oracle."""
+    c = CONFIGS["C2"]
+    pts = c.points()
+    zd = orc.depth_grid(c.zmin, c.zmax, c.D)
+    d, bad = orc.quantize(pts["z"], c.zmin, c.zmax, c.D)
+    assert bad == 0
+    p = w.pack_points(pts["x"], pts["y"], pts["a"], d)
+    u = w.cgh_direct(c.lam, c.pitch, zd, p, c.Nh, c.Nh)
+    w.sync_status()
+    rmax = float(orc.support_radius(c.lam, c.pitch, zd.max())) + 2
+    S = 256
+    g = np.random.default_rng(11)
+    for ox, oy in [(0, 0)] + [tuple(int(v) for v in g.integers(0, c.Nh - S, 2)) for _ in range(2)]:
+        near = ((pts["x"] >= ox - rmax) & (pts["x"] < ox + S + rmax) &
+                (pts["y"] >= oy - rmax) & (pts["y"] < oy + S + rmax))
+        ref = orc.cgh_direct(c.lam, c.pitch, pts["x"][near], pts["y"][near], pts["a"][near], zd[d[near]],
+                             ox, oy, S, S, True, threads=NPROC)
+        got = u[oy:oy + S, ox:ox + S].cpu().numpy()
+        assert rel_l2(got, ref) <= 1e-5, (ox, oy)

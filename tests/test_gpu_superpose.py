@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+from tests._bounds import FieldBound, check_bits, check_field
 from tests._helpers import rel_l2, tile_major_to_mallat
 from workloads import CONFIGS, aligned, uniform_cloud
 
@@ -68,9 +69,13 @@ def test_c1_wavelet_buffer_and_field(w, orc, c1, rule):
     u = w.inverse_haar(wbuf, c.Nh, c.Nh, c.L).cpu().numpy()
     w.sync_status()
     psi = orc.superpose(olut, pts, c.Nh, rule=rule)
-    assert rel_l2(tile_major_to_mallat(wbuf.cpu().numpy(), c.Nh, c.Nh, c.L), psi) <= TOL
+    got = tile_major_to_mallat(wbuf.cpu().numpy(), c.Nh, c.Nh, c.L)
+    assert rel_l2(got, psi) <= TOL
+    fb = FieldBound(orc, olut, pts, c.Nh, rule=rule)
+    check_field(got, psi, fb.coeffs(c.Nh, 0, 0))
     ref = orc.haar_inv(psi, c.L)
     assert rel_l2(u, ref) <= TOL
+    check_field(u, ref, fb.window(c.Nh, 0, 0))
 
 
 def test_c1_wasabi_vs_eq1_reported(w, orc, c1):
@@ -194,3 +199,41 @@ def test_fixed_point_is_deterministic_and_matches_float(w, orc, monkeypatch, c1)
     psi = orc.superpose(olut, pts, c.Nh)
     assert rel_l2(tile_major_to_mallat(f1, c.Nh, c.Nh, c.L), psi) <= TOL
     assert rel_l2(a1, f1) <= TOL
+
+
+@pytest.mark.parametrize("want,T", [("bits", 256), ("both", 192)])
+def test_widest_tiles_many_candidate_batches(w, orc, monkeypatch, want, T):
+    """The benchmark's launch configurations on a hologram small enough for
+    the whole-field oracle: 1,024-thread CTAs on 256-pixel super-tiles with
+    real-part accumulation (bits alone) and on 192-pixel super-tiles with
+    complex accumulation, C3's optics and LUT shape (633 nm, W = 1024, L = 4,
+    keep 1%, z in [0.1, 1.0] mm), and enough points within reach of every
+    super-tile that its candidates need several batches (a batch holds at
+    most 8,192 LUT ranges).  Element-wise bounds on every pixel."""
+    monkeypatch.setenv("WASABI_SUPERPOSE_T", str(T))
+    monkeypatch.setenv("WASABI_SUPERPOSE_THREADS", "1024")
+    lam, pitch, zmin, zmax, D, W, L, gamma, Nh, N = 633e-9, 1e-6, 0.1e-3, 1.0e-3, 16, 1024, 4, 0.01, 1024, 1800
+    pts = uniform_cloud(77, N, Nh, zmin, zmax)
+    r = np.random.default_rng(77)
+    pts["x"] = r.integers(-300, Nh + 300, N).astype(np.int32)
+    pts["y"] = r.integers(-300, Nh + 300, N).astype(np.int32)
+    zd = orc.depth_grid(zmin, zmax, D)
+    pts["d"], _ = orc.quantize(pts["z"], zmin, zmax, D)
+    olut = orc.build_lut(lam, pitch, zd, W, L, gamma, threads=NPROC)
+    lut = w.build_lut(lam, pitch, zd, W, L, gamma)
+    for d in range(D):
+        assert np.array_equal(lut.selection(d), olut.depth(d)[0]), d
+    p = w.pack_points(pts["x"], pts["y"], pts["a"], pts["d"])
+    ref = orc.hologram(olut, pts, Nh)
+    bnd = FieldBound(orc, olut, pts, Nh).window(Nh, 0, 0)
+    out = w.hologram(lut, p, Nh, Nh, want=want)
+    w.sync_status()
+    bits = out if want == "bits" else out[1]
+    mine = np.unpackbits(bits.view(Nh, Nh // 8).cpu().numpy(), axis=1, bitorder="little").astype(bool)
+    flips = check_bits(mine, ref, bnd)
+    if want == "both":
+        got = out[0].cpu().numpy()
+        assert rel_l2(got, ref) <= TOL
+        check_field(got, ref, bnd)
+    print(f"{want} T={T}: {flips} bit flips of {Nh * Nh}")
+    lut.close()
