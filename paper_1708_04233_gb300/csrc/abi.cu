@@ -213,12 +213,12 @@ void superpose_config(const wasabi_lut* lut, int w, int h, int kind, int* cell, 
   }
   T = env_int("WASABI_SUPERPOSE_T", T);
   nt = env_int("WASABI_SUPERPOSE_THREADS", nt);
-  T = std::min(T, 256);
+  T = std::min(T, kMaxSuperTile);
   T = std::max(T, std::max(1 << lut->L, 32));
   // A multiple of 32 pixels (one word of the packed binary output) and of 2^L.
   const int unit = std::max(1 << lut->L, 32);
   T = std::max(unit, T / unit * unit);
-  while (T > unit && superpose_smem_bytes(T, lut->L, lut->lmin, lut->D, false, 2048) > 220 * 1024)
+  while (T > unit && superpose_smem_bytes(T, lut->L, lut->lmin, lut->D, false, superpose_min_range_cap()) > 220 * 1024)
     T = std::max(unit, T / 2 / unit * unit);
   nt = std::max(superpose_min_threads(), std::min(1024, nt / 32 * 32));
   *cell = T;
@@ -425,7 +425,7 @@ wasabi_status wasabi_build_lut_wavelet(double lambda, double pitch, const double
   c.take<unsigned>(1);                                               // levels
   {
     const int unit = std::max(1 << levels, 32);  // super-tile sides: multiples of 32 and of 2^L
-    for (int T = unit; T <= 256 && lut->ncode < kMaxCodes; T += unit) lut->code_k[lut->ncode++] = T >> levels;
+    for (int T = unit; T <= kMaxSuperTile && lut->ncode < kMaxCodes; T += unit) lut->code_k[lut->ncode++] = T >> levels;
   }
   c.take<uint2>((size_t)lut->ncode * (size_t)base);                 // plane-code records
   const size_t persist_bytes = align_up(c.off, 256);
@@ -794,7 +794,7 @@ wasabi_status wsb::superpose_impl(const wasabi_lut* lut, const wasabi_point* poi
   int* status;
   int sms;
   if (!device_info(&status, &sms)) return WASABI_E_CUDA;
-  if (cell < std::max(1 << lut->L, 32) || cell > 256 || cell % std::max(1 << lut->L, 32) ||
+  if (cell < std::max(1 << lut->L, 32) || cell > kMaxSuperTile || cell % std::max(1 << lut->L, 32) ||
       threads < superpose_min_threads() || threads > 1024 || threads % 32) {
     set_error("superpose: bad configuration (super-tile %d, %d threads)", cell, threads);
     return WASABI_E_INVALID;

@@ -336,7 +336,7 @@ wasabi_status wasabi_autotune(wasabi_lut* lut, int holo_side, int64_t n_points, 
   const int cells[] = {64, 128, 192, 256};
   const int tcounts[] = {256, 384, 512, 1024};
   for (int cell : cells) {
-    if (cell < std::max(1 << lut->L, 32) || superpose_smem_bytes(cell, lut->L, lut->lmin, lut->D, false, 2048) > 220 * 1024)
+    if (cell < std::max(1 << lut->L, 32) || superpose_smem_bytes(cell, lut->L, lut->lmin, lut->D, false, superpose_min_range_cap()) > 220 * 1024)
       continue;
     for (int nt : tcounts) {
       if (nt < superpose_min_threads()) continue;

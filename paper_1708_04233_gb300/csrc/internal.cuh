@@ -42,11 +42,12 @@ __host__ __device__ inline void unpack_pos(uint32_t pos, int* p, int* q, int* le
 // first.  Rows are G_l + 1 cells apart and planes are padded to 4 modulo 16
 // cells, so that lanes adding into neighbouring rows or other bands of the
 // same cells fall into different shared-memory banks.  A coefficient's plane
-// code is (l << 29) | (band plane * plane size + q * row + p) with (p, q) its
-// window-relative position: adding a survivor's per-level base (its shift of
-// Eq. (2), the guard and the level's offset) gives the accumulator index,
-// with no bounds test (every visited coefficient lands inside the guard band
-// by construction of the LUT ranges).
+// code is (l << 29) | 4 (band plane * plane size + q * row + p) with (p, q)
+// its window-relative position -- the byte offset of its cell's 32-bit word:
+// adding a survivor's per-level base (its shift of Eq. (2), the guard and the
+// level's offset, in the same units) gives the accumulator address, with no
+// bounds test (every visited coefficient lands inside the guard band by
+// construction of the LUT ranges).
 __host__ __device__ inline int plane_side(int k, int L, int l) { return (k + 2) << (L - l); }
 __host__ __device__ inline int plane_row(int k, int L, int l) { return plane_side(k, L, l) + 1; }
 __host__ __device__ inline int plane_size(int k, int L, int l) {
@@ -59,7 +60,7 @@ __host__ __device__ inline uint32_t plane_code(uint32_t pos, int L, int k) {
   unpack_pos(pos, &p, &q, &lev, &band);
   if (lev < 1 || lev > L) return 0;  // unused capacity: never visited
   const int bi = lev == L ? band : band - 1;
-  return ((uint32_t)lev << 29) | (uint32_t)(bi * plane_size(k, L, lev) + q * plane_row(k, L, lev) + p);
+  return ((uint32_t)lev << 29) | (uint32_t)(4 * (bi * plane_size(k, L, lev) + q * plane_row(k, L, lev) + p));
 }
 // Accumulator size (cells, a multiple of 4) for levels lmin..L.
 __host__ __device__ inline int plane_total(int k, int L, int lmin) {
@@ -67,9 +68,11 @@ __host__ __device__ inline int plane_total(int k, int L, int lmin) {
   for (int l = lmin; l <= L; ++l) n += plane_count(L, l) * plane_size(k, L, l);
   return (n + 3) & ~3;
 }
+// Widest super-tile (pixels) the superposition takes.
+constexpr int kMaxSuperTile = 256;
 // Most plane codes a LUT keeps: one per super-tile width k the superposition
-// can use (super-tiles are multiples of 32 pixels, at most 256).
-constexpr int kMaxCodes = 8;
+// can use (super-tiles are multiples of 32 pixels, at most kMaxSuperTile).
+constexpr int kMaxCodes = kMaxSuperTile / 32;
 
 // Slot of (level, band, ix, iy) inside a 2^L x 2^L tile (m = L - level).
 __host__ __device__ inline int tile_slot(int L, int lev, int band, int ix, int iy) {
@@ -340,7 +343,7 @@ struct SuperposeArgs {
   int acc_float;        // 0: exact fixed-point accumulation, 1: FP32 atomics
   int re_only;          // 1: accumulate real parts only (every job wants bits alone)
   int has_ref;          // 1: some job binarises against a spherical reference wave
-  int rcap;             // LUT ranges per candidate batch (superpose_range_cap)
+  int rcap;             // passes per window (superpose_range_cap); survivors per batch rcap / 2, at most 1,024
   int* status;
   int threads;          // block size
   int grid;             // SMs: the launch puts as many CTAs on each as fit
@@ -350,6 +353,8 @@ size_t superpose_smem_bytes(int cell, int L, int lmin, int D, bool re_only, int 
 // Range capacity for a launch: larger when only real parts are accumulated
 // and the freed shared memory still lets two CTAs share an SM.
 int superpose_range_cap(int cell, int L, int lmin, int D, bool re_only, int threads);
+// The smallest pass capacity a launch may use (shared-memory feasibility checks).
+int superpose_min_range_cap();
 // Kinds of superposition launch, for the default configuration.
 // kConfigShared: the configuration batches use, and every call on a hologram
 // below kConfigLargeSide pixels a side (so such a call and a batch job give

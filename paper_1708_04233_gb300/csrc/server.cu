@@ -71,7 +71,6 @@ class Arena {
   }
   static size_t granule(size_t b) { return align_up(std::max<size_t>(b, 1), 256); }
   size_t size() const { return size_; }
-  size_t used() const { return used_; }
   size_t peak() const { return peak_; }
 
  private:

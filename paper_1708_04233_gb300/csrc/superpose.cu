@@ -2,9 +2,8 @@
 // the inverse transform and binarisation fused into its epilogue.
 //
 // The hologram is cut into super-tiles of T x T pixels (k = T / 2^L tiles a
-// side).  Persistent CTAs (two per SM, so that one CTA's latency-bound
-// phases overlap the other's) claim super-tiles from a global counter; for
-// each one a CTA
+// side).  Persistent CTAs claim super-tiles from a global counter; for each
+// one a CTA
 //   1. zeroes its shared-memory accumulator: one plane per kept (level, band)
 //      covering the super-tile and a guard band one tile wide (levels finer
 //      than the LUT's finest kept level are known to stay zero);
@@ -12,23 +11,26 @@
 //      survivors whose footprint (window-tile box of their depth, shifted,
 //      plus one tile of carry) meets the super-tile; for each kept level it
 //      folds the point's shift of Eq. (2) into one accumulator base;
-//   3. turns every survivor into one LUT range per window-tile row that can
-//      land in the super-tile (contiguous by construction of the LUT); one
-//      block-wide scan both drops empty ranges and prefix-sums their lengths
-//      into a flat list of coefficient visits;
-//   4. splits the visits evenly over the warps; each warp walks a contiguous
-//      slice 32 visits at a time (coalesced LUT loads), finds each lane's
-//      range with one shared-memory load and a warp OR-reduction, and adds
-//      a_j * c at base + plane code (no bounds test: coefficients that land
-//      outside the super-tile fall into the guard band and are dropped);
+//   3. cuts every survivor's LUT entries that can land in the super-tile into
+//      passes of at most 32 consecutive entries: one LUT range per window-tile
+//      row (contiguous by construction of the LUT), split every 32 entries.
+//      A block-wide scan numbers the passes, so the list is the same in every
+//      run;
+//   4. deals the passes evenly to the warps; a warp takes one pass at a time
+//      (four in flight), lane i visiting entry i of the pass: one 8-byte
+//      record load (plane code, value), the survivor's level base from shared
+//      memory, a_j * c, one shared-memory add at base + code (no bounds test:
+//      coefficients that land outside the super-tile fall into the guard band
+//      and are dropped);
 //   5. writes the finished super-tile once: to the tile-major wavelet buffer
 //      (streaming vector stores, zeros for absent levels) and/or, through the
 //      inverse transform in shared memory, as the complex field or the packed
-//      binary hologram.
+//      binary hologram (each thread rebuilds 8 x 8 pixel blocks).
 // Every output element is written exactly once: no global atomics and no
 // zeroing pass.  Shared-memory atomics resolve collisions between survivors.
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -39,13 +41,21 @@ namespace wsb {
 namespace {
 
 constexpr int kMaxCellRows = 256;
-constexpr int kRangeCap = 2048;  // LUT ranges per batch (complex accumulation)
-constexpr int kRangeMax = 8192;  // LUT ranges per batch, at most (threads x kPerMax)
-constexpr int kPerMax = 8;       // range slots per thread (block size >= 256)
-constexpr int kLookahead = 32;   // range starts one visit lookup reads (one per lane)
+constexpr int kPass = 64;         // LUT entries per pass (two per lane)
+constexpr int kPassUnroll = 2;    // passes a warp has in flight
+constexpr int kRangeMin = 1024;   // pass capacity per window, at least
+constexpr int kRangeMax = 8192;   // pass capacity per window, at most
+constexpr int kSurvMax = 1024;    // survivors per candidate batch, at most
 // Dynamic shared memory per CTA that still lets two CTAs share an SM (with
 // the kernel's static shared memory and the per-CTA reservation).
 constexpr size_t kTwoCtaSmem = 104 * 1024;
+constexpr size_t kOneCtaSmem = 220 * 1024;
+
+// Survivors per candidate batch for a pass capacity.
+__host__ __device__ inline int survivor_cap(int rcap) {
+  const int p = rcap / 2;
+  return p < kSurvMax ? p : kSurvMax;
+}
 
 __device__ __forceinline__ int floor_div(int a, int b) {
   const int q = a / b;
@@ -67,30 +77,29 @@ __device__ __forceinline__ float2 decode16(uint32_t q, float s) {
   return make_float2(re * s, im * s);
 }
 
-// Exclusive scan over the block of one 64-bit value per thread; returns the
-// prefix and writes the total to *total (all threads).
-__device__ __forceinline__ unsigned long long block_scan64(unsigned long long v, unsigned long long* total,
-                                                           unsigned long long* warp_buf) {
+// Exclusive scan over the block of one int per thread; returns the prefix and
+// writes the total to *total (all threads).
+__device__ __forceinline__ int block_scan(int v, int* total, int* warp_buf) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  unsigned long long x = v;
+  int x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
   if (lane == 31) warp_buf[wid] = x;
   __syncthreads();
   if (wid == 0) {
-    unsigned long long t = lane < nw ? warp_buf[lane] : 0ull;
+    int t = lane < nw ? warp_buf[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
       if (lane >= o) t += y;
     }
     warp_buf[lane] = t;
   }
   __syncthreads();
-  const unsigned long long excl = (wid ? warp_buf[wid - 1] : 0ull) + x - v;
+  const int excl = (wid ? warp_buf[wid - 1] : 0) + x - v;
   *total = warp_buf[31];
   __syncthreads();
   return excl;
@@ -107,22 +116,16 @@ __device__ __forceinline__ int last_le(const int* pre, int lo, int hi, int v) {
 
 struct Smem {
   float2* acc;   // accumulator planes (plane_total cells: complex, or real parts only), see plane_code
-  int4* sp;      // survivors: Ax, Ay, depth, unused
-  int2* svb;     // survivors x kept levels: accumulator base of the level, amplitude bits
-  int2* rrec;    // ranges: LUT offset minus visit prefix, survivor
-  int* rpre;     // ranges: visit prefix (range capacity + 1)
+  int4* sp;      // survivors: Ax, Ay, depth, amplitude bits (a_j times the fixed-point scale)
+  int* sb;       // survivors x 8: at index l, the byte offset of level l's base cell minus (l << 29)
+  int4* pass;    // passes: first LUT entry, entries, shared address of the survivor's sb row, amplitude bits
   int2* dbox;    // depths: tlo, thi
 };
-
-__host__ __device__ inline int survivor_cap(int k, int rcap) {
-  const int p = rcap / (k + 1);
-  return p < 1024 ? p : 1024;
-}
 
 __host__ __device__ inline size_t smem_layout(int T, int L, int lmin, int D, bool re_only, int rcap, Smem* s,
                                               unsigned char* base) {
   const int k = T >> L;
-  const int P = survivor_cap(k, rcap);
+  const int P = survivor_cap(rcap);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -131,38 +134,46 @@ __host__ __device__ inline size_t smem_layout(int T, int L, int lmin, int D, boo
   };
   unsigned char* p0 = take((size_t)plane_total(k, L, lmin) * (re_only ? sizeof(float) : sizeof(float2)));
   unsigned char* p1 = take((size_t)P * sizeof(int4));
-  unsigned char* p2 = take((size_t)P * (L - lmin + 1) * sizeof(int2));
-  unsigned char* p3 = take((size_t)(rcap + 1) * sizeof(int2));
-  unsigned char* p4 = take((size_t)(rcap + 1 + kLookahead) * sizeof(int));
-  unsigned char* p5 = take((size_t)D * sizeof(int2));
+  unsigned char* p2 = take((size_t)P * 8 * sizeof(int));
+  unsigned char* p3 = take((size_t)(rcap + kPassUnroll) * sizeof(int4));  // + spare slots read past the end
+  unsigned char* p4 = take((size_t)D * sizeof(int2));
   if (s) {
     s->acc = reinterpret_cast<float2*>(p0);
     s->sp = reinterpret_cast<int4*>(p1);
-    s->svb = reinterpret_cast<int2*>(p2);
-    s->rrec = reinterpret_cast<int2*>(p3);
-    s->rpre = reinterpret_cast<int*>(p4);
-    s->dbox = reinterpret_cast<int2*>(p5);
+    s->sb = reinterpret_cast<int*>(p2);
+    s->pass = reinterpret_cast<int4*>(p3);
+    s->dbox = reinterpret_cast<int2*>(p4);
   }
   return off;
 }
 
-// Optional per-phase cycle counters (thread 0 of each CTA, summed over CTAs),
-// compiled in only with -DWASABI_PHASE_TIMERS for profiling builds.
-#ifdef WASABI_PHASE_TIMERS
-#define PT_MARK(i)                    \
-  do {                                \
-    if (tid == 0) {                   \
-      const long long t_ = clock64(); \
-      pt[i] += t_ - pt_last;          \
-      pt_last = t_;                   \
-    }                                 \
-  } while (0)
-#else
-#define PT_MARK(i) \
-  do {             \
-  } while (0)
-#endif
-
+// Shared-memory accesses by 32-bit shared-window address (the hot loops keep
+// their addresses in this form: one register, no generic-address arithmetic).
+__device__ __forceinline__ unsigned sh_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ int lds32(unsigned a) {
+  int v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int2 lds64(unsigned a) {
+  int2 v;
+  asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int4 lds128(unsigned a) {
+  int4 v;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+// Shared-memory add without return, only where lane < n.
+__device__ __forceinline__ void red_add_lt(unsigned a, int v, int lane, int n) {
+  asm volatile("{\n .reg .pred q;\n setp.lt.s32 q, %2, %3;\n @q red.shared.add.s32 [%0], %1;\n}" ::"r"(a), "r"(v),
+               "r"(lane), "r"(n));
+}
+__device__ __forceinline__ void red_add_lt(unsigned a, float v, int lane, int n) {
+  asm volatile("{\n .reg .pred q;\n setp.lt.s32 q, %2, %3;\n @q red.shared.add.f32 [%0], %1;\n}" ::"r"(a), "f"(v),
+               "r"(lane), "r"(n));
+}
 // Bit i of an 8-bit value moved to bit 4 i.
 __device__ __forceinline__ unsigned spread_nibbles(unsigned x) {
   x = (x | (x << 12)) & 0x000f000fu;
@@ -172,8 +183,10 @@ __device__ __forceinline__ unsigned spread_nibbles(unsigned x) {
 }
 
 // Inverse transform (Sec. 1, step 3) and binarisation (Sec. 2) of a finished
-// super-tile, straight from the shared-memory accumulator: the wavelet
-// buffer never goes to global memory.  Levels finer than lmin were never
+// super-tile, straight from the shared-memory accumulator, in 4 x 4 pixel
+// blocks: the form for the spherical-reference epilogue and for L = 2 (the
+// 8 x 8 form below serves the others).  The wavelet buffer never goes to
+// global memory.  Levels finer than lmin were never
 // accumulated and read as zero.  Each thread rebuilds 4 x 4 pixel blocks in
 // the add order of the separate inverse kernel, from the same FP32
 // coefficient values that kernel would read, so the two paths give the same
@@ -354,6 +367,178 @@ __device__ __forceinline__ void supertile_inverse(const float2* acc, bool fixed,
 }
 
 
+
+__device__ __forceinline__ float ipv(float s, float lh, float hl, float hh, int ax, int ay) {
+  return ipick1(s, lh, hl, hh, ax, ay);
+}
+__device__ __forceinline__ float2 ipv(float2 s, float2 lh, float2 hl, float2 hh, int ax, int ay) {
+  return ipick(s, lh, hl, hh, ax, ay);
+}
+__device__ __forceinline__ float re_of(float v) { return v; }
+__device__ __forceinline__ float re_of(float2 v) { return v.x; }
+__device__ __forceinline__ float half_of(float v) { return v * 0.5f; }
+__device__ __forceinline__ float2 half_of(float2 v) { return make_float2(v.x * 0.5f, v.y * 0.5f); }
+template <bool R>
+struct EpiVal { using T = float2; };
+template <>
+struct EpiVal<true> { using T = float; };
+
+// Inverse transform (Sec. 1, step 3) and binarisation (Sec. 2) of a finished
+// super-tile in 8 x 8 pixel blocks (L >= 3, plane reference), one block per
+// thread: the block's level-3 scaling value from the coarser levels along its
+// path, the level-3 details give four level-2 scaling values, the level-2
+// details sixteen level-1 values, and the level-1 details (when kept) the 64
+// pixels.  Every step is the separate inverse kernel's (ipick, same add
+// order, same FP32 inputs), so the pixels equal that kernel's; levels finer
+// than lmin were never accumulated and read as zero (with no level-1 details
+// each level-1 value s gives s / 2 to its four pixels).  Four consecutive
+// lanes hold four neighbouring blocks: their rows of eight bits form one
+// 32-bit word of the packed hologram.
+// RE_ONLY (bits alone): real parts only, transformed unscaled from the
+// fixed-point integers (power-of-two scaling commutes with the adds and
+// halvings, so the signs are those of the scaled field); re_acc: the
+// accumulator holds real parts only.  Otherwise complex values go to u and/or
+// are binarised.
+template <int L, bool RE_ONLY>
+__device__ __forceinline__ void supertile_inverse8(const float2* acc, bool fixed, bool re_acc, float dq, int lmin,
+                                                   int k, int kx, int ky, int Sx, int Sy, const JobDev& J,
+                                                   const int* lvC, const int* lvG, const int* lvPS, int tid,
+                                                   int NT) {
+  static_assert(L >= 3, "8 x 8 blocks need at least three levels");
+  using V = typename EpiVal<RE_ONLY>::T;
+  int C[L + 1], G[L + 1], PS[L + 1];
+#pragma unroll
+  for (int l = 1; l <= L; ++l) {
+    C[l] = lvC[l];
+    G[l] = lvG[l];
+    PS[l] = lvPS[l];
+  }
+  const unsigned acc_s = sh_addr(acc);
+  auto zero = []() -> V {
+    if constexpr (RE_ONLY) return 0.f;
+    else return make_float2(0.f, 0.f);
+  };
+  // Coefficient of level l, band plane pl, at super-tile cell (cx, cy).
+  auto coef = [&](int l, int pl, int cx, int cy) -> V {
+    if (l < lmin) return zero();
+    const unsigned i = (unsigned)(C[l] + pl * PS[l] + cy * G[l] + cx);
+    if constexpr (RE_ONLY) {
+      const int q = lds32(acc_s + (re_acc ? 4u : 8u) * i);  // word of the real part
+      return fixed ? (float)q : __int_as_float(q);
+    } else {
+      const int2 q = lds64(acc_s + 8u * i);
+      if (fixed) return make_float2((float)q.x * dq, (float)q.y * dq);
+      return make_float2(__int_as_float(q.x), __int_as_float(q.y));
+    }
+  };
+  const int bpr = (k << L) >> 3;  // 8 x 8 blocks per super-tile row
+  const int total = bpr * ((ky << L) >> 3);
+  const int xvalid = (kx << L) >> 3;
+  const int X0 = Sx << L, Y0 = Sy << L, xend = (Sx + kx) << L;
+  const int w = J.w;
+  float2* u = J.u;
+  uint8_t* bits = J.bits;
+  const int lane = tid & 31;
+  for (int b0 = 0; b0 < total; b0 += NT) {  // uniform trip count: whole warps shuffle
+    const int b = b0 + tid;
+    const int brow = b / bpr, bcol = b - brow * bpr;
+    const bool inrow = b < total;
+    const bool valid = inrow && bcol < xvalid;
+    const int px0 = 8 * bcol, py0 = 8 * brow;
+    V s3 = zero(), lh3 = zero(), hl3 = zero(), hh3 = zero();
+    if (valid) {
+      s3 = coef(L, 0, px0 >> L, py0 >> L);
+#pragma unroll
+      for (int l = L; l >= 4; --l) {
+        const int cx = px0 >> l, cy = py0 >> l, pl = l == L ? 1 : 0;
+        s3 = ipv(s3, coef(l, pl, cx, cy), coef(l, pl + 1, cx, cy), coef(l, pl + 2, cx, cy), (px0 >> (l - 1)) & 1,
+                 (py0 >> (l - 1)) & 1);
+      }
+      const int pl3 = L == 3 ? 1 : 0;
+      lh3 = coef(3, pl3, bcol, brow);
+      hl3 = coef(3, pl3 + 1, bcol, brow);
+      hh3 = coef(3, pl3 + 2, bcol, brow);
+    }
+    const int xw = X0 + 32 * (bcol >> 2);  // first pixel of this lane group's bit word
+    const int x0 = X0 + px0;
+    // One bit word per pixel row: the four lanes' bytes, row y written by one lane.
+    auto put_bits = [&](int y, unsigned byte, int r) {
+      unsigned v = byte << (8 * (lane & 3));
+      v |= __shfl_xor_sync(0xffffffffu, v, 1);
+      v |= __shfl_xor_sync(0xffffffffu, v, 2);
+      if ((lane & 3) == (r & 3) && inrow && xw < xend) {
+        const size_t byte0 = ((size_t)y * w + xw) >> 3;
+        if (xw + 32 <= xend && (w & 31) == 0) {
+          *reinterpret_cast<unsigned*>(bits + byte0) = v;
+        } else {
+          const int nb = min(4, (xend - xw) >> 3);
+          for (int q = 0; q < nb; ++q) bits[byte0 + q] = (uint8_t)(v >> (8 * q));
+        }
+      }
+    };
+#pragma unroll
+    for (int ay = 0; ay < 2; ++ay) {
+      V s1[2][4];
+#pragma unroll
+      for (int ax = 0; ax < 2; ++ax) {
+        const V s2 = ipv(s3, lh3, hl3, hh3, ax, ay);
+        V l2 = zero(), h2 = zero(), d2 = zero();
+        if (valid) {
+          const int cx = 2 * bcol + ax, cy = 2 * brow + ay;
+          l2 = coef(2, 0, cx, cy);
+          h2 = coef(2, 1, cx, cy);
+          d2 = coef(2, 2, cx, cy);
+        }
+#pragma unroll
+        for (int qy = 0; qy < 2; ++qy)
+#pragma unroll
+          for (int qx = 0; qx < 2; ++qx) s1[qy][2 * ax + qx] = ipv(s2, l2, h2, d2, qx, qy);
+      }
+#pragma unroll
+      for (int qy = 0; qy < 2; ++qy) {
+        const int j = 2 * ay + qy;         // level-1 row of the block: pixel rows 2j, 2j + 1
+        const int y = Y0 + py0 + 2 * j;
+        unsigned byte[2] = {0u, 0u};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {      // level-1 column: pixels 2i, 2i + 1
+          V p[2][2];
+          if (lmin >= 2) {
+            const V h = half_of(s1[qy][i]);
+            p[0][0] = p[0][1] = p[1][0] = p[1][1] = h;
+          } else {
+            V l1 = zero(), h1 = zero(), d1 = zero();
+            if (valid) {
+              const int cx = 4 * bcol + i, cy = 4 * brow + j;
+              l1 = coef(1, 0, cx, cy);
+              h1 = coef(1, 1, cx, cy);
+              d1 = coef(1, 2, cx, cy);
+            }
+#pragma unroll
+            for (int ry = 0; ry < 2; ++ry)
+#pragma unroll
+              for (int rx = 0; rx < 2; ++rx) p[ry][rx] = ipv(s1[qy][i], l1, h1, d1, rx, ry);
+          }
+#pragma unroll
+          for (int ry = 0; ry < 2; ++ry) {
+            if constexpr (!RE_ONLY) {
+              if (u != nullptr && valid)
+                __stcs(reinterpret_cast<float4*>(u + (size_t)(y + ry) * w + x0 + 2 * i),
+                       make_float4(p[ry][0].x, p[ry][0].y, p[ry][1].x, p[ry][1].y));
+            }
+            if (valid)
+              byte[ry] |= (re_of(p[ry][0]) > 0.f ? 1u : 0u) << (2 * i) | (re_of(p[ry][1]) > 0.f ? 1u : 0u)
+                                                                         << (2 * i + 1);
+          }
+        }
+        if (bits != nullptr) {
+          put_bits(y, byte[0], 2 * j);
+          put_bits(y + 1, byte[1], 2 * j + 1);
+        }
+      }
+    }
+  }
+}
+
 // Kernel modes: complex accumulation; real parts only (every job of the
 // launch wants bits alone with R = 1); complex accumulation with the
 // reference-wave epilogue compiled in (a launch where some job binarises
@@ -364,23 +549,21 @@ constexpr int kModeComplex = 0, kModeRe = 1, kModeRef = 2;
 template <int L, int DT, int MODE>
 __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
   constexpr int TSL = 1 << (2 * L);
-  static_assert(TSL <= kRangeCap, "the write-out slot table lives in the range records");
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = a.cell;
   const int k = T >> L;
   constexpr bool RE = MODE == kModeRe;
   constexpr bool re_acc = RE;
   const int rcap = a.rcap;
-  const int P = survivor_cap(k, rcap);
+  const int P = survivor_cap(rcap);
   const int lmin = a.lut.lmin;
-  const int NLV = L - lmin + 1;  // kept levels
-  const int NA = plane_total(k, L, lmin);  // accumulator size (complex)
+  const int NA = plane_total(k, L, lmin);  // accumulator size (cells)
   Smem S;
   smem_layout(T, L, lmin, a.lut.D, re_acc, rcap, &S, smem);
   const int NW = NA * (re_acc ? 1 : 2);  // accumulator words (a multiple of 4)
   __shared__ int s_st, s_n, s_total;
+  __shared__ int warp_buf[32];
   __shared__ int s_rowstart[kMaxCellRows], s_rowpre[kMaxCellRows + 1];
-  __shared__ unsigned long long warp_buf[32];
   // Per level l: index of the first super-tile cell past the guard, row
   // stride, plane size (see plane_code).
   __shared__ int lvC[8], lvG[8], lvPS[8];
@@ -413,10 +596,6 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
   float4* acc4 = reinterpret_cast<float4*>(S.acc);
   int* acci = reinterpret_cast<int*>(S.acc);
   const bool fixed = !a.acc_float;
-#ifdef WASABI_PHASE_TIMERS
-  long long pt[6] = {0, 0, 0, 0, 0, 0};
-  long long pt_last = clock64();
-#endif
   int next = 0;  // thread 0: the item claimed for the next iteration
   if (tid == 0) next = atomicAdd(counter, 1);
 
@@ -427,7 +606,6 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
       next = atomicAdd(counter, 1);  // claim the next item early
     }
     __syncthreads();
-    PT_MARK(0);
     const int item = s_st;
     if (item >= nsp) break;
     // Item -> (job, super-tile).
@@ -490,7 +668,6 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
       if (lane == 31) s_total = incl;
     }
     __syncthreads();
-    PT_MARK(1);
     const int total = s_total;
     // Fixed-point scale 2^sh: every partial sum stays below 2^31 in magnitude.
     const float bound = (float)total * (J.amax * cmax);
@@ -513,158 +690,154 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
             Ay + bx.y + 1 >= Sy) {
           const int s = atomicAdd(&s_n, 1);
           const float amp = __int_as_float(p.z) * (fixed ? qs : 1.0f);
-          S.sp[s] = make_int4(Ax, Ay, p.w, 0);
+          S.sp[s] = make_int4(Ax, Ay, p.w, __float_as_int(amp));
           // shift_l(X) of Eq. (2): floor((X + half * 2^(l-1)) / 2^l), made
           // relative to the super-tile origin in level-l units, folded with
-          // the level's accumulator offset into one base per level.
+          // the level's accumulator offset into one base per level (minus
+          // the level bits of the plane codes it is added to).
           for (int l = lmin; l <= L; ++l) {
             const int hb = half << (l - 1);
             const int ox = ((X + hb) >> l) - (Sx << (L - l)), oy = ((Y + hb) >> l) - (Sy << (L - l));
-            S.svb[s * NLV + (l - lmin)] = make_int2(lvC[l] + oy * lvG[l] + ox, __float_as_int(amp));
+            S.sb[s * 8 + l] = (int)(4u * (unsigned)(lvC[l] + oy * lvG[l] + ox) - ((unsigned)l << 29));
           }
         }
       }
       __syncthreads();
-      PT_MARK(2);
       const int n = s_n;
-      // ---- LUT ranges: slot f = s * (k + 1) + j is window-tile row j of
-      // survivor s; thread t owns slots [t * per, (t + 1) * per).
+      // ---- passes: slot f = s * (k + 1) + j is window-tile row j of the
+      // survivor's clipped tile box; thread t owns slots [t * per, (t + 1) * per).
       const int nslot = n * (k + 1);
-      const int per = (nslot + NT - 1) / NT;  // <= kPerMax
-      int rst[kPerMax], rln[kPerMax];
-      unsigned long long loc = 0;  // (non-empty ranges << 32) | visits
-#pragma unroll
-      for (int u = 0; u < kPerMax; ++u) {
-        rst[u] = 0;
-        rln[u] = 0;
-        const int f = tid * per + u;
-        if (u < per && f < nslot) {
-          const int s = f / (k + 1), j = f - s * (k + 1);
-          const int4 sp = S.sp[s];
-          const int2 bx = S.dbox[sp.z];
-          const int tya = max(bx.x, Sy - sp.y - 1), tyb = min(bx.y, Sy + ky - 1 - sp.y);
-          const int txa = max(bx.x, Sx - sp.x - 1), txb = min(bx.y, Sx + kx - 1 - sp.x);
+      const int per = (nslot + NT - 1) / NT;
+      const unsigned sp_s = sh_addr(S.sp), sb_s = sh_addr(S.sb), pass_s = sh_addr(S.pass), box_s = sh_addr(S.dbox);
+      const unsigned acc_s = sh_addr(S.acc);
+      // Walks this thread's slots in order, calling fn(survivor, first entry,
+      // entries, amplitude bits) for each non-empty LUT range; the survivor's
+      // clipped tile box is computed once per survivor.
+      auto walk_slots = [&](auto&& fn) {
+        const int f0 = tid * per;
+        const int f1 = min(nslot, f0 + per);
+        if (f0 >= f1) return;
+        int s = f0 / (k + 1), j = f0 - s * (k + 1);
+        int cur = -1, tya = 0, tyb = -1, txa = 0, txb = -1, dro = 0, ampb = 0;
+        for (int f = f0; f < f1; ++f) {
+          if (s != cur) {
+            cur = s;
+            const int4 sp = lds128(sp_s + 16u * s);
+            const int2 bx = lds64(box_s + 8u * sp.z);
+            tya = max(bx.x, Sy - sp.y - 1);
+            tyb = min(bx.y, Sy + ky - 1 - sp.y);
+            txa = max(bx.x, Sx - sp.x - 1);
+            txb = min(bx.y, Sx + kx - 1 - sp.x);
+            dro = sp.z * ntpd;
+            ampb = sp.w;
+          }
           const int row = tya + j;
           if (row <= tyb && txa <= txb) {
-            const int ro = sp.z * ntpd + row * lut.nwt;
-            rst[u] = __ldg(&lut.tile_off[ro + txa]);
-            rln[u] = __ldg(&lut.tile_off[ro + txb + 1]) - rst[u];
+            const int ro = dro + row * lut.nwt;
+            const int st0 = __ldg(&lut.tile_off[ro + txa]);
+            const int len = __ldg(&lut.tile_off[ro + txb + 1]) - st0;
+            if (len > 0) fn(s, st0, len, ampb);
+          }
+          if (++j == k + 1) {
+            j = 0;
+            ++s;
           }
         }
-      }
-#pragma unroll
-      for (int u = 0; u < kPerMax; ++u)
-        if (rln[u] > 0) loc += (1ull << 32) | (unsigned long long)rln[u];
-      unsigned long long tot;
-      const unsigned long long ex = block_scan64(loc, &tot, warp_buf);
-      const int nranges = (int)(tot >> 32), nvis = (int)(tot & 0xffffffffu);
-      {
-        int c = (int)(ex >> 32), vrun = (int)(ex & 0xffffffffu);
-#pragma unroll
-        for (int u = 0; u < kPerMax; ++u) {
-          if (rln[u] > 0) {
-            S.rrec[c] = make_int2(rst[u] - vrun, (tid * per + u) / (k + 1));
-            S.rpre[c] = vrun;
-            ++c;
-            vrun += rln[u];
-          }
+      };
+      int mine = 0;
+      walk_slots([&](int, int, int len, int) { mine += (len + kPass - 1) / kPass; });
+      int npass;
+      const int pbase = block_scan(mine, &npass, warp_buf);
+      // Passes in windows of rcap: the slots write the window's passes, then
+      // the warps visit them.
+      for (int w0 = 0; w0 < npass; w0 += rcap) {
+        const int np = min(rcap, npass - w0);
+        const int ng = (np + kPassUnroll - 1) / kPassUnroll;  // groups of kPassUnroll passes
+        if (mine > 0 && pbase < w0 + rcap && pbase + mine > w0) {
+          int pi = pbase;
+          walk_slots([&](int s, int st0, int len, int ampb) {
+            for (int o = 0; o < len; o += kPass, ++pi)
+              if (pi >= w0 && pi < w0 + rcap)
+                S.pass[pi - w0] = make_int4(st0 + o, min(kPass, len - o), (int)(sb_s + 32u * s), ampb);
+          });
         }
-        // Terminator, then sentinels for the lookahead of the visit lookup.
-        if (tid == 0) {
-          S.rpre[nranges] = nvis;
-          S.rrec[nranges] = make_int2(0, 0);
-        }
-        if (tid < kLookahead) S.rpre[nranges + 1 + tid] = 0x7fffffff;
-      }
-      __syncthreads();
-      PT_MARK(3);
-      // ---- visits: warp w takes [w*per, (w+1)*per), 32 at a time, kUnroll
-      // chunks per round: every chunk's range lookup (shared memory only) and
-      // LUT loads are issued before any of them is consumed.
-      if (nvis > 0) {
-        constexpr int kUnroll = 4;  // visits per lane per round: two windows of 64
-        const int vper = (nvis + nwarps - 1) / nwarps;
-        const int v0 = warp * vper, v1 = min(nvis, v0 + vper);
-        const unsigned le = (2u << lane) - 1u;  // lanes <= this one
-        int rb = v0 < v1 ? last_le(S.rpre, 0, nranges - 1, v0) : 0;
-        for (int b0 = v0; b0 < v1; b0 += 32 * kUnroll) {
-          int ee[kUnroll], sv[kUnroll];
-          uint2 ppu[kUnroll];   // records: plane code, value word
-          float vyu[kUnroll];   // FP32 imaginary part (complex accumulation), or the block scale
+        // The last group is filled with empty passes (no entries; their
+        // loaded entries are entry 0 and their level bases those of survivor 0).
+        if (tid < ng * kPassUnroll - np) S.pass[np + tid] = make_int4(1, 0, (int)sb_s, 0);
+        __syncthreads();
+        // ---- visits: warp w takes groups w, w + warps, ...; a group's
+        // records and LUT loads are all issued before any is consumed.  Lane
+        // i visits entries i, i + 32, ... of each pass; lanes past a pass's
+        // end load a valid entry and add nothing.
+        auto visit = [&](auto fixed_tag) {
+          constexpr bool FX = decltype(fixed_tag)::value;
+          constexpr int EPL = kPass / 32;  // entries per lane and pass
+          for (int g = warp; g < ng; g += nwarps) {
+            uint2 rec[kPassUnroll][EPL];
+            float vy[kPassUnroll][EPL];  // FP32 imaginary part (complex accumulation), or the block scale
+            unsigned sbo[kPassUnroll];
+            float amp[kPassUnroll];
+            int cnt[kPassUnroll];
 #pragma unroll
-          for (int h = 0; h < kUnroll / 2; ++h) {
-            // Window [b, b + 64): lane l takes visits b + l and b + 32 + l.  The
-            // range of visit i is rb plus the number of range starts in (b, i]
-            // (ranges are non-empty, so starts are distinct); one load per
-            // lane brings the next 32 starts, enough unless 32 of them fall
-            // inside the window -- then it is looked up 32 visits at a time.
-            const int b = b0 + 64 * h;
-            const int mpos = S.rpre[rb + 1 + lane] - b;
-            const unsigned lo = (unsigned)mpos < 32u ? 1u << mpos : 0u;
-            const unsigned hi = (unsigned)(mpos - 32) < 32u ? 1u << (mpos - 32) : 0u;
-            const unsigned Mlo = __reduce_or_sync(0xffffffffu, lo), Mhi = __reduce_or_sync(0xffffffffu, hi);
-            int r0, r1;
-            if (__popc(Mlo) + __popc(Mhi) < kLookahead) {
-              r0 = rb + __popc(Mlo & le);
-              r1 = rb + __popc(Mlo) + __popc(Mhi & le);
-            } else {  // many short ranges: two windows of 32
-              r0 = rb + __popc(Mlo & le);
-              const int rm = __shfl_sync(0xffffffffu, r0, 31);
-              const int mp2 = S.rpre[rm + 1 + lane] - (b + 32);
-              const unsigned M2 = __reduce_or_sync(0xffffffffu, (unsigned)mp2 < 32u ? 1u << mp2 : 0u);
-              r1 = rm + __popc(M2 & le);
+            for (int u = 0; u < kPassUnroll; ++u) {
+              const int4 r = lds128(pass_s + 16u * (kPassUnroll * g + u));
+              cnt[u] = r.y;
+              sbo[u] = (unsigned)r.z;
+              amp[u] = __int_as_float(r.w);
+#pragma unroll
+              for (int h = 0; h < EPL; ++h) {
+                const int e = r.x + min(lane + 32 * h, r.y - 1);
+                rec[u][h] = __ldg(&lut.code[e]);
+                if (DT != WASABI_F32) vy[u][h] = __ldg(&lut.scale[e >> 5]);
+                else if (!re_acc) vy[u][h] = __ldg(&lut.val[e].y);
+              }
             }
-            rb = __shfl_sync(0xffffffffu, r1, 31);
-            const int2 rec0 = S.rrec[r0], rec1 = S.rrec[r1];
-            const int i0 = b + lane, i1 = b + 32 + lane;
-            ee[2 * h] = i0 < v1 ? i0 + rec0.x : -1;
-            sv[2 * h] = rec0.y;
-            ee[2 * h + 1] = i1 < v1 ? i1 + rec1.x : -1;
-            sv[2 * h + 1] = rec1.y;
-          }
 #pragma unroll
-          for (int u = 0; u < kUnroll; ++u) {
-            if (ee[u] >= 0) {
-              ppu[u] = __ldg(&lut.code[ee[u]]);
-              if (DT != WASABI_F32) vyu[u] = __ldg(&lut.scale[ee[u] >> 5]);
-              else if (!re_acc) vyu[u] = __ldg(&lut.val[ee[u]].y);
-            }
-          }
+            for (int u = 0; u < kPassUnroll; ++u) {
 #pragma unroll
-          for (int u = 0; u < kUnroll; ++u) {
-            if (ee[u] < 0) continue;
-            const uint2 pe = ppu[u];
-            const float2 v = DT == WASABI_F32 ? make_float2(__uint_as_float(pe.y), vyu[u]) : decode16<DT>(pe.y, vyu[u]);
-            const int2 sb = S.svb[sv[u] * NLV + (int)(pe.x >> 29) - lmin];
-            const int ai = (int)(pe.x & 0x1fffffffu) + sb.x;
-            const float amp = __int_as_float(sb.y);
-            // a_j c in FP32; in fixed point exactly scaled by 2^sh (folded
-            // into amp) and rounded to the nearest integer: the integer sums
-            // are exact.
-            if (re_acc) {
-              if (fixed) atomicAdd(&acci[ai], __float2int_rn(amp * v.x));
-              else atomicAdd(reinterpret_cast<float*>(acci) + ai, amp * v.x);
-            } else if (fixed) {
-              atomicAdd(&acci[2 * ai], __float2int_rn(amp * v.x));
-              atomicAdd(&acci[2 * ai + 1], __float2int_rn(amp * v.y));
-            } else {
-              atomicAdd(reinterpret_cast<float*>(acci) + 2 * ai, amp * v.x);
-              atomicAdd(reinterpret_cast<float*>(acci) + 2 * ai + 1, amp * v.y);
+              for (int h = 0; h < EPL; ++h) {
+                const int li = lane + 32 * h;
+                const uint2 pe = rec[u][h];
+                const float2 v = DT == WASABI_F32 ? make_float2(__uint_as_float(pe.y), vy[u][h])
+                                                  : decode16<DT>(pe.y, vy[u][h]);
+                // Byte offset of the accumulator word: plane code plus the
+                // survivor's base of the code's level (which carries minus
+                // the level bits).
+                const unsigned ab = pe.x + (unsigned)lds32(sbo[u] + 4u * (pe.x >> 29));
+                // a_j c in FP32; in fixed point exactly scaled by 2^sh (folded
+                // into amp) and rounded to the nearest integer: the integer
+                // sums are exact.
+                if constexpr (re_acc) {
+                  if constexpr (FX) red_add_lt(acc_s + ab, __float2int_rn(amp[u] * v.x), li, cnt[u]);
+                  else red_add_lt(acc_s + ab, amp[u] * v.x, li, cnt[u]);
+                } else {
+                  const unsigned a2 = acc_s + 2u * ab;
+                  if constexpr (FX) {
+                    red_add_lt(a2, __float2int_rn(amp[u] * v.x), li, cnt[u]);
+                    red_add_lt(a2 + 4u, __float2int_rn(amp[u] * v.y), li, cnt[u]);
+                  } else {
+                    red_add_lt(a2, amp[u] * v.x, li, cnt[u]);
+                    red_add_lt(a2 + 4u, amp[u] * v.y, li, cnt[u]);
+                  }
+                }
+              }
             }
           }
-        }
+        };
+        if (fixed) visit(std::true_type{});
+        else visit(std::false_type{});
+        __syncthreads();
       }
-      __syncthreads();
-      PT_MARK(4);
     }
+
 
     const float dq = ldexpf(1.0f, -sh);
     // Write the super-tile's tiles to the tile-major buffer: each tile's TSL
     // slots are contiguous there; slots of levels finer than lmin are zero.
-    // Slot -> accumulator offset table (in the free range records): offset of
+    // Slot -> accumulator offset table (in the free pass records): offset of
     // the slot's cell for tile (0, 0), row stride and m = L - level.
     if (wbuf != nullptr) {
-      int2* tab = S.rrec;
+      int2* tab = reinterpret_cast<int2*>(S.pass);
       for (int q = tid; q < TSL; q += NT) {
         int lev, band, ix, iy;
         slot_decode(L, q, &lev, &band, &ix, &iy);
@@ -699,25 +872,30 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
       }
     }
     if constexpr (RE) {  // bits alone, plane reference (the host sends nothing else here)
-      if (L >= 2 && J.bits != nullptr)
-        supertile_inverse<L, true, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS,
-                                          tid, NT, nullptr);
+      if (J.bits != nullptr) {
+        if constexpr (L >= 3)
+          supertile_inverse8<L, true>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid, NT);
+        else if constexpr (L == 2)
+          supertile_inverse<L, true, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS,
+                                            tid, NT, nullptr);
+      }
     } else if (MODE == kModeRef && L >= 2 && J.bits != nullptr && J.ref.kind != 0) {
       supertile_inverse<L, false, MODE == kModeRef>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG,
                                                     lvPS, tid, NT, &s_ref);
-    } else if (L >= 2 && J.u != nullptr) {
-      supertile_inverse<L, false, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS,
-                                         tid, NT, nullptr);
-    } else if (L >= 2 && J.bits != nullptr) {
-      supertile_inverse<L, true, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS,
-                                        tid, NT, nullptr);
+    } else if (J.u != nullptr) {
+      if constexpr (L >= 3)
+        supertile_inverse8<L, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid, NT);
+      else if constexpr (L == 2)
+        supertile_inverse<L, false, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS,
+                                           tid, NT, nullptr);
+    } else if (J.bits != nullptr) {
+      if constexpr (L >= 3)
+        supertile_inverse8<L, true>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid, NT);
+      else if constexpr (L == 2)
+        supertile_inverse<L, true, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS,
+                                          tid, NT, nullptr);
     }
-    PT_MARK(5);
   }
-#ifdef WASABI_PHASE_TIMERS
-  if (tid == 0)
-    for (int i = 0; i < 6; ++i) atomicAdd(&a.batch->timers[i], (unsigned long long)pt[i]);
-#endif
 }
 
 template <int L, int DT, int MODE>
@@ -761,21 +939,21 @@ size_t superpose_smem_bytes(int cell, int L, int lmin, int D, bool re_only, int 
   return smem_layout(cell, L, lmin, D, re_only, rcap, nullptr, nullptr);
 }
 
+int superpose_min_range_cap() { return kRangeMin; }
+
+// Pass capacity per window for a launch: the largest power of two up to
+// kRangeMax whose shared memory fits the CTA's share of the SM (one
+// 1,024-thread CTA per SM, or two smaller ones), at least kRangeMin.
 int superpose_range_cap(int cell, int L, int lmin, int D, bool re_only, int threads) {
-  const int big = std::min(kRangeMax, threads * kPerMax);
+  const size_t budget = threads > 512 ? kOneCtaSmem : kTwoCtaSmem;
   if (const char* v = std::getenv("WASABI_RANGE_CAP")) {  // tuning override
-    const int r = std::max(kRangeCap, std::min(big, std::atoi(v)));
-    if (superpose_smem_bytes(cell, L, lmin, D, re_only, r) <= 220 * 1024) return r;
+    int r = std::max(kRangeMin, std::min(kRangeMax, std::atoi(v)));
+    r = r / 4 * 4;
+    if (superpose_smem_bytes(cell, L, lmin, D, re_only, r) <= kOneCtaSmem) return r;
   }
-  // Two CTAs per SM (up to 512 threads) share the SM's shared memory; a
-  // 1,024-thread CTA has it alone.  The larger range capacity when it fits.
-  if (threads > 512) {
-    for (int r = big; r > kRangeCap; r >>= 1)
-      if (superpose_smem_bytes(cell, L, lmin, D, re_only, r) <= 220 * 1024) return r;
-    return kRangeCap;
-  }
-  if (re_only && big > kRangeCap && superpose_smem_bytes(cell, L, lmin, D, true, big) <= kTwoCtaSmem) return big;
-  return kRangeCap;
+  for (int r = kRangeMax; r > kRangeMin; r >>= 1)
+    if (superpose_smem_bytes(cell, L, lmin, D, re_only, r) <= budget) return r;
+  return kRangeMin;
 }
 
 // Default configuration per kind of launch (measured on C2, C3 and the
@@ -793,16 +971,16 @@ int superpose_range_cap(int cell, int L, int lmin, int D, bool re_only, int thre
 void superpose_default_config(int L, int lmin, int D, int kind, int* cell, int* threads) {
   const int unit = (1 << L) > 32 ? (1 << L) : 32;
   const bool re = kind == kConfigRe;
-  auto fits_one = [&](int T) { return superpose_smem_bytes(T, L, lmin, D, re, kRangeCap) <= 220 * 1024; };
+  auto fits_one = [&](int T) { return superpose_smem_bytes(T, L, lmin, D, re, kRangeMin) <= kOneCtaSmem; };
   if (kind == kConfigRe) {
-    for (int T = 256 / unit * unit; T >= 128 && T >= unit; T -= unit)
+    for (int T = kMaxSuperTile / unit * unit; T >= 128 && T >= unit; T -= unit)
       if (fits_one(T)) { *cell = T; *threads = 1024; return; }
   } else if (kind == kConfigComplex) {
     for (int T : {192, 128})
       if (T % unit == 0 && fits_one(T)) { *cell = T; *threads = 1024; return; }
   }
   int T = 256;
-  while (T > unit && superpose_smem_bytes(T, L, lmin, D, false, kRangeCap) > kTwoCtaSmem) T >>= 1;
+  while (T > unit && superpose_smem_bytes(T, L, lmin, D, false, kRangeMin) > kTwoCtaSmem) T >>= 1;
   if (T < unit) T = unit;
   if (T < 128 && 128 % unit == 0 && fits_one(128)) { *cell = 128; *threads = 1024; return; }
   *cell = T;
@@ -810,11 +988,11 @@ void superpose_default_config(int L, int lmin, int D, int kind, int* cell, int* 
 }
 
 int superpose_max_cell_rows() { return kMaxCellRows; }
-int superpose_min_threads() { return kRangeCap / kPerMax; }
+int superpose_min_threads() { return 128; }
 
 cudaError_t launch_superpose(const SuperposeArgs& a, cudaStream_t s) {
-  if (a.threads > 1024 || a.threads < kRangeCap / kPerMax || a.threads % 32 || !a.lut.code ||
-      a.rcap < kRangeCap || a.rcap > kRangeMax || a.rcap > a.threads * kPerMax)
+  if (a.threads > 1024 || a.threads < superpose_min_threads() || a.threads % 32 || !a.lut.code ||
+      a.rcap < kRangeMin || a.rcap > kRangeMax || a.rcap % 4)
     return cudaErrorInvalidValue;
   switch (a.lut.L) {
     case 1: return launch_l<1>(a, s);

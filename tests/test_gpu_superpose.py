@@ -201,17 +201,21 @@ def test_fixed_point_is_deterministic_and_matches_float(w, orc, monkeypatch, c1)
     assert rel_l2(a1, f1) <= TOL
 
 
-@pytest.mark.parametrize("want,T", [("bits", 256), ("both", 192)])
-def test_widest_tiles_many_candidate_batches(w, orc, monkeypatch, want, T):
+@pytest.mark.parametrize("want,T,rcap", [("bits", 256, 0), ("both", 192, 0), ("bits", 256, 1024)])
+def test_widest_tiles_many_candidate_batches(w, orc, monkeypatch, want, T, rcap):
     """The benchmark's launch configurations on a hologram small enough for
     the whole-field oracle: 1,024-thread CTAs on 256-pixel super-tiles with
     real-part accumulation (bits alone) and on 192-pixel super-tiles with
     complex accumulation, C3's optics and LUT shape (633 nm, W = 1024, L = 4,
     keep 1%, z in [0.1, 1.0] mm), and enough points within reach of every
-    super-tile that its candidates need several batches (a batch holds at
-    most 8,192 LUT ranges).  Element-wise bounds on every pixel."""
+    super-tile that its coefficient visits need several rounds of passes (a
+    round holds at most the launch's pass capacity; rcap = 1,024 forces many
+    rounds and candidate batches of 256).  Element-wise bounds on every
+    pixel."""
     monkeypatch.setenv("WASABI_SUPERPOSE_T", str(T))
     monkeypatch.setenv("WASABI_SUPERPOSE_THREADS", "1024")
+    if rcap:
+        monkeypatch.setenv("WASABI_RANGE_CAP", str(rcap))
     lam, pitch, zmin, zmax, D, W, L, gamma, Nh, N = 633e-9, 1e-6, 0.1e-3, 1.0e-3, 16, 1024, 4, 0.01, 1024, 1800
     pts = uniform_cloud(77, N, Nh, zmin, zmax)
     r = np.random.default_rng(77)
