@@ -494,6 +494,41 @@ __device__ __forceinline__ void supertile_inverse8(const float2* acc, bool fixed
 #pragma unroll
           for (int qx = 0; qx < 2; ++qx) s1[qy][2 * ax + qx] = ipv(s2, l2, h2, d2, qx, qy);
       }
+      if constexpr (RE_ONLY) {
+        if (lmin >= 2) {
+          // No level-1 details: both pixel rows of level-1 row j are the signs
+          // of s1[.][0..3] / 2, each covering two pixels (the halving does not
+          // change a sign: the values are integers, or FP32 sums far from the
+          // subnormal range).  One word per pair of rows.
+#pragma unroll
+          for (int qy = 0; qy < 2; ++qy) {
+            const int j = 2 * ay + qy;
+            unsigned b4 = 0;
+            if (valid) {
+#pragma unroll
+              for (int i = 0; i < 4; ++i) b4 |= (s1[qy][i] > 0.f ? 1u : 0u) << i;
+            }
+            const unsigned byte = (b4 & 1u) * 3u | (b4 & 2u) * 6u | (b4 & 4u) * 12u | (b4 & 8u) * 24u;
+            unsigned v = byte << (8 * (lane & 3));
+            v |= __shfl_xor_sync(0xffffffffu, v, 1);
+            v |= __shfl_xor_sync(0xffffffffu, v, 2);
+            if ((lane & 3) == j && inrow && xw < xend) {
+              const int y = Y0 + py0 + 2 * j;
+#pragma unroll
+              for (int ry = 0; ry < 2; ++ry) {
+                const size_t byte0 = ((size_t)(y + ry) * w + xw) >> 3;
+                if (xw + 32 <= xend && (w & 31) == 0) {
+                  *reinterpret_cast<unsigned*>(bits + byte0) = v;
+                } else {
+                  const int nb = min(4, (xend - xw) >> 3);
+                  for (int q = 0; q < nb; ++q) bits[byte0 + q] = (uint8_t)(v >> (8 * q));
+                }
+              }
+            }
+          }
+          continue;
+        }
+      }
 #pragma unroll
       for (int qy = 0; qy < 2; ++qy) {
         const int j = 2 * ay + qy;         // level-1 row of the block: pixel rows 2j, 2j + 1
@@ -594,7 +629,6 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
   int* counter = &a.batch->counter;
   const float cmax = __ldg(lut.cmax);
   float4* acc4 = reinterpret_cast<float4*>(S.acc);
-  int* acci = reinterpret_cast<int*>(S.acc);
   const bool fixed = !a.acc_float;
   int next = 0;  // thread 0: the item claimed for the next iteration
   if (tid == 0) next = atomicAdd(counter, 1);
@@ -846,29 +880,71 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
                              : make_int2(-1, 0);
       }
       __syncthreads();
-      const int nq = kx * ky * (TSL / 2);  // pairs of slots
-      for (int i = tid; i < nq; i += NT) {
-        const int tile = i / (TSL / 2), q = i - tile * (TSL / 2);
-        const int tj = tile / kx, tt = tile - tj * kx;
+      const unsigned acc_s = sh_addr(S.acc);
+      // Thread -> one pair of slots (2 q, 2 q + 1) and every (NT / (TSL / 2))-th
+      // tile: the slot table is read once, and the 16-byte stores of
+      // consecutive threads are consecutive in the tile.
+      constexpr int QP = TSL / 2;
+      const int ntiles = kx * ky;
+      const int q = tid % QP, step = NT / QP;
+      int co[2], rs[2], shf[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int2 e = tab[2 * q + h];
+        co[h] = e.x;
+        rs[h] = e.y >> 8;
+        shf[h] = e.y & 255;
+      }
+      int tj = 0, tt = tid / QP;
+      while (tt >= kx && step > 0) {
+        tt -= kx;
+        ++tj;
+      }
+      for (int tile = tid / QP; step > 0 && tile < ntiles; tile += step) {
         float v[4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int2 e = tab[2 * q + h];
           float2 c = make_float2(0.f, 0.f);
-          if (e.x >= 0) {
-            const int ci = e.x + ((tj * (e.y >> 8) + tt) << (e.y & 255));
-            if (fixed) {
-              const int2 iv = reinterpret_cast<const int2*>(acci)[ci];
-              c = make_float2((float)iv.x * dq, (float)iv.y * dq);
-            } else {
-              c = S.acc[ci];
-            }
+          if (co[h] >= 0) {
+            const unsigned ci = (unsigned)(co[h] + ((tj * rs[h] + tt) << shf[h]));
+            const int2 iv = lds64(acc_s + 8u * ci);
+            c = fixed ? make_float2((float)iv.x * dq, (float)iv.y * dq)
+                      : make_float2(__int_as_float(iv.x), __int_as_float(iv.y));
           }
           v[2 * h] = c.x;
           v[2 * h + 1] = c.y;
         }
         float4* dst = reinterpret_cast<float4*>(wbuf + ((size_t)(Sy + tj) * ntx + Sx + tt) * TSL) + q;
         __stcs(dst, make_float4(v[0], v[1], v[2], v[3]));
+        tt += step;
+        while (tt >= kx) {
+          tt -= kx;
+          ++tj;
+        }
+      }
+      // Blocks narrower than a tile's slot pairs: one pair per thread-step.
+      if (step == 0) {
+        const int nq = ntiles * QP;
+        for (int i = tid; i < nq; i += NT) {
+          const int tile = i / QP, qq = i - tile * QP;
+          const int tj2 = tile / kx, tt2 = tile - tj2 * kx;
+          float v[4];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int2 e = tab[2 * qq + h];
+            float2 c = make_float2(0.f, 0.f);
+            if (e.x >= 0) {
+              const unsigned ci = (unsigned)(e.x + ((tj2 * (e.y >> 8) + tt2) << (e.y & 255)));
+              const int2 iv = lds64(acc_s + 8u * ci);
+              c = fixed ? make_float2((float)iv.x * dq, (float)iv.y * dq)
+                        : make_float2(__int_as_float(iv.x), __int_as_float(iv.y));
+            }
+            v[2 * h] = c.x;
+            v[2 * h + 1] = c.y;
+          }
+          float4* dst = reinterpret_cast<float4*>(wbuf + ((size_t)(Sy + tj2) * ntx + Sx + tt2) * TSL) + qq;
+          __stcs(dst, make_float4(v[0], v[1], v[2], v[3]));
+        }
       }
     }
     if constexpr (RE) {  // bits alone, plane reference (the host sends nothing else here)
