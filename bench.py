@@ -406,19 +406,32 @@ def coiflet_summary(w, torch, dev, c, depths, pbuf, stream, u_direct, units_haar
 def precision_forms(w, torch, dev, c, depths, pbuf, stream):
     """C4: the fused hologram with the LUT stored as FP32, FP16 and BF16
     (per-32 FP32 scales); time of the hologram call per form.  The error of
-    each form against the FP64 oracle is measured by the test suite."""
-    out = {}
+    each form against the FP64 oracle is measured by the test suite
+    (tests/test_gpu_fullsize.py::test_c4_precision_forms_vs_fp64)."""
+    out = {"workload": f"{c.name}: {c.Nh}x{c.Nh} complex field, {c.N} {c.cloud} points, {c.D} depths, "
+                       f"W={c.W}, L={c.L}, keep={c.gamma}"}
     u = torch.empty((c.Nh, c.Nh), dtype=torch.complex64, device=dev)
     for dt in ("f32", "f16s", "bf16s"):
         lut = w.build_lut(c.lam, c.pitch, depths, c.W, c.L, c.gamma, dtype=dt, stream=stream)
         scratch = torch.empty(w.scratch_bytes(lut, pbuf.shape[0], c.Nh, c.Nh), dtype=torch.uint8, device=dev)
         with torch.cuda.stream(stream):
             ms = _time(torch, stream, lambda: w.hologram(lut, pbuf, c.Nh, c.Nh, want="complex", u=u,
-                                                          scratch=scratch, stream=stream))
+                                                          scratch=scratch, stream=stream), reps=20)
         out[dt] = {"hologram_ms": ms}
         lut.close()
     w.sync_status(stream)
+    for dt in ("f16s", "bf16s"):
+        out[dt]["speedup_vs_f32"] = out["f32"]["hologram_ms"] / out[dt]["hologram_ms"]
     return out
+
+
+def precision_summary(w, torch, dev, stream):
+    """The C4 precision forms beside the default run: C4's own seeded points."""
+    c = CONFIGS["C4"]
+    p = c.points()
+    t = {k: torch.from_numpy(p[k]).to(dev) for k in "xyza"}
+    pbuf = w.quantize_points(t["x"], t["y"], t["z"], t["a"], c.zmin, c.zmax, c.D)
+    return precision_forms(w, torch, dev, c, w.depth_grid(c.zmin, c.zmax, c.D), pbuf, stream)
 
 
 def serving_summary(w, torch, dev, n_jobs: int = 512, budget_gib: float = 4.0, streams: int = 4,
@@ -719,6 +732,7 @@ def run_gpu(args, c):
             out["paper_reference_wave"] = reference_summary(w, torch, c, depths, pbuf, stream, units)
             out["streaming"] = streaming_summary(w, torch, dev, c, args.stream_side, args.stream_band)
             out["paper_setup"] = paper_setup_summary(w, torch, dev)
+            out["precision_forms"] = precision_summary(w, torch, dev, stream)
         if not args.no_cpu_baseline and c.name != "P":
             out["cpu_baseline"] = oracle_sample(c, pts, os.cpu_count() or 1)
         print(json.dumps(out), flush=True)

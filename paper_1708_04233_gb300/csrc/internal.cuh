@@ -177,11 +177,6 @@ cudaError_t launch_lut_build(const LutBuildArgs& a, cudaStream_t s);
 // Order-1 coiflet filters (FP64): scaling filter h_k and wavelet filter
 // g_k = (-1)^k h_{1-k}, k = -2 .. 3.
 void coif1_filters(double lo[6], double hi[6]);
-// Inverse of an L-level periodic order-1 coiflet transform of a tile-major
-// wavelet buffer: tile-major -> Mallat (into a), L synthesis levels (a <-> b),
-// complex result in out (row-major, w x h) if given, else left in a.
-cudaError_t launch_coif_inverse(const float2* wbuf, int w, int h, int L, float2* a, float2* b, cudaStream_t s,
-                                float2* out);
 // Window tiles one PSF block transforms (1,024 threads, one per pixel).
 inline int psf_tiles_per_block(int L) {
   const int tsl = 1 << (2 * L);

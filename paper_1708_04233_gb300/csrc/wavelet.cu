@@ -3,11 +3,12 @@
 // hologram superposed from a coiflet LUT.
 //
 // The coiflet transform is periodic over the whole hologram and its filters
-// overlap 2^L x 2^L tiles, so the inverse is not tile-local as Haar's is: the
-// tile-major buffer is permuted into the Mallat layout, then each level runs
-// two separable synthesis passes over the level's low-pass region (along y
-// into a second buffer, then along x back), and a last pass writes the field
-// and/or the binary hologram against the frame's reference wave.
+// overlap 2^L x 2^L tiles, so the inverse is not tile-local as Haar's is: each
+// level is one pass over tiles of its output, which gathers its input bands
+// with a one-cell halo (details straight from the tile-major buffer, the
+// low-pass band from the coarser level's result) and synthesises along y and
+// then x in shared memory; the last level writes the field and/or the binary
+// hologram against the frame's reference wave.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -40,52 +41,6 @@ struct CoifTaps {
   float lo[6], hi[6];
 };
 
-// One synthesis output: sample j of a line of S samples receives
-// h_k s[m] + g_k d[m] for every k = j - 2m (mod S), k = -2 .. 3; s and d are
-// the line's low and high halves (S / 2 each), `step` apart in memory.
-// The taps with k = j - 2m of j's parity pair with m = j/2 + 1, j/2, j/2 - 1
-// (k = -2, 0, 2 for even j; -1, 1, 3 for odd j), taken in that order, each
-// m wrapped once (h = 1: every m is 0).
-__device__ __forceinline__ float2 coif_synth(const CoifTaps& t, const float2* line, long long step, int S, int j) {
-  const int h = S / 2, m0 = j >> 1, par = j & 1;
-  int mp = m0 + 1, mm = m0 - 1;
-  if (mp >= h) mp -= h;
-  if (mm < 0) mm += h;
-  const int ms[3] = {mp, m0, mm};
-  float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const int i = 2 * q + par;  // tap slot of k = 2q - 2 + par
-    const float2 sv = line[(long long)ms[q] * step], dv = line[(long long)(h + ms[q]) * step];
-    acc.x = __fmaf_rn(t.lo[i], sv.x, acc.x);
-    acc.y = __fmaf_rn(t.lo[i], sv.y, acc.y);
-    acc.x = __fmaf_rn(t.hi[i], dv.x, acc.x);
-    acc.y = __fmaf_rn(t.hi[i], dv.y, acc.y);
-  }
-  return acc;
-}
-
-// Along y over the Sx x Sy low-pass region: a -> b (consecutive threads take
-// consecutive columns).
-__global__ void coif_syn_cols_kernel(const float2* __restrict__ a, float2* __restrict__ b, int w, int Sx, int Sy,
-                                     CoifTaps t) {
-  const long long n = (long long)Sx * Sy;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(i / Sx), col = (int)(i - (long long)j * Sx);
-    b[(long long)j * w + col] = coif_synth(t, a + col, w, Sy, j);
-  }
-}
-
-// Along x over the region: b -> a.
-__global__ void coif_syn_rows_kernel(const float2* __restrict__ b, float2* __restrict__ a, int w, int Sx, int Sy,
-                                     CoifTaps t) {
-  const long long n = (long long)Sx * Sy;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(i / Sx), j = (int)(i - (long long)r * Sx);
-    a[(long long)r * w + j] = coif_synth(t, b + (long long)r * w, 1, Sx, j);
-  }
-}
-
 // Re(u conj R) for the frame's reference (R = 1 for the plane wave), phase
 // in double-float per pixel.
 __device__ __forceinline__ float ref_re(const RefDbf& ref, float2 u, long long X, long long Y) {
@@ -95,47 +50,172 @@ __device__ __forceinline__ float ref_re(const RefDbf& ref, float2 u, long long X
   return fmaf(u.x, cs, ref.sgn * u.y * sn);
 }
 
-// Field and/or bits (eight pixels of a row per thread when bits are wanted).
-__global__ void coif_out_kernel(const float2* __restrict__ a, int w, int h, float2* __restrict__ u,
-                                uint8_t* __restrict__ bits, int ox, int oy, RefDbf ref) {
-  const int per = bits ? 8 : 1;
-  const long long n = (long long)w * h / per;
-  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
-    const long long i0 = g * per;
-    const long long y = i0 / w, x0 = i0 - y * w;
-    unsigned byte = 0;
-    for (int q = 0; q < per; ++q) {
-      const float2 v = a[i0 + q];
-      if (u) u[i0 + q] = v;
-      if (bits && ref_re(ref, v, ox + x0 + q, oy + y) > 0.f) byte |= 1u << q;
+// One synthesis level (L -> L - 1, ..., 1 -> 0) of the periodic inverse,
+// both directions in one pass over a TX x TY tile of the level's output (the
+// S x S low-pass band of the next finer level, S = side >> (l - 1)).  Output
+// sample j of a line takes h_k s[m] + g_k d[m] for k = j - 2m (mod the half
+// length): the taps of j's parity with m = j/2 + 1, j/2, j/2 - 1 (k = -2, 0, 2
+// for even j; -1, 1, 3 for odd j), each low tap then each high tap by fused
+// multiply-add in that order.  A tile of outputs needs TY/2 + 2 input rows and
+// TX/2 + 2 input columns of each of the four input bands (one cell of halo on
+// each side, wrapped); they are gathered into shared memory -- the detail
+// bands straight from the tile-major buffer, the low-pass band from the
+// coarser level's result (or the buffer at the coarsest level) -- then
+// synthesised along y for the needed columns and along x for the tile.
+constexpr int kCoifTX = 64, kCoifTY = 32;
+constexpr int kCoifNX = kCoifTX / 2 + 2, kCoifNY = kCoifTY / 2 + 2;
+
+struct CoifLevelArgs {
+  const float2* wbuf;  // tile-major wavelet buffer (side x side)
+  int side, L, l;      // hologram side, levels, level synthesised
+  const float2* prev;  // level-l low-pass band, dense (side >> l)^2; null at l == L (read from the buffer)
+  float2* out;         // level-(l - 1) low-pass band, dense S x S; the field (side x side) at l == 1, or null
+  uint8_t* bits;       // l == 1: the binary hologram against the reference, or null
+  int ox, oy;
+  RefDbf ref;
+  CoifTaps t;
+};
+
+// FULL: the level's side S is at least kCoifTX, so every tile is a whole
+// kCoifTX x kCoifTY and one wrap per index suffices (sizes known at compile
+// time: no integer division by a run-time value in the index arithmetic).
+template <bool FULL>
+__global__ void __launch_bounds__(256) coif_level_kernel(const __grid_constant__ CoifLevelArgs a) {
+  __shared__ float2 in[4][kCoifNY][kCoifNX];  // LL, LH (high x), HL (high y), HH
+  __shared__ float2 lx[kCoifTY][kCoifNX], hx[kCoifTY][kCoifNX];
+  const int S = a.side >> (a.l - 1), hh = S / 2;
+  const int TX = FULL ? kCoifTX : min(kCoifTX, S), TY = FULL ? kCoifTY : min(kCoifTY, S);
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int NX = TX / 2 + 2, NY = TY / 2 + 2;
+  const int m = a.L - a.l, msk = (1 << m) - 1, TSL = 1 << (2 * a.L), ntx = a.side >> a.L;
+  const int bx = x0 / 2 - 1, by = y0 / 2 - 1;  // first input column / row (unwrapped)
+  auto wrap = [&](int v) {
+    if (FULL) return v < 0 ? v + hh : (v >= hh ? v - hh : v);
+    return (v % hh + hh) % hh;
+  };
+  for (int i = threadIdx.x; i < 4 * NY * NX; i += blockDim.x) {
+    const int part = i / (NY * NX), r = (i / NX) % NY, c = i % NX;
+    const int P = wrap(bx + c), Q = wrap(by + r);
+    float2 v;
+    if (part == 0 && a.prev) {
+      v = a.prev[(size_t)Q * hh + P];
+    } else {
+      // Band `part` of level l at (P, Q): its tile and in-tile slot.
+      const size_t tile = (size_t)(Q >> m) * ntx + (P >> m);
+      const int slot = part == 0 ? 0 : (part << (2 * m)) + ((Q & msk) << m) + (P & msk);
+      v = a.wbuf[tile * TSL + slot];
     }
-    if (bits) bits[g] = (uint8_t)byte;
+    in[part][r][c] = v;
+  }
+  __syncthreads();
+  const CoifTaps& t = a.t;
+  // Along y: rows y0 .. y0 + TY - 1 of the low-x (LL, HL) and high-x (LH, HH)
+  // halves, for the NX input columns.
+  for (int i = threadIdx.x; i < TY * NX; i += blockDim.x) {
+    const int yy = i / NX, c = i - yy * NX;
+    const int par = (y0 + yy) & 1, rb = (yy >> 1) + 2;  // (y0 + yy) / 2 + 1 - by
+    float2 lo = make_float2(0.f, 0.f), hi = lo;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int k = 2 * q + par, r = rb - q;
+      const float2 s0 = in[0][r][c], d0 = in[2][r][c], s1 = in[1][r][c], d1 = in[3][r][c];
+      lo.x = __fmaf_rn(t.lo[k], s0.x, lo.x);
+      lo.y = __fmaf_rn(t.lo[k], s0.y, lo.y);
+      lo.x = __fmaf_rn(t.hi[k], d0.x, lo.x);
+      lo.y = __fmaf_rn(t.hi[k], d0.y, lo.y);
+      hi.x = __fmaf_rn(t.lo[k], s1.x, hi.x);
+      hi.y = __fmaf_rn(t.lo[k], s1.y, hi.y);
+      hi.x = __fmaf_rn(t.hi[k], d1.x, hi.x);
+      hi.y = __fmaf_rn(t.hi[k], d1.y, hi.y);
+    }
+    lx[yy][c] = lo;
+    hx[yy][c] = hi;
+  }
+  __syncthreads();
+  // Along x: thread -> row yy, E = min(8, TX) consecutive outputs (one byte
+  // of bits at the last level, where S is a multiple of 8).
+  const int E = min(8, TX), per_row = (TX + E - 1) / E;
+  for (int i = threadIdx.x; i < TY * per_row; i += blockDim.x) {
+    const int yy = i / per_row, xg = (i - yy * per_row) * E;
+    const int y = y0 + yy;
+    float2 o[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      o[e] = make_float2(0.f, 0.f);
+      if (e >= E || xg + e >= TX) continue;  // past the tile: no input columns
+      const int xx = xg + e, par = (x0 + xx) & 1, cb = (xx >> 1) + 2;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int k = 2 * q + par, c = cb - q;
+        const float2 sv = lx[yy][c], dv = hx[yy][c];
+        acc.x = __fmaf_rn(t.lo[k], sv.x, acc.x);
+        acc.y = __fmaf_rn(t.lo[k], sv.y, acc.y);
+        acc.x = __fmaf_rn(t.hi[k], dv.x, acc.x);
+        acc.y = __fmaf_rn(t.hi[k], dv.y, acc.y);
+      }
+      o[e] = acc;
+    }
+    const int x = x0 + xg;
+    if (x >= S || y >= S || xg >= TX) continue;
+    if (a.out) {
+      if (E == 8 && x + 8 <= S) {
+        float4* dst = reinterpret_cast<float4*>(a.out + (size_t)y * S + x);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dst[e] = make_float4(o[2 * e].x, o[2 * e].y, o[2 * e + 1].x, o[2 * e + 1].y);
+      } else {
+        for (int e = 0; e < E && x + e < S && xg + e < TX; ++e) a.out[(size_t)y * S + x + e] = o[e];
+      }
+    }
+    if (a.bits) {  // last level: S is the side, a multiple of 8, and E == 8
+      unsigned byte = 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (ref_re(a.ref, o[e], (long long)a.ox + x + e, (long long)a.oy + y) > 0.f) byte |= 1u << e;
+      a.bits[((size_t)y * S + x) >> 3] = (uint8_t)byte;
+    }
   }
 }
-
-unsigned grid_for(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 8192)); }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
 
-cudaError_t launch_coif_inverse(const float2* wbuf, int w, int h, int L, float2* a, float2* b, cudaStream_t s,
-                                float2* out) {
+// Inverse of an L-level periodic order-1 coiflet transform of a tile-major
+// wavelet buffer: levels L .. 1, each one pass (coif_level_kernel); the
+// coarser levels' results alternate between a and b (dense, side >> (l - 1)
+// a side); the last level writes the field (out) and/or the bits.
+cudaError_t launch_coif_inverse(const float2* wbuf, int side, int L, float2* a, float2* b, float2* out,
+                                uint8_t* bits, int ox, int oy, const RefDev& ref, cudaStream_t s) {
   double lo[6], hi[6];
   coif1_filters(lo, hi);
-  CoifTaps t;
-  for (int i = 0; i < 6; ++i) { t.lo[i] = (float)lo[i]; t.hi[i] = (float)hi[i]; }
-  cudaError_t e = launch_wbuf_to_mallat(wbuf, w, h, L, a, s);
-  for (int l = L; l >= 1 && e == cudaSuccess; --l) {
-    const int Sx = w >> (l - 1), Sy = h >> (l - 1);
-    const long long n = (long long)Sx * Sy;
-    coif_syn_cols_kernel<<<grid_for(n), 256, 0, s>>>(a, b, w, Sx, Sy, t);
-    if ((e = cudaGetLastError()) != cudaSuccess) break;
-    // The last level writes the field straight into `out` when given.
-    coif_syn_rows_kernel<<<grid_for(n), 256, 0, s>>>(b, (l == 1 && out) ? out : a, w, Sx, Sy, t);
-    e = cudaGetLastError();
+  CoifLevelArgs g;
+  for (int i = 0; i < 6; ++i) { g.t.lo[i] = (float)lo[i]; g.t.hi[i] = (float)hi[i]; }
+  g.wbuf = wbuf;
+  g.side = side;
+  g.L = L;
+  g.ox = ox;
+  g.oy = oy;
+  g.ref = ref_dbf(ref);
+  const float2* prev = nullptr;
+  float2* bufs[2] = {a, b};
+  for (int l = L; l >= 1; --l) {
+    const int S = side >> (l - 1);
+    g.l = l;
+    g.prev = prev;
+    g.out = l > 1 ? bufs[l & 1] : out;
+    g.bits = l > 1 ? nullptr : bits;
+    const int TX = std::min(kCoifTX, S), TY = std::min(kCoifTY, S);
+    const dim3 grid((unsigned)((S + TX - 1) / TX), (unsigned)((S + TY - 1) / TY));
+    if (S >= kCoifTX && S % kCoifTX == 0)
+      coif_level_kernel<true><<<grid, 256, 0, s>>>(g);
+    else
+      coif_level_kernel<false><<<grid, 256, 0, s>>>(g);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    prev = g.out;
   }
-  return e;
+  return cudaSuccess;
 }
 
 }  // namespace wsb
@@ -189,14 +269,8 @@ wasabi_status wasabi_inverse_wavelet(const void* wbuf_dev, int holo_w, int holo_
   const cudaStream_t s = (cudaStream_t)stream;
   float2* a = static_cast<float2*>(scratch_dev);
   float2* b = reinterpret_cast<float2*>(static_cast<char*>(scratch_dev) + need / 2);
-  float2* u = static_cast<float2*>(u_dev);
-  cudaError_t e = launch_coif_inverse(static_cast<const float2*>(wbuf_dev), holo_w, holo_h, levels, a, b, s, u);
-  if (e == cudaSuccess && bits_dev) {  // the field is in u when it was asked for, else in a
-    const long long groups = (long long)holo_w * holo_h / 8;
-    coif_out_kernel<<<grid_for(groups), 256, 0, s>>>(u ? u : a, holo_w, holo_h, nullptr, bits_dev, ox, oy,
-                                                     ref_dbf(ref));
-    e = cudaGetLastError();
-  }
+  const cudaError_t e = launch_coif_inverse(static_cast<const float2*>(wbuf_dev), holo_w, levels, a, b,
+                                            static_cast<float2*>(u_dev), bits_dev, ox, oy, ref, s);
   return e == cudaSuccess ? WASABI_OK : cuda_fail("inverse_wavelet", e);
 }
 
