@@ -93,7 +93,35 @@ __global__ void __launch_bounds__(256) coif_level_kernel(const __grid_constant__
     if (FULL) return v < 0 ? v + hh : (v >= hh ? v - hh : v);
     return (v % hh + hh) % hh;
   };
-  for (int i = threadIdx.x; i < 4 * NY * NX; i += blockDim.x) {
+  if (FULL) {
+    // Pairs of neighbouring cells (P even, P + 1) in one 16-byte load: both
+    // lie in one row of one tile of the buffer (P and P + 1 differ only in
+    // the lowest bit) or of the dense low-pass band, and never straddle the
+    // periodic wrap (the half side is even).  Input columns c = P - bx run
+    // from -1 to kCoifNX; the two outside [0, kCoifNX) are dropped.
+    constexpr int NP = kCoifNX / 2 + 1;  // pairs per input row
+    for (int i = threadIdx.x; i < 4 * kCoifNY * NP; i += blockDim.x) {
+      const int part = i / (kCoifNY * NP), r = (i / NP) % kCoifNY, j = i % NP;
+      const int c0 = 2 * j - 1;  // column of the pair's first cell
+      const int P = wrap(bx + c0), Q = wrap(by + r);
+      float4 v;
+      if (part == 0 && a.prev) {
+        v = *reinterpret_cast<const float4*>(a.prev + (size_t)Q * hh + P);
+      } else {
+        const size_t tile = (size_t)(Q >> m) * ntx + (P >> m);
+        const int slot = part == 0 ? 0 : (part << (2 * m)) + ((Q & msk) << m) + (P & msk);
+        if (m == 0) {  // the coarsest level: neighbouring cells are in neighbouring tiles
+          const float2 v0 = a.wbuf[tile * TSL + slot], v1 = a.wbuf[(tile + 1) * TSL + slot];
+          v = make_float4(v0.x, v0.y, v1.x, v1.y);
+        } else {
+          v = *reinterpret_cast<const float4*>(a.wbuf + tile * TSL + slot);
+        }
+      }
+      if (c0 >= 0) in[part][r][c0] = make_float2(v.x, v.y);
+      if (c0 + 1 < kCoifNX) in[part][r][c0 + 1] = make_float2(v.z, v.w);
+    }
+  }
+  for (int i = threadIdx.x; !FULL && i < 4 * NY * NX; i += blockDim.x) {
     const int part = i / (NY * NX), r = (i / NX) % NY, c = i % NX;
     const int P = wrap(bx + c), Q = wrap(by + r);
     float2 v;
@@ -109,52 +137,63 @@ __global__ void __launch_bounds__(256) coif_level_kernel(const __grid_constant__
   }
   __syncthreads();
   const CoifTaps& t = a.t;
-  // Along y: rows y0 .. y0 + TY - 1 of the low-x (LL, HL) and high-x (LH, HH)
-  // halves, for the NX input columns.
-  for (int i = threadIdx.x; i < TY * NX; i += blockDim.x) {
-    const int yy = i / NX, c = i - yy * NX;
-    const int par = (y0 + yy) & 1, rb = (yy >> 1) + 2;  // (y0 + yy) / 2 + 1 - by
-    float2 lo = make_float2(0.f, 0.f), hi = lo;
+  // Along y: thread -> one input column c and eight output rows; the six
+  // input rows those rows need are read once per band.
+  auto synth = [&](const float2* sv, const float2* dv, int par, int base) {
+    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const int k = 2 * q + par, r = rb - q;
-      const float2 s0 = in[0][r][c], d0 = in[2][r][c], s1 = in[1][r][c], d1 = in[3][r][c];
-      lo.x = __fmaf_rn(t.lo[k], s0.x, lo.x);
-      lo.y = __fmaf_rn(t.lo[k], s0.y, lo.y);
-      lo.x = __fmaf_rn(t.hi[k], d0.x, lo.x);
-      lo.y = __fmaf_rn(t.hi[k], d0.y, lo.y);
-      hi.x = __fmaf_rn(t.lo[k], s1.x, hi.x);
-      hi.y = __fmaf_rn(t.lo[k], s1.y, hi.y);
-      hi.x = __fmaf_rn(t.hi[k], d1.x, hi.x);
-      hi.y = __fmaf_rn(t.hi[k], d1.y, hi.y);
+      const int k = 2 * q + par, r = base - q;
+      acc.x = __fmaf_rn(t.lo[k], sv[r].x, acc.x);
+      acc.y = __fmaf_rn(t.lo[k], sv[r].y, acc.y);
+      acc.x = __fmaf_rn(t.hi[k], dv[r].x, acc.x);
+      acc.y = __fmaf_rn(t.hi[k], dv[r].y, acc.y);
     }
-    lx[yy][c] = lo;
-    hx[yy][c] = hi;
+    return acc;
+  };
+  const int ngy = (TY + 7) / 8;
+  for (int i = threadIdx.x; i < ngy * NX; i += blockDim.x) {
+    const int gy = i / NX, c = i - gy * NX, yb = 8 * gy;
+    // Output rows yb .. yb + 7 need input rows yb/2 .. yb/2 + 5.
+    float2 s0[6], d0[6], s1[6], d1[6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      const int rr = min(yb / 2 + r, NY - 1);
+      s0[r] = in[0][rr][c];
+      d0[r] = in[2][rr][c];
+      s1[r] = in[1][rr][c];
+      d1[r] = in[3][rr][c];
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int yy = yb + e;
+      if (yy >= TY) break;
+      const int par = (y0 + yy) & 1, base = (e >> 1) + 2;  // (yy >> 1) + 2 - yb / 2
+      lx[yy][c] = synth(s0, d0, par, base);
+      hx[yy][c] = synth(s1, d1, par, base);
+    }
   }
   __syncthreads();
   // Along x: thread -> row yy, E = min(8, TX) consecutive outputs (one byte
-  // of bits at the last level, where S is a multiple of 8).
+  // of bits at the last level, where S is a multiple of 8); the six input
+  // columns they need are read once.
   const int E = min(8, TX), per_row = (TX + E - 1) / E;
   for (int i = threadIdx.x; i < TY * per_row; i += blockDim.x) {
     const int yy = i / per_row, xg = (i - yy * per_row) * E;
     const int y = y0 + yy;
+    float2 sv[6], dv[6];
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) {
+      const int c = min(xg / 2 + cc, NX - 1);
+      sv[cc] = lx[yy][c];
+      dv[cc] = hx[yy][c];
+    }
     float2 o[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       o[e] = make_float2(0.f, 0.f);
       if (e >= E || xg + e >= TX) continue;  // past the tile: no input columns
-      const int xx = xg + e, par = (x0 + xx) & 1, cb = (xx >> 1) + 2;
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int k = 2 * q + par, c = cb - q;
-        const float2 sv = lx[yy][c], dv = hx[yy][c];
-        acc.x = __fmaf_rn(t.lo[k], sv.x, acc.x);
-        acc.y = __fmaf_rn(t.lo[k], sv.y, acc.y);
-        acc.x = __fmaf_rn(t.hi[k], dv.x, acc.x);
-        acc.y = __fmaf_rn(t.hi[k], dv.y, acc.y);
-      }
-      o[e] = acc;
+      o[e] = synth(sv, dv, (x0 + xg + e) & 1, (e >> 1) + 2);
     }
     const int x = x0 + xg;
     if (x >= S || y >= S || xg >= TX) continue;
