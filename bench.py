@@ -47,11 +47,15 @@ TRAFFIC = {("C3", "fused"): ("7551f1a469529e2d", (11.013e6 + 79.222e6) * 4.015)}
 ISSUE = {("C3", "fused"): ("7551f1a469529e2d", 0.650, 2.49)}
 
 
-def _superpose_sha():
+def _sha(name):
     import hashlib
-    src = os.path.join(ROOT, "paper_1708_04233_gb300", "csrc", "superpose.cu")
+    src = os.path.join(ROOT, "paper_1708_04233_gb300", "csrc", name)
     with open(src, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _superpose_sha():
+    return _sha("superpose.cu")
 
 
 def _traffic(c, path):
@@ -322,6 +326,36 @@ def streaming_summary(w, torch, dev, c, side: int, band_h: int, reps: int = 2):
             "device_bytes_held": "two bands of bits + two binning scratches"}
 
 
+# FP32 lane instructions (FFMA + FADD + FMUL, ncu smsp__sass_thread_inst_executed_op_*_pred_on)
+# per term of the apertured Eq. (1) kernel at C2 (9.61e11 for 1.714e10 terms),
+# valid while direct.cu is the profiled source (sha256 prefix).
+DIRECT_FP32 = ("c38be776c999e9af", 9.6120e11 / 17138704217)
+
+
+def eq1_terms(x, y, z, lam, pitch, w, h):
+    """Point-pixel pairs the apertured Eq. (1) sums: pixels (x + dx, y + dy)
+    inside the w x h hologram with dx^2 + dy^2 < R(z)^2, R the support radius
+    z tan(asin(lambda / 2p)) / p (the point's own pixel always counts)."""
+    s = lam / (2 * pitch)
+    R2 = (np.abs(z) * (s / np.sqrt(1 - s * s)) / pitch) ** 2
+    x = np.asarray(x, np.int64)
+    y = np.asarray(y, np.int64)
+    rmax = int(np.ceil(np.sqrt(R2.max()))) + 1 if R2.size else 0
+    total = 0
+    for dy in range(-rmax, rmax + 1):
+        T = R2 - dy * dy
+        ok = T > 0
+        hw = np.where(ok, np.ceil(np.sqrt(np.maximum(T, 0))) - 1, -1).astype(np.int64)
+        hw = np.where(ok & ((hw + 1) ** 2 < T), hw + 1, hw)  # |dx| <= hw  <=>  dx^2 < T
+        hw = np.where(ok & (hw ** 2 >= T), hw - 1, hw)
+        if dy == 0:
+            hw = np.maximum(hw, 0)
+        yy = y + dy
+        lo, hi = np.maximum(x - hw, 0), np.minimum(x + hw, w - 1)
+        total += int(np.sum(np.where((yy >= 0) & (yy < h) & (hw >= 0) & (hi >= lo), hi - lo + 1, 0)))
+    return total
+
+
 def direct_comparison(w, torch, dev, c, depths, pbuf, u_wasabi, stream, wasabi_step_ms):
     """C2: Eq. (1) summed directly on the GPU (aperture form) on the same
     points, its time against the WASABI step, and the WASABI approximation
@@ -358,7 +392,19 @@ def direct_comparison(w, torch, dev, c, depths, pbuf, u_wasabi, stream, wasabi_s
     pool = lambda x: torch.nn.functional.avg_pool2d(x[None, None], 1 << c.L)[0, 0]
     corr_pooled = corr_of(pool(a_), pool(b_))
     direct_comparison.u_direct = u_direct
+    # Roofline: FP32 lane instructions per term (ncu, this source) x terms,
+    # against 152 SMs x 128 FP32 lanes x the maximum SM clock.
+    p_host = pbuf.cpu().numpy()
+    terms = eq1_terms(p_host[:, 0], p_host[:, 1], np.asarray(depths)[p_host[:, 3].view(np.uint32)], c.lam,
+                      c.pitch, c.Nh, c.Nh)
+    peak = 152 * 128 * 2070e6
+    roof = {"bound": "alu", "unit": "FP32 lane-instr/s", "terms": terms, "terms_per_s": terms / (ms * 1e-3),
+            "peak": peak, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz"}
+    if _sha("direct.cu") == DIRECT_FP32[0]:
+        ach = DIRECT_FP32[1] * terms / (ms * 1e-3)
+        roof.update({"fp32_instr_per_term": DIRECT_FP32[1], "achieved": ach, "frac": ach / peak})
     return {"kernel": "direct_kernel (Eq. (1), aperture form; double-float phase reduction)", "ms": ms,
+            "roofline": roof,
             "wasabi_step_ms": wasabi_step_ms, "speedup": ms / wasabi_step_ms,
             "rel_l2_wasabi_vs_eq1": float(diff / ref),
             "reconstruction": {"d_m": -zmid, "ms": rms, "method": "angular spectrum (cuFFT C2C)",
