@@ -12,16 +12,19 @@
 //      plus one tile of carry) meets the super-tile; for each kept level it
 //      folds the point's shift of Eq. (2) into one accumulator base;
 //   3. cuts every survivor's LUT entries that can land in the super-tile into
-//      passes of at most 32 consecutive entries: one LUT range per window-tile
-//      row (contiguous by construction of the LUT), split every 32 entries.
-//      A block-wide scan numbers the passes, so the list is the same in every
-//      run;
-//   4. deals the passes evenly to the warps; a warp takes one pass at a time
-//      (four in flight), lane i visiting entry i of the pass: one 8-byte
-//      record load (plane code, value), the survivor's level base from shared
-//      memory, a_j * c, one shared-memory add at base + code (no bounds test:
-//      coefficients that land outside the super-tile fall into the guard band
-//      and are dropped);
+//      passes of at most 64 consecutive entries: one LUT range per window-tile
+//      row (contiguous by construction of the LUT), split every 64 entries.
+//      Each thread loads the ranges of several rows at once, and each warp
+//      reserves its passes with one shared-memory add (the list's order
+//      varies, the exact fixed-point sums do not); a batch with more passes
+//      than the list holds is numbered by a block-wide scan instead and
+//      visited in windows;
+//   4. deals the passes to the warps in groups of two, lane i visiting
+//      entries i and i + 32 of a pass: one 8-byte record load (plane code,
+//      value), the survivor's level base from shared memory, a_j * c, one
+//      shared-memory add at base + code (no bounds test: coefficients that
+//      land outside the super-tile fall into the guard band and are
+//      dropped);
 //   5. writes the finished super-tile once: to the tile-major wavelet buffer
 //      (streaming vector stores, zeros for absent levels) and/or, through the
 //      inverse transform in shared memory, as the complex field or the packed
@@ -43,6 +46,7 @@ namespace {
 constexpr int kMaxCellRows = 256;
 constexpr int kPass = 64;         // LUT entries per pass (two per lane)
 constexpr int kPassUnroll = 2;    // passes a warp has in flight
+constexpr int kSlotChunk = 4;     // LUT range slots a thread has in flight while building passes
 constexpr int kRangeMin = 1024;   // pass capacity per window, at least
 constexpr int kRangeMax = 8192;   // pass capacity per window, at most
 constexpr int kSurvMax = 1024;    // survivors per candidate batch, at most
@@ -75,34 +79,6 @@ __device__ __forceinline__ float2 decode16(uint32_t q, float s) {
     im = __bfloat162float(__ushort_as_bfloat16((unsigned short)(q >> 16)));
   }
   return make_float2(re * s, im * s);
-}
-
-// Exclusive scan over the block of one int per thread; returns the prefix and
-// writes the total to *total (all threads).
-__device__ __forceinline__ int block_scan(int v, int* total, int* warp_buf) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) warp_buf[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    int t = lane < nw ? warp_buf[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
-    }
-    warp_buf[lane] = t;
-  }
-  __syncthreads();
-  const int excl = (wid ? warp_buf[wid - 1] : 0) + x - v;
-  *total = warp_buf[31];
-  __syncthreads();
-  return excl;
 }
 
 // Last index r in [lo, hi] with pre[r] <= v (pre non-decreasing, pre[lo] <= v).
@@ -596,8 +572,7 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
   Smem S;
   smem_layout(T, L, lmin, a.lut.D, re_acc, rcap, &S, smem);
   const int NW = NA * (re_acc ? 1 : 2);  // accumulator words (a multiple of 4)
-  __shared__ int s_st, s_n, s_total;
-  __shared__ int warp_buf[32];
+  __shared__ int s_st, s_n, s_np[2], s_total;
   __shared__ int s_rowstart[kMaxCellRows], s_rowpre[kMaxCellRows + 1];
   // Per level l: index of the first super-tile cell past the guard, row
   // stride, plane size (see plane_code).
@@ -711,7 +686,10 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
     const int CH = min(P, NT);  // candidates per batch: at most one per thread
     for (int c0 = 0; c0 < total; c0 += CH) {
       // ---- survivors of this batch of candidates
-      if (tid == 0) s_n = 0;
+      if (tid == 0) {
+        s_n = 0;
+        s_np[0] = 0;
+      }
       __syncthreads();
       if (tid < CH && c0 + tid < total) {
         const int i = c0 + tid;
@@ -738,72 +716,63 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
       }
       __syncthreads();
       const int n = s_n;
-      // ---- passes: slot f = s * (k + 1) + j is window-tile row j of the
-      // survivor's clipped tile box; thread t owns slots [t * per, (t + 1) * per).
-      const int nslot = n * (k + 1);
-      const int per = (nslot + NT - 1) / NT;
+      // ---- slot f = s * (k + 1) + j is window-tile row j of the survivor's
+      // clipped tile box.
+      const int K1 = k + 1;
+      const int nslot = n * K1;
       const unsigned sp_s = sh_addr(S.sp), sb_s = sh_addr(S.sb), pass_s = sh_addr(S.pass), box_s = sh_addr(S.dbox);
       const unsigned acc_s = sh_addr(S.acc);
-      // Walks this thread's slots in order, calling fn(survivor, first entry,
-      // entries, amplitude bits) for each non-empty LUT range; the survivor's
-      // clipped tile box is computed once per survivor.
+      // Walks this thread's slots t, t + NT, t + 2 NT, ... kSlotChunk at a
+      // time, the LUT range loads of a chunk in flight together, and calls
+      // fn(st, ln, sv, am, np) per chunk with each slot's first entry, entry
+      // count, survivor and amplitude bits (empty slots: no entries), np the
+      // chunk's passes.  The trip count is the same for every thread.
       auto walk_slots = [&](auto&& fn) {
-        const int f0 = tid * per;
-        const int f1 = min(nslot, f0 + per);
-        if (f0 >= f1) return;
-        int s = f0 / (k + 1), j = f0 - s * (k + 1);
-        int cur = -1, tya = 0, tyb = -1, txa = 0, txb = -1, dro = 0, ampb = 0;
-        for (int f = f0; f < f1; ++f) {
-          if (s != cur) {
-            cur = s;
-            const int4 sp = lds128(sp_s + 16u * s);
-            const int2 bx = lds64(box_s + 8u * sp.z);
-            tya = max(bx.x, Sy - sp.y - 1);
-            tyb = min(bx.y, Sy + ky - 1 - sp.y);
-            txa = max(bx.x, Sx - sp.x - 1);
-            txb = min(bx.y, Sx + kx - 1 - sp.x);
-            dro = sp.z * ntpd;
-            ampb = sp.w;
+        int s = tid / K1, j = tid - s * K1;
+        const int ds = NT / K1, dj = NT - ds * K1;
+        for (int f0 = 0; f0 < nslot; f0 += kSlotChunk * NT) {
+          int st[kSlotChunk], ln[kSlotChunk], sv[kSlotChunk], am[kSlotChunk];
+#pragma unroll
+          for (int c = 0; c < kSlotChunk; ++c) {
+            st[c] = 0;
+            ln[c] = 0;
+            sv[c] = s;
+            am[c] = 0;
+            if (f0 + c * NT + tid < nslot) {
+              const int4 sp = lds128(sp_s + 16u * s);
+              const int2 bx = lds64(box_s + 8u * sp.z);
+              const int row = max(bx.x, Sy - sp.y - 1) + j;
+              const int tyb = min(bx.y, Sy + ky - 1 - sp.y);
+              const int txa = max(bx.x, Sx - sp.x - 1), txb = min(bx.y, Sx + kx - 1 - sp.x);
+              if (row <= tyb && txa <= txb) {
+                const int* to = lut.tile_off + sp.z * ntpd + row * lut.nwt;
+                st[c] = __ldg(to + txa);
+                ln[c] = __ldg(to + txb + 1);
+              }
+              am[c] = sp.w;
+            }
+            s += ds;
+            j += dj;
+            if (j >= K1) {
+              j -= K1;
+              ++s;
+            }
           }
-          const int row = tya + j;
-          if (row <= tyb && txa <= txb) {
-            const int ro = dro + row * lut.nwt;
-            const int st0 = __ldg(&lut.tile_off[ro + txa]);
-            const int len = __ldg(&lut.tile_off[ro + txb + 1]) - st0;
-            if (len > 0) fn(s, st0, len, ampb);
+          int np = 0;
+#pragma unroll
+          for (int c = 0; c < kSlotChunk; ++c) {
+            ln[c] -= st[c];
+            np += (ln[c] + kPass - 1) / kPass;
           }
-          if (++j == k + 1) {
-            j = 0;
-            ++s;
-          }
+          fn(st, ln, sv, am, np);
         }
       };
-      int mine = 0;
-      walk_slots([&](int, int, int len, int) { mine += (len + kPass - 1) / kPass; });
-      int npass;
-      const int pbase = block_scan(mine, &npass, warp_buf);
-      // Passes in windows of rcap: the slots write the window's passes, then
-      // the warps visit them.
-      for (int w0 = 0; w0 < npass; w0 += rcap) {
-        const int np = min(rcap, npass - w0);
-        const int ng = (np + kPassUnroll - 1) / kPassUnroll;  // groups of kPassUnroll passes
-        if (mine > 0 && pbase < w0 + rcap && pbase + mine > w0) {
-          int pi = pbase;
-          walk_slots([&](int s, int st0, int len, int ampb) {
-            for (int o = 0; o < len; o += kPass, ++pi)
-              if (pi >= w0 && pi < w0 + rcap)
-                S.pass[pi - w0] = make_int4(st0 + o, min(kPass, len - o), (int)(sb_s + 32u * s), ampb);
-          });
-        }
-        // The last group is filled with empty passes (no entries; their
-        // loaded entries are entry 0 and their level bases those of survivor 0).
-        if (tid < ng * kPassUnroll - np) S.pass[np + tid] = make_int4(1, 0, (int)sb_s, 0);
-        __syncthreads();
-        // ---- visits: warp w takes groups w, w + warps, ...; a group's
-        // records and LUT loads are all issued before any is consumed.  Lane
-        // i visits entries i, i + 32, ... of each pass; lanes past a pass's
-        // end load a valid entry and add nothing.
-        auto visit = [&](auto fixed_tag) {
+      // ---- visits: warp w takes groups w, w + warps, ... of the ng groups
+      // of kPassUnroll passes; a group's records and LUT loads are all
+      // issued before any is consumed.  Lane i visits entries i, i + 32, ...
+      // of each pass; lanes past a pass's end load a valid entry and add
+      // nothing.
+      auto visit = [&](auto fixed_tag, int ng) {
           constexpr bool FX = decltype(fixed_tag)::value;
           constexpr int EPL = kPass / 32;  // entries per lane and pass
           for (int g = warp; g < ng; g += nwarps) {
@@ -858,9 +827,56 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
             }
           }
         };
-        if (fixed) visit(std::true_type{});
-        else visit(std::false_type{});
+      auto pad_visit = [&](int np) {
+        // The last group is filled with empty passes (no entries; their
+        // loaded entries are entry 0 and their level bases those of survivor 0).
+        const int ng = (np + kPassUnroll - 1) / kPassUnroll;
+        if (tid < ng * kPassUnroll - np) S.pass[np + tid] = make_int4(1, 0, (int)sb_s, 0);
         __syncthreads();
+        if (fixed) visit(std::true_type{}, ng);
+        else visit(std::false_type{}, ng);
+        __syncthreads();
+      };
+      // ---- passes: every walk over the slots appends the passes not yet
+      // visited to the list, a warp reserving its passes with one
+      // shared-memory add, and stores those that fit; then the warps visit
+      // the list.  A thread's reservations grow along its slot order, so the
+      // passes it has stored are always the first `done` of its sequence,
+      // and a batch with more passes than the list holds takes one more walk
+      // per list.  The list's order varies from run to run; the fixed-point
+      // sums do not depend on it.  Two counters alternate, so one is reset
+      // while the other is in use.
+      int done = 0;
+      for (int round = 0;; ++round) {
+        int* cnt = &s_np[round & 1];
+        if (tid == 0) s_np[(round + 1) & 1] = 0;  // last read before the previous visit's barriers
+        int seen = 0;  // this thread's passes in the chunks walked so far
+        walk_slots([&](const int* st, const int* ln, const int* sv, const int* am, int np) {
+          const int skip = min(max(done - seen, 0), np);  // stored in an earlier round
+          seen += np;
+          const int want = np - skip;
+          int incl = want;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+          }
+          const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+          int wb = 0;
+          if (lane == 0 && wtot > 0) wb = atomicAdd(cnt, wtot);
+          const int base = __shfl_sync(0xffffffffu, wb, 0) + incl - want;
+          int pi = base - skip;  // list index of the chunk's first pass
+#pragma unroll
+          for (int c = 0; c < kSlotChunk; ++c)
+            for (int o = 0; o < ln[c]; o += kPass, ++pi)
+              if (pi >= base && pi < rcap)
+                S.pass[pi] = make_int4(st[c] + o, min(kPass, ln[c] - o), (int)(sb_s + 32u * sv[c]), am[c]);
+          done += max(0, min(want, rcap - base));
+        });
+        __syncthreads();
+        const int nres = *cnt;
+        pad_visit(min(nres, rcap));
+        if (nres <= rcap) break;
       }
     }
 
