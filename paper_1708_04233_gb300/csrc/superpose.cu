@@ -81,6 +81,34 @@ __device__ __forceinline__ float2 decode16(uint32_t q, float s) {
   return make_float2(re * s, im * s);
 }
 
+// Exclusive scan over the block of one int per thread; returns the prefix and
+// writes the total to *total (all threads).
+__device__ __forceinline__ int block_scan(int v, int* total, int* warp_buf) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_buf[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int t = lane < nw ? warp_buf[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    warp_buf[lane] = t;
+  }
+  __syncthreads();
+  const int excl = (wid ? warp_buf[wid - 1] : 0) + x - v;
+  *total = warp_buf[31];
+  __syncthreads();
+  return excl;
+}
+
 // Last index r in [lo, hi] with pre[r] <= v (pre non-decreasing, pre[lo] <= v).
 __device__ __forceinline__ int last_le(const int* pre, int lo, int hi, int v) {
   while (lo < hi) {
@@ -572,7 +600,8 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
   Smem S;
   smem_layout(T, L, lmin, a.lut.D, re_acc, rcap, &S, smem);
   const int NW = NA * (re_acc ? 1 : 2);  // accumulator words (a multiple of 4)
-  __shared__ int s_st, s_n, s_np[2], s_total;
+  __shared__ int s_st, s_n, s_np, s_total;
+  __shared__ int warp_buf[32];
   __shared__ int s_rowstart[kMaxCellRows], s_rowpre[kMaxCellRows + 1];
   // Per level l: index of the first super-tile cell past the guard, row
   // stride, plane size (see plane_code).
@@ -688,7 +717,7 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
       // ---- survivors of this batch of candidates
       if (tid == 0) {
         s_n = 0;
-        s_np[0] = 0;
+        s_np = 0;
       }
       __syncthreads();
       if (tid < CH && c0 + tid < total) {
@@ -726,7 +755,8 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
       // time, the LUT range loads of a chunk in flight together, and calls
       // fn(st, ln, sv, am, np) per chunk with each slot's first entry, entry
       // count, survivor and amplitude bits (empty slots: no entries), np the
-      // chunk's passes.  The trip count is the same for every thread.
+      // chunk's passes; fn returns false to stop.  While fn returns true the
+      // trip count is the same for every thread.
       auto walk_slots = [&](auto&& fn) {
         int s = tid / K1, j = tid - s * K1;
         const int ds = NT / K1, dj = NT - ds * K1;
@@ -764,7 +794,7 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
             ln[c] -= st[c];
             np += (ln[c] + kPass - 1) / kPass;
           }
-          fn(st, ln, sv, am, np);
+          if (!fn(st, ln, sv, am, np)) break;
         }
       };
       // ---- visits: warp w takes groups w, w + warps, ... of the ng groups
@@ -837,46 +867,60 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
         else visit(std::false_type{}, ng);
         __syncthreads();
       };
-      // ---- passes: every walk over the slots appends the passes not yet
-      // visited to the list, a warp reserving its passes with one
-      // shared-memory add, and stores those that fit; then the warps visit
-      // the list.  A thread's reservations grow along its slot order, so the
-      // passes it has stored are always the first `done` of its sequence,
-      // and a batch with more passes than the list holds takes one more walk
-      // per list.  The list's order varies from run to run; the fixed-point
-      // sums do not depend on it.  Two counters alternate, so one is reset
-      // while the other is in use.
-      int done = 0;
-      for (int round = 0;; ++round) {
-        int* cnt = &s_np[round & 1];
-        if (tid == 0) s_np[(round + 1) & 1] = 0;  // last read before the previous visit's barriers
-        int seen = 0;  // this thread's passes in the chunks walked so far
-        walk_slots([&](const int* st, const int* ln, const int* sv, const int* am, int np) {
-          const int skip = min(max(done - seen, 0), np);  // stored in an earlier round
-          seen += np;
-          const int want = np - skip;
-          int incl = want;
+      // ---- passes, one walk: a warp reserves its passes with one
+      // shared-memory add and stores those that fit in the list.  The list's
+      // order varies from run to run; the fixed-point sums do not depend on
+      // it.  A thread's reservations grow along its slot order, so the passes
+      // it has stored are the first `done` of its sequence of `total`.
+      int done = 0, total = 0;
+      walk_slots([&](const int* st, const int* ln, const int* sv, const int* am, int np) {
+        int incl = np;
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+        int wb = 0;
+        if (lane == 0 && wtot > 0) wb = atomicAdd(&s_np, wtot);
+        int pi = __shfl_sync(0xffffffffu, wb, 0) + incl - np;
+        done += max(0, min(np, rcap - pi));
+        total += np;
+#pragma unroll
+        for (int c = 0; c < kSlotChunk; ++c)
+          for (int o = 0; o < ln[c]; o += kPass, ++pi)
+            if (pi < rcap) S.pass[pi] = make_int4(st[c] + o, min(kPass, ln[c] - o), (int)(sb_s + 32u * sv[c]), am[c]);
+        return true;
+      });
+      __syncthreads();
+      const int nres = s_np;
+      pad_visit(min(nres, rcap));
+      if (nres > rcap) {
+        // The passes that did not fit: a block-wide scan numbers each
+        // thread's rest, and every list of rcap of them is written by the
+        // threads whose numbers meet it (walking up to the list's end), then
+        // visited.
+        const int rest = total - done;
+        int nrest;
+        const int pbase = block_scan(rest, &nrest, warp_buf);
+        for (int w0 = 0; w0 < nrest; w0 += rcap) {
+          if (rest > 0 && pbase < w0 + rcap && pbase + rest > w0) {
+            int pi = pbase - done;  // number of the sequence's first pass (the stored ones fall below pbase)
+            walk_slots([&](const int* st, const int* ln, const int* sv, const int* am, int np) {
+              if (pi + np > max(pbase, w0)) {
+                int q = pi;
+#pragma unroll
+                for (int c = 0; c < kSlotChunk; ++c)
+                  for (int o = 0; o < ln[c]; o += kPass, ++q)
+                    if (q >= pbase && q >= w0 && q < w0 + rcap)
+                      S.pass[q - w0] = make_int4(st[c] + o, min(kPass, ln[c] - o), (int)(sb_s + 32u * sv[c]), am[c]);
+              }
+              pi += np;
+              return pi < w0 + rcap;
+            });
           }
-          const int wtot = __shfl_sync(0xffffffffu, incl, 31);
-          int wb = 0;
-          if (lane == 0 && wtot > 0) wb = atomicAdd(cnt, wtot);
-          const int base = __shfl_sync(0xffffffffu, wb, 0) + incl - want;
-          int pi = base - skip;  // list index of the chunk's first pass
-#pragma unroll
-          for (int c = 0; c < kSlotChunk; ++c)
-            for (int o = 0; o < ln[c]; o += kPass, ++pi)
-              if (pi >= base && pi < rcap)
-                S.pass[pi] = make_int4(st[c] + o, min(kPass, ln[c] - o), (int)(sb_s + 32u * sv[c]), am[c]);
-          done += max(0, min(want, rcap - base));
-        });
-        __syncthreads();
-        const int nres = *cnt;
-        pad_visit(min(nres, rcap));
-        if (nres <= rcap) break;
+          pad_visit(min(rcap, nrest - w0));
+        }
       }
     }
 

@@ -241,3 +241,34 @@ def test_widest_tiles_many_candidate_batches(w, orc, monkeypatch, want, T, rcap)
         check_field(got, ref, bnd)
     print(f"{want} T={T}: {flips} bit flips of {Nh * Nh}")
     lut.close()
+
+
+@pytest.mark.parametrize("want,T", [("both", 192), ("bits", 256)])
+def test_pass_list_overflow_is_exact(w, monkeypatch, want, T):
+    """Dense points: every candidate batch has more passes than the pass list
+    holds (at its smallest capacity, 1,024 passes), so the passes that do not
+    fit are numbered by the block-wide scan and visited in further lists.  The
+    fixed-point sums are exact, so the result must equal, bit for bit, the
+    same launch with the default capacity (whose batches overflow less)."""
+    monkeypatch.setenv("WASABI_SUPERPOSE_T", str(T))
+    monkeypatch.setenv("WASABI_SUPERPOSE_THREADS", "1024")
+    lam, pitch, zmin, zmax, D, W, L, gamma, Nh, N = 633e-9, 1e-6, 0.1e-3, 1.0e-3, 16, 1024, 4, 0.01, 768, 2500
+    r = np.random.default_rng(5)
+    x = r.integers(-200, Nh + 200, N).astype(np.int32)
+    y = r.integers(-200, Nh + 200, N).astype(np.int32)
+    a = r.uniform(0.2, 1.0, N).astype(np.float32)
+    d = r.integers(0, D, N).astype(np.int32)
+    zd = np.linspace(zmin, zmax, D)
+    lut = w.build_lut(lam, pitch, zd, W, L, gamma)
+    p = w.pack_points(x, y, a, d)
+    outs = []
+    for rcap in (None, "1024"):
+        if rcap:
+            monkeypatch.setenv("WASABI_RANGE_CAP", rcap)
+        out = w.hologram(lut, p, Nh, Nh, want=want)
+        w.sync_status()
+        outs.append([t.cpu().numpy() for t in (out if want == "both" else (out,))])
+    for u, v in zip(*outs):
+        assert np.array_equal(u, v)
+    assert np.count_nonzero(outs[0][-1]) > 0
+    lut.close()
