@@ -63,6 +63,14 @@ __device__ __forceinline__ float ref_re(const RefDbf& ref, float2 u, long long X
 // coarser level's result (or the buffer at the coarsest level) -- then
 // synthesised along y for the needed columns and along x for the tile.
 constexpr int kCoifTX = 64, kCoifTY = 32;
+
+// Asynchronous global-to-shared copies (cached in L2 only for 16 bytes).
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(unsigned dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
 constexpr int kCoifNX = kCoifTX / 2 + 2, kCoifNY = kCoifTY / 2 + 2;
 
 struct CoifLevelArgs {
@@ -81,7 +89,9 @@ struct CoifLevelArgs {
 // time: no integer division by a run-time value in the index arithmetic).
 template <bool FULL>
 __global__ void __launch_bounds__(256) coif_level_kernel(const __grid_constant__ CoifLevelArgs a) {
-  __shared__ float2 in[4][kCoifNY][kCoifNX];  // LL, LH (high x), HL (high y), HH
+  // LL, LH (high x), HL (high y), HH; input column c at index c + 1 (the
+  // row holds columns -1 .. kCoifNX, so that cell pairs land 16-byte aligned).
+  __shared__ __align__(16) float2 in[4][kCoifNY][kCoifNX + 2];
   __shared__ float2 lx[kCoifTY][kCoifNX], hx[kCoifTY][kCoifNX];
   const int S = a.side >> (a.l - 1), hh = S / 2;
   const int TX = FULL ? kCoifTX : min(kCoifTX, S), TY = FULL ? kCoifTY : min(kCoifTY, S);
@@ -94,32 +104,32 @@ __global__ void __launch_bounds__(256) coif_level_kernel(const __grid_constant__
     return (v % hh + hh) % hh;
   };
   if (FULL) {
-    // Pairs of neighbouring cells (P even, P + 1) in one 16-byte load: both
+    // Pairs of neighbouring cells (P even, P + 1) in one 16-byte copy: both
     // lie in one row of one tile of the buffer (P and P + 1 differ only in
     // the lowest bit) or of the dense low-pass band, and never straddle the
     // periodic wrap (the half side is even).  Input columns c = P - bx run
-    // from -1 to kCoifNX; the two outside [0, kCoifNX) are dropped.
+    // from -1 to kCoifNX, shared indices 0 .. kCoifNX + 1.  The copies are
+    // asynchronous (global to shared, no registers), so all of a thread's
+    // copies are in flight together.
     constexpr int NP = kCoifNX / 2 + 1;  // pairs per input row
     for (int i = threadIdx.x; i < 4 * kCoifNY * NP; i += blockDim.x) {
       const int part = i / (kCoifNY * NP), r = (i / NP) % kCoifNY, j = i % NP;
-      const int c0 = 2 * j - 1;  // column of the pair's first cell
-      const int P = wrap(bx + c0), Q = wrap(by + r);
-      float4 v;
+      const int P = wrap(bx + 2 * j - 1), Q = wrap(by + r);
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(&in[part][r][2 * j]);
       if (part == 0 && a.prev) {
-        v = *reinterpret_cast<const float4*>(a.prev + (size_t)Q * hh + P);
+        cp_async16(dst, a.prev + (size_t)Q * hh + P);
       } else {
         const size_t tile = (size_t)(Q >> m) * ntx + (P >> m);
         const int slot = part == 0 ? 0 : (part << (2 * m)) + ((Q & msk) << m) + (P & msk);
         if (m == 0) {  // the coarsest level: neighbouring cells are in neighbouring tiles
-          const float2 v0 = a.wbuf[tile * TSL + slot], v1 = a.wbuf[(tile + 1) * TSL + slot];
-          v = make_float4(v0.x, v0.y, v1.x, v1.y);
+          cp_async8(dst, a.wbuf + tile * TSL + slot);
+          cp_async8(dst + 8u, a.wbuf + (tile + 1) * TSL + slot);
         } else {
-          v = *reinterpret_cast<const float4*>(a.wbuf + tile * TSL + slot);
+          cp_async16(dst, a.wbuf + tile * TSL + slot);
         }
       }
-      if (c0 >= 0) in[part][r][c0] = make_float2(v.x, v.y);
-      if (c0 + 1 < kCoifNX) in[part][r][c0 + 1] = make_float2(v.z, v.w);
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
   }
   for (int i = threadIdx.x; !FULL && i < 4 * NY * NX; i += blockDim.x) {
     const int part = i / (NY * NX), r = (i / NX) % NY, c = i % NX;
@@ -133,7 +143,7 @@ __global__ void __launch_bounds__(256) coif_level_kernel(const __grid_constant__
       const int slot = part == 0 ? 0 : (part << (2 * m)) + ((Q & msk) << m) + (P & msk);
       v = a.wbuf[tile * TSL + slot];
     }
-    in[part][r][c] = v;
+    in[part][r][c + 1] = v;
   }
   __syncthreads();
   const CoifTaps& t = a.t;
@@ -159,10 +169,10 @@ __global__ void __launch_bounds__(256) coif_level_kernel(const __grid_constant__
 #pragma unroll
     for (int r = 0; r < 6; ++r) {
       const int rr = min(yb / 2 + r, NY - 1);
-      s0[r] = in[0][rr][c];
-      d0[r] = in[2][rr][c];
-      s1[r] = in[1][rr][c];
-      d1[r] = in[3][rr][c];
+      s0[r] = in[0][rr][c + 1];
+      d0[r] = in[2][rr][c + 1];
+      s1[r] = in[1][rr][c + 1];
+      d1[r] = in[3][rr][c + 1];
     }
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
