@@ -19,7 +19,7 @@
 //      varies, the exact fixed-point sums do not); a batch with more passes
 //      than the list holds is numbered by a block-wide scan instead and
 //      visited in windows;
-//   4. deals the passes to the warps in groups of two, lane i visiting
+//   4. deals the passes to the warps in groups of three, lane i visiting
 //      entries i and i + 32 of a pass: one 8-byte record load (plane code,
 //      value), the survivor's level base from shared memory, a_j * c, one
 //      shared-memory add at base + code (no bounds test: coefficients that
@@ -45,7 +45,7 @@ namespace {
 
 constexpr int kMaxCellRows = 256;
 constexpr int kPass = 64;         // LUT entries per pass (two per lane)
-constexpr int kPassUnroll = 2;    // passes a warp has in flight
+constexpr int kPassUnroll = 3;    // passes a warp has in flight, at most (see PU in the kernel)
 constexpr int kSlotChunk = 4;     // LUT range slots a thread has in flight while building passes
 constexpr int kRangeMin = 1024;   // pass capacity per window, at least
 constexpr int kRangeMax = 8192;   // pass capacity per window, at most
@@ -120,7 +120,8 @@ __device__ __forceinline__ int last_le(const int* pre, int lo, int hi, int v) {
 
 struct Smem {
   float2* acc;   // accumulator planes (plane_total cells: complex, or real parts only), see plane_code
-  int4* sp;      // survivors: Ax, Ay, depth, amplitude bits (a_j times the fixed-point scale)
+  int4* sp;      // survivors: tile_off index of the first range, rows, tiles per row, amplitude bits
+                 // (a_j times the fixed-point scale)
   int* sb;       // survivors x 8: at index l, the byte offset of level l's base cell minus (l << 29)
   int4* pass;    // passes: first LUT entry, entries, shared address of the survivor's sb row, amplitude bits
   int2* dbox;    // depths: tlo, thi
@@ -593,6 +594,9 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
   const int k = T >> L;
   constexpr bool RE = MODE == kModeRe;
   constexpr bool re_acc = RE;
+  // Passes a warp has in flight: three where the registers allow it (FP32
+  // LUT, plane reference, three or more levels), else two.
+  constexpr int PU = (MODE == kModeRef || DT != WASABI_F32 || L <= 2) ? 2 : kPassUnroll;
   const int rcap = a.rcap;
   const int P = survivor_cap(rcap);
   const int lmin = a.lut.lmin;
@@ -600,7 +604,7 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
   Smem S;
   smem_layout(T, L, lmin, a.lut.D, re_acc, rcap, &S, smem);
   const int NW = NA * (re_acc ? 1 : 2);  // accumulator words (a multiple of 4)
-  __shared__ int s_st, s_n, s_np, s_total;
+  __shared__ int s_st, s_n, s_np, s_rmax, s_total;
   __shared__ int warp_buf[32];
   __shared__ int s_rowstart[kMaxCellRows], s_rowpre[kMaxCellRows + 1];
   // Per level l: index of the first super-tile cell past the guard, row
@@ -718,6 +722,7 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
       if (tid == 0) {
         s_n = 0;
         s_np = 0;
+        s_rmax = 1;
       }
       __syncthreads();
       if (tid < CH && c0 + tid < total) {
@@ -731,7 +736,14 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
             Ay + bx.y + 1 >= Sy) {
           const int s = atomicAdd(&s_n, 1);
           const float amp = __int_as_float(p.z) * (fixed ? qs : 1.0f);
-          S.sp[s] = make_int4(Ax, Ay, p.w, __float_as_int(amp));
+          // The survivor's window tiles that can land in the super-tile (its
+          // depth's tile box shifted by (Ax, Ay), one tile of carry): rows
+          // tya .. tyb, columns txa .. txb; one LUT range per row.
+          const int tya = max(bx.x, Sy - Ay - 1), tyb = min(bx.y, Sy + ky - 1 - Ay);
+          const int txa = max(bx.x, Sx - Ax - 1), txb = min(bx.y, Sx + kx - 1 - Ax);
+          const int rows = txa <= txb ? max(0, tyb - tya + 1) : 0;
+          S.sp[s] = make_int4(p.w * ntpd + tya * lut.nwt + txa, rows, txb - txa + 1, __float_as_int(amp));
+          atomicMax(&s_rmax, rows);
           // shift_l(X) of Eq. (2): floor((X + half * 2^(l-1)) / 2^l), made
           // relative to the super-tile origin in level-l units, folded with
           // the level's accumulator offset into one base per level (minus
@@ -745,11 +757,11 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
       }
       __syncthreads();
       const int n = s_n;
-      // ---- slot f = s * (k + 1) + j is window-tile row j of the survivor's
-      // clipped tile box.
-      const int K1 = k + 1;
+      // ---- slot f = s * K1 + j is window-tile row j of the survivor's
+      // clipped tile box (K1: the batch's most rows, at most k + 1).
+      const int K1 = s_rmax;
       const int nslot = n * K1;
-      const unsigned sp_s = sh_addr(S.sp), sb_s = sh_addr(S.sb), pass_s = sh_addr(S.pass), box_s = sh_addr(S.dbox);
+      const unsigned sp_s = sh_addr(S.sp), sb_s = sh_addr(S.sb), pass_s = sh_addr(S.pass);
       const unsigned acc_s = sh_addr(S.acc);
       // Walks this thread's slots t, t + NT, t + 2 NT, ... kSlotChunk at a
       // time, the LUT range loads of a chunk in flight together, and calls
@@ -770,14 +782,10 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
             am[c] = 0;
             if (f0 + c * NT + tid < nslot) {
               const int4 sp = lds128(sp_s + 16u * s);
-              const int2 bx = lds64(box_s + 8u * sp.z);
-              const int row = max(bx.x, Sy - sp.y - 1) + j;
-              const int tyb = min(bx.y, Sy + ky - 1 - sp.y);
-              const int txa = max(bx.x, Sx - sp.x - 1), txb = min(bx.y, Sx + kx - 1 - sp.x);
-              if (row <= tyb && txa <= txb) {
-                const int* to = lut.tile_off + sp.z * ntpd + row * lut.nwt;
-                st[c] = __ldg(to + txa);
-                ln[c] = __ldg(to + txb + 1);
+              if (j < sp.y) {
+                const int* to = lut.tile_off + sp.x + j * lut.nwt;
+                st[c] = __ldg(to);
+                ln[c] = __ldg(to + sp.z);
               }
               am[c] = sp.w;
             }
@@ -798,7 +806,7 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
         }
       };
       // ---- visits: warp w takes groups w, w + warps, ... of the ng groups
-      // of kPassUnroll passes; a group's records and LUT loads are all
+      // of PU passes; a group's records and LUT loads are all
       // issued before any is consumed.  Lane i visits entries i, i + 32, ...
       // of each pass; lanes past a pass's end load a valid entry and add
       // nothing.
@@ -806,14 +814,14 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
           constexpr bool FX = decltype(fixed_tag)::value;
           constexpr int EPL = kPass / 32;  // entries per lane and pass
           for (int g = warp; g < ng; g += nwarps) {
-            uint2 rec[kPassUnroll][EPL];
-            float vy[kPassUnroll][EPL];  // FP32 imaginary part (complex accumulation), or the block scale
-            unsigned sbo[kPassUnroll];
-            float amp[kPassUnroll];
-            int cnt[kPassUnroll];
+            uint2 rec[PU][EPL];
+            float vy[PU][EPL];  // FP32 imaginary part (complex accumulation), or the block scale
+            unsigned sbo[PU];
+            float amp[PU];
+            int cnt[PU];
 #pragma unroll
-            for (int u = 0; u < kPassUnroll; ++u) {
-              const int4 r = lds128(pass_s + 16u * (kPassUnroll * g + u));
+            for (int u = 0; u < PU; ++u) {
+              const int4 r = lds128(pass_s + 16u * (PU * g + u));
               cnt[u] = r.y;
               sbo[u] = (unsigned)r.z;
               amp[u] = __int_as_float(r.w);
@@ -826,7 +834,7 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
               }
             }
 #pragma unroll
-            for (int u = 0; u < kPassUnroll; ++u) {
+            for (int u = 0; u < PU; ++u) {
 #pragma unroll
               for (int h = 0; h < EPL; ++h) {
                 const int li = lane + 32 * h;
@@ -860,8 +868,8 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
       auto pad_visit = [&](int np) {
         // The last group is filled with empty passes (no entries; their
         // loaded entries are entry 0 and their level bases those of survivor 0).
-        const int ng = (np + kPassUnroll - 1) / kPassUnroll;
-        if (tid < ng * kPassUnroll - np) S.pass[np + tid] = make_int4(1, 0, (int)sb_s, 0);
+        const int ng = (np + PU - 1) / PU;
+        if (tid < ng * PU - np) S.pass[np + tid] = make_int4(1, 0, (int)sb_s, 0);
         __syncthreads();
         if (fixed) visit(std::true_type{}, ng);
         else visit(std::false_type{}, ng);
