@@ -48,19 +48,28 @@ __host__ __device__ inline void unpack_pos(uint32_t pos, int* p, int* q, int* le
 // level's offset, in the same units) gives the accumulator address, with no
 // bounds test (every visited coefficient lands inside the guard band by
 // construction of the LUT ranges).
-__host__ __device__ inline int plane_side(int k, int L, int l) { return (k + 2) << (L - l); }
-__host__ __device__ inline int plane_row(int k, int L, int l) { return plane_side(k, L, l) + 1; }
-__host__ __device__ inline int plane_size(int k, int L, int l) {
+__host__ __device__ constexpr int plane_side(int k, int L, int l) { return (k + 2) << (L - l); }
+__host__ __device__ constexpr int plane_row(int k, int L, int l) { return plane_side(k, L, l) + 1; }
+__host__ __device__ constexpr int plane_size(int k, int L, int l) {
   const int n = plane_row(k, L, l) * plane_side(k, L, l);
   return n + ((4 - n % 16) + 16) % 16;
 }
-__host__ __device__ inline int plane_count(int L, int l) { return l == L ? 4 : 3; }
+__host__ __device__ constexpr int plane_count(int L, int l) { return l == L ? 4 : 3; }
 __host__ __device__ inline uint32_t plane_code(uint32_t pos, int L, int k) {
   int p, q, lev, band;
   unpack_pos(pos, &p, &q, &lev, &band);
   if (lev < 1 || lev > L) return 0;  // unused capacity: never visited
   const int bi = lev == L ? band : band - 1;
   return ((uint32_t)lev << 29) | (uint32_t)(4 * (bi * plane_size(k, L, lev) + q * plane_row(k, L, lev) + p));
+}
+// Index of level l's first super-tile cell past the guard band (planes of the
+// coarse levels first, levels below lmin absent).
+__host__ __device__ constexpr int plane_first(int k, int L, int lmin, int l) {
+  int base = 0;
+  for (int m = L; m > l; --m)
+    if (m >= lmin) base += plane_count(L, m) * plane_size(k, L, m);
+  const int g = 1 << (L - l);
+  return base + g * plane_row(k, L, l) + g;
 }
 // Accumulator size (cells, a multiple of 4) for levels lmin..L.
 __host__ __device__ inline int plane_total(int k, int L, int lmin) {

@@ -404,7 +404,9 @@ struct EpiVal<true> { using T = float; };
 // halvings, so the signs are those of the scaled field); re_acc: the
 // accumulator holds real parts only.  Otherwise complex values go to u and/or
 // are binarised.
-template <int L, bool RE_ONLY>
+// KC > 0: the form for super-tiles of k = KC tiles with fixed-point sums and
+// lmin = LMC (the caller checks), the layout then known at compile time.
+template <int L, bool RE_ONLY, int KC = 0, int LMC = 0>
 __device__ __forceinline__ void supertile_inverse8(const float2* acc, bool fixed, bool re_acc, float dq, int lmin,
                                                    int k, int kx, int ky, int Sx, int Sy, const JobDev& J,
                                                    const int* lvC, const int* lvG, const int* lvPS, int tid,
@@ -412,11 +414,22 @@ __device__ __forceinline__ void supertile_inverse8(const float2* acc, bool fixed
   static_assert(L >= 3, "8 x 8 blocks need at least three levels");
   using V = typename EpiVal<RE_ONLY>::T;
   int C[L + 1], G[L + 1], PS[L + 1];
+  if constexpr (KC > 0) {
+    fixed = true;
+    lmin = LMC;
+    k = KC;
+  }
 #pragma unroll
   for (int l = 1; l <= L; ++l) {
-    C[l] = lvC[l];
-    G[l] = lvG[l];
-    PS[l] = lvPS[l];
+    if constexpr (KC > 0) {
+      C[l] = plane_first(KC, L, LMC, l);
+      G[l] = plane_row(KC, L, l);
+      PS[l] = plane_size(KC, L, l);
+    } else {
+      C[l] = lvC[l];
+      G[l] = lvG[l];
+      PS[l] = lvPS[l];
+    }
   }
   const unsigned acc_s = sh_addr(acc);
   auto zero = []() -> V {
@@ -625,13 +638,10 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
     S.dbox[d] = make_int2(m.tlo, m.thi);
   }
   if (tid == 0) {
-    int base = 0;
     for (int l = L; l >= 1; --l) {
-      const int R = plane_row(k, L, l), g = 1 << (L - l);
-      lvG[l] = R;
+      lvG[l] = plane_row(k, L, l);
       lvPS[l] = plane_size(k, L, l);
-      lvC[l] = base + g * R + g;
-      if (l >= lmin) base += plane_count(L, l) * lvPS[l];
+      lvC[l] = plane_first(k, L, lmin, l);
     }
   }
   int* counter = &a.batch->counter;
@@ -747,11 +757,14 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
           // shift_l(X) of Eq. (2): floor((X + half * 2^(l-1)) / 2^l), made
           // relative to the super-tile origin in level-l units, folded with
           // the level's accumulator offset into one base per level (minus
-          // the level bits of the plane codes it is added to).
+          // the level bits of the plane codes it is added to), plus the
+          // accumulator's shared address (halved for complex cells, whose
+          // word offsets are doubled).
+          const unsigned acc0 = sh_addr(S.acc) >> (re_acc ? 0 : 1);
           for (int l = lmin; l <= L; ++l) {
             const int hb = half << (l - 1);
             const int ox = ((X + hb) >> l) - (Sx << (L - l)), oy = ((Y + hb) >> l) - (Sy << (L - l));
-            S.sb[s * 8 + l] = (int)(4u * (unsigned)(lvC[l] + oy * lvG[l] + ox) - ((unsigned)l << 29));
+            S.sb[s * 8 + l] = (int)(acc0 + 4u * (unsigned)(lvC[l] + oy * lvG[l] + ox) - ((unsigned)l << 29));
           }
         }
       }
@@ -762,7 +775,6 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
       const int K1 = s_rmax;
       const int nslot = n * K1;
       const unsigned sp_s = sh_addr(S.sp), sb_s = sh_addr(S.sb), pass_s = sh_addr(S.pass);
-      const unsigned acc_s = sh_addr(S.acc);
       // Walks this thread's slots t, t + NT, t + 2 NT, ... kSlotChunk at a
       // time, the LUT range loads of a chunk in flight together, and calls
       // fn(st, ln, sv, am, np) per chunk with each slot's first entry, entry
@@ -841,18 +853,18 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
                 const uint2 pe = rec[u][h];
                 const float2 v = DT == WASABI_F32 ? make_float2(__uint_as_float(pe.y), vy[u][h])
                                                   : decode16<DT>(pe.y, vy[u][h]);
-                // Byte offset of the accumulator word: plane code plus the
-                // survivor's base of the code's level (which carries minus
-                // the level bits).
+                // Shared address of the accumulator word (halved for complex
+                // cells): plane code plus the survivor's base of the code's
+                // level (which carries minus the level bits).
                 const unsigned ab = pe.x + (unsigned)lds32(sbo[u] + 4u * (pe.x >> 29));
                 // a_j c in FP32; in fixed point exactly scaled by 2^sh (folded
                 // into amp) and rounded to the nearest integer: the integer
                 // sums are exact.
                 if constexpr (re_acc) {
-                  if constexpr (FX) red_add_lt(acc_s + ab, __float2int_rn(amp[u] * v.x), li, cnt[u]);
-                  else red_add_lt(acc_s + ab, amp[u] * v.x, li, cnt[u]);
+                  if constexpr (FX) red_add_lt(ab, __float2int_rn(amp[u] * v.x), li, cnt[u]);
+                  else red_add_lt(ab, amp[u] * v.x, li, cnt[u]);
                 } else {
-                  const unsigned a2 = acc_s + 2u * ab;
+                  const unsigned a2 = 2u * ab;
                   if constexpr (FX) {
                     red_add_lt(a2, __float2int_rn(amp[u] * v.x), li, cnt[u]);
                     red_add_lt(a2 + 4u, __float2int_rn(amp[u] * v.y), li, cnt[u]);
@@ -1017,11 +1029,18 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
     }
     if constexpr (RE) {  // bits alone, plane reference (the host sends nothing else here)
       if (J.bits != nullptr) {
-        if constexpr (L >= 3)
-          supertile_inverse8<L, true>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid, NT);
-        else if constexpr (L == 2)
+        constexpr int KD = kMaxSuperTile >> L;  // the widest super-tile, the default for bits
+        if constexpr (L >= 3) {
+          if (k == KD && lmin == 2 && fixed)
+            supertile_inverse8<L, true, KD, 2>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS,
+                                               tid, NT);
+          else
+            supertile_inverse8<L, true>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid,
+                                        NT);
+        } else if constexpr (L == 2) {
           supertile_inverse<L, true, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS,
                                             tid, NT, nullptr);
+        }
       }
     } else if (MODE == kModeRef && L >= 2 && J.bits != nullptr && J.ref.kind != 0) {
       supertile_inverse<L, false, MODE == kModeRef>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG,
