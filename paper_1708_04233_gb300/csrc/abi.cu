@@ -427,7 +427,7 @@ wasabi_status wasabi_build_lut_wavelet(double lambda, double pitch, const double
     const int unit = std::max(1 << levels, 32);  // super-tile sides: multiples of 32 and of 2^L
     for (int T = unit; T <= kMaxSuperTile && lut->ncode < kMaxCodes; T += unit) lut->code_k[lut->ncode++] = T >> levels;
   }
-  c.take<uint2>((size_t)lut->ncode * (size_t)base);                 // plane-code records
+  c.take<uint2>((size_t)lut->ncode * (size_t)base + kCodePad);      // plane-code records
   const size_t persist_bytes = align_up(c.off, 256);
   cudaError_t e = pool_alloc(&lut->block, persist_bytes, s);
   if (e != cudaSuccess) { delete lut; set_error("build_lut: cudaMallocAsync: %s", cudaGetErrorString(e)); return WASABI_E_NOMEM; }
@@ -444,7 +444,14 @@ wasabi_status wasabi_build_lut_wavelet(double lambda, double pitch, const double
   lut->nr_dev = c.take<long long>((size_t)n_depths);
   lut->cmax = c.take<float>(1);
   lut->levels = c.take<unsigned>(1);
-  lut->code = c.take<uint2>((size_t)lut->ncode * (size_t)base);
+  lut->code = c.take<uint2>((size_t)lut->ncode * (size_t)base + kCodePad);
+  e = cudaMemsetAsync(lut->code + (size_t)lut->ncode * (size_t)base, 0, kCodePad * sizeof(uint2), s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(lut->block, s);
+    delete lut;
+    set_error("build_lut: %s", cudaGetErrorString(e));
+    return WASABI_E_CUDA;
+  }
 
   // Build scratch.
   Carver sc;

@@ -79,6 +79,9 @@ __host__ __device__ inline int plane_total(int k, int L, int lmin) {
 }
 // Widest super-tile (pixels) the superposition takes.
 constexpr int kMaxSuperTile = 256;
+// Records allocated past the last plane-code array: the superposition's
+// lanes past a pass's end read up to one pass (64 records) beyond it.
+constexpr int kCodePad = 64;
 // Most plane codes a LUT keeps: one per super-tile width k the superposition
 // can use (super-tiles are multiples of 32 pixels, at most kMaxSuperTile).
 constexpr int kMaxCodes = kMaxSuperTile / 32;

@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
     // Fixed-point scale 2^sh: every partial sum stays below 2^31 in magnitude.
     const float bound = (float)total * (J.amax * cmax);
     const int sh = bound > 0.f ? max(-100, min(30, (int)floorf(log2f(2.0e9f / bound)))) : 30;
-    const float qs = ldexpf(1.0f, sh);
+    const float qs = __int_as_float((sh + 127) << 23);  // 2^sh (-100 <= sh <= 30)
 
     const int CH = min(P, NT);  // candidates per batch: at most one per thread
     for (int c0 = 0; c0 < total; c0 += CH) {
@@ -782,8 +782,13 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
       // chunk's passes; fn returns false to stop.  While fn returns true the
       // trip count is the same for every thread.
       auto walk_slots = [&](auto&& fn) {
-        int s = tid / K1, j = tid - s * K1;
-        const int ds = NT / K1, dj = NT - ds * K1;
+        // tid / K1 and NT / K1 in FP32: n + 1/2 is exact and the product's
+        // relative error is below 2^-23, so for n <= 1024 and K1 <= 257 it
+        // stays under the 1 / (2 K1) that separates n / K1 + 1 / (2 K1) from
+        // the next integer.
+        const float rk = __frcp_rn((float)K1);
+        int s = __float2int_rz(((float)tid + 0.5f) * rk), j = tid - s * K1;
+        const int ds = __float2int_rz(((float)NT + 0.5f) * rk), dj = NT - ds * K1;
         for (int f0 = 0; f0 < nslot; f0 += kSlotChunk * NT) {
           int st[kSlotChunk], ln[kSlotChunk], sv[kSlotChunk], am[kSlotChunk];
 #pragma unroll
@@ -812,7 +817,7 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
 #pragma unroll
           for (int c = 0; c < kSlotChunk; ++c) {
             ln[c] -= st[c];
-            np += (ln[c] + kPass - 1) / kPass;
+            np += (int)((unsigned)(ln[c] + kPass - 1) / kPass);  // ln >= 0
           }
           if (!fn(st, ln, sv, am, np)) break;
         }
@@ -820,8 +825,9 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
       // ---- visits: warp w takes groups w, w + warps, ... of the ng groups
       // of PU passes; a group's records and LUT loads are all
       // issued before any is consumed.  Lane i visits entries i, i + 32, ...
-      // of each pass; lanes past a pass's end load a valid entry and add
-      // nothing.
+      // of each pass; lanes past a pass's end load the records that follow
+      // (a code array is followed by the next one or by kCodePad records of
+      // padding) and add nothing.
       auto visit = [&](auto fixed_tag, int ng) {
           constexpr bool FX = decltype(fixed_tag)::value;
           constexpr int EPL = kPass / 32;  // entries per lane and pass
@@ -839,7 +845,7 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
               amp[u] = __int_as_float(r.w);
 #pragma unroll
               for (int h = 0; h < EPL; ++h) {
-                const int e = r.x + min(lane + 32 * h, r.y - 1);
+                const int e = r.x + lane + 32 * h;
                 rec[u][h] = __ldg(&lut.code[e]);
                 if (DT != WASABI_F32) vy[u][h] = __ldg(&lut.scale[e >> 5]);
                 else if (!re_acc) vy[u][h] = __ldg(&lut.val[e].y);
@@ -945,7 +951,7 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
     }
 
 
-    const float dq = ldexpf(1.0f, -sh);
+    const float dq = __int_as_float((127 - sh) << 23);  // 2^-sh
     // Write the super-tile's tiles to the tile-major buffer: each tile's TSL
     // slots are contiguous there; slots of levels finer than lmin are zero.
     // Slot -> accumulator offset table (in the free pass records): offset of
