@@ -50,6 +50,7 @@ constexpr int kSlotChunk = 4;     // LUT range slots a thread has in flight whil
 constexpr int kRangeMin = 1024;   // pass capacity per window, at least
 constexpr int kRangeMax = 8192;   // pass capacity per window, at most
 constexpr int kSurvMax = 1024;    // survivors per candidate batch, at most
+constexpr int kComplexTile = 192;  // default super-tile side (pixels) of complex accumulation
 // Dynamic shared memory per CTA that still lets two CTAs share an SM (with
 // the kernel's static shared memory and the per-CTA reservation).
 constexpr size_t kTwoCtaSmem = 104 * 1024;
@@ -1052,9 +1053,15 @@ __global__ void __launch_bounds__(1024, 1) superpose_kernel(SuperposeArgs a) {
       supertile_inverse<L, false, MODE == kModeRef>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG,
                                                     lvPS, tid, NT, &s_ref);
     } else if (J.u != nullptr) {
-      if constexpr (L >= 3)
-        supertile_inverse8<L, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid, NT);
-      else if constexpr (L == 2)
+      if constexpr (L >= 3) {
+        constexpr int KX = kComplexTile >> L;  // the default super-tile of complex accumulation
+        if (k == KX && lmin == 2 && fixed)
+          supertile_inverse8<L, false, KX, 2>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS,
+                                              tid, NT);
+        else
+          supertile_inverse8<L, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS, tid,
+                                       NT);
+      } else if constexpr (L == 2)
         supertile_inverse<L, false, false>(S.acc, fixed, re_acc, dq, lmin, k, kx, ky, Sx, Sy, J, lvC, lvG, lvPS,
                                            tid, NT, nullptr);
     } else if (J.bits != nullptr) {
@@ -1145,7 +1152,7 @@ void superpose_default_config(int L, int lmin, int D, int kind, int* cell, int* 
     for (int T = kMaxSuperTile / unit * unit; T >= 128 && T >= unit; T -= unit)
       if (fits_one(T)) { *cell = T; *threads = 1024; return; }
   } else if (kind == kConfigComplex) {
-    for (int T : {192, 128})
+    for (int T : {kComplexTile, 128})
       if (T % unit == 0 && fits_one(T)) { *cell = T; *threads = 1024; return; }
   }
   int T = 256;
