@@ -38,13 +38,13 @@ UNIT = "Mpoint*coeff/s"
 # dram__bytes_write.sum from one ncu capture, scaled to a full launch), valid
 # only while the kernel source is the one that was profiled (sha256 prefix of
 # superpose.cu).
-# Captured on the 32,768^2 slice of C3 (10.7 MB read + 79.4 MB written) and
+# Captured on the 32,768^2 slice of C3 (10.6 MB read + 79.2 MB written) and
 # scaled by the point-coefficients processed (x4.015).
-TRAFFIC = {("C3", "fused"): ("17c10ba23febed89", (10.708e6 + 79.382e6) * 4.015)}
+TRAFFIC = {("C3", "fused"): ("c5b7dd36496046a9", (10.596e6 + 79.180e6) * 4.015)}
 # The same kernel's issue-slot utilisation and warp instructions per
 # point·coefficient from its full ncu capture (32,768^2 slice of C3): the
 # instruction roofline it is bound by.
-ISSUE = {("C3", "fused"): ("17c10ba23febed89", 0.598, 1.97)}
+ISSUE = {("C3", "fused"): ("c5b7dd36496046a9", 0.598, 1.97)}
 
 
 def _sha(name):
